@@ -1,0 +1,233 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix:
+the exact solution (Eq. ex_Jac_appl), the algebraic forms Eq. P1 / Eq. P2 of
+Alg. 2 / Alg. 4, the exactness limit M^-1 = J^-1, Prop. 3.1, GMRES theory,
+the greedy-MIS theorem, the Chebyshev polynomial and the fixed-stress
+bound."""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fracgen
+from oracle import amg as oamg
+from oracle import dense, rng, schur
+from oracle import sparse as osp
+from oracle.amg import AMG, AmgOptions
+from oracle.fgmres import fgmres
+from oracle.precond import BlockPreconditioner
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_oracle_rng_reference_outputs():
+    ref = [int(l, 16) for l in open(os.path.join(GOLD, "splitmix64_seed0.txt"))
+           if l.strip() and not l.startswith("#")]
+    assert [int(v) for v in rng.rand_u64(0, 0, np.arange(4))] == ref
+    u = rng.uniform(7, 3, np.arange(100000))
+    assert u.min() >= 0 and u.max() < 1 and abs(u.mean() - 0.5) < 5e-3
+
+
+@pytest.fixture(scope="module")
+def small_mixed():
+    # 4^3 cells, three central planes, stick/slip/open mix; ~840 unknowns
+    return fracgen.generate("planes64", N=4, seed=2)
+
+
+@pytest.mark.parametrize("variant", ["tpu", "tup"])
+def test_fgmres_matches_dense_solution(tiny, variant):
+    J = osp.jacobian(tiny)
+    xs = dense.solve(tiny)
+    M = BlockPreconditioner(tiny, variant, opt=AmgOptions(coarse_max=64))
+    r = fgmres(lambda v: J @ v, M, tiny.b, tol=1e-12, maxit=300)
+    # the true residual floors near eps * || |J| |x| || / ||b|| ~ 1e-10 here
+    # (tractions are ~1e7 times the displacements); the solution is tighter
+    assert r.relres <= 1e-9
+    assert np.linalg.norm(r.x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("variant", ["tpu", "tup"])
+def test_algorithm_equals_block_factor_form(small_mixed, variant):
+    """Alg. 2 (Alg. 4) with exact inner solves is the operator of Eq. P1
+    (Eq. P2)."""
+    P = small_mixed
+    assert set(np.unique(P.state)) == {0, 1, 2}
+    M = BlockPreconditioner(P, variant, "exact", "exact")
+    Md = dense.m1_matrix(P) if variant == "tpu" else dense.m2_matrix(P)
+    rs = np.random.default_rng(5)
+    for _ in range(3):
+        w = rs.standard_normal(P.n)
+        a, b = M(w), Md @ w
+        assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("variant", ["tpu", "tup"])
+def test_exact_factors_give_one_iteration(variant):
+    """All faces open: H is block diagonal, so H~ = H; with the exact Schur
+    complements S (Eq. Schur_1) or S2 (Eq. Schur2_2) the inexact LDU of
+    Eq. LDU1/LDU2 is exact, M^-1 = J^-1, and FGMRES stops after one step."""
+    P = fracgen.generate("planes64", N=4, p_stick=0.0, p_slip=0.0, seed=1)
+    assert np.all(P.state == 2)
+    J = osp.jacobian(P)
+    if variant == "tpu":
+        M = BlockPreconditioner(P, "tpu", "exact", "exact",
+                                u_matrix=sp.csr_matrix(dense.schur_exact_tpu(P)))
+    else:
+        M = BlockPreconditioner(P, "tup", "exact", "exact",
+                                p_matrix=sp.csr_matrix(dense.schur2_exact(P)))
+    r = fgmres(lambda v: J @ v, M, P.b, tol=1e-10, maxit=20)
+    assert r.iters == 1 and r.relres <= 1e-9
+
+
+def test_prop31_unit_eigenvalues_tpu(small_mixed):
+    """Prop. 3.1: M1^-1 J has the eigenvalue 1 with multiplicity >= n_p."""
+    P = small_mixed
+    J = osp.jacobian(P).toarray()
+    ev = np.linalg.eigvals(dense.m1_matrix(P) @ J)
+    assert np.sum(np.abs(ev - 1.0) < 1e-7) >= P.n_p
+
+
+def test_S1_positive_definite_and_S2_symmetric(small_mixed):
+    """S1 is positive definite in every state; S~2 is symmetric (Sec. 3.2)."""
+    P = small_mixed
+    S1 = schur.s1(P).toarray()
+    assert np.linalg.eigvalsh(0.5 * (S1 + S1.T)).min() > 0
+    S2 = schur.s2_tilde(P, schur.s1(P)).toarray()
+    assert np.abs(S2 - S2.T).max() <= 1e-14 * np.abs(S2).max()
+
+
+def test_fixed_stress_sign_and_bound():
+    """With p^l = 0 the flux derivative F_u vanishes, Q2 = -Psi(Q1^T)/dt, and
+    for S1 SPD the local diagonal of Eq. FS_algebraic is negative on open
+    faces, zero elsewhere, and bounded by the exact diag(Q2 S1^-1 Q1):
+    (S1_KK)^-1 <= (S1^-1)_KK in the Loewner order."""
+    P = fracgen.generate("planes64", N=4, p_stick=0.7, p_slip=0.0, pl_scale=0.0, seed=3)
+    S1 = schur.s1(P)
+    assert abs(S1 - S1.T).max() <= 1e-12 * abs(S1).max()
+    sk = schur.fixed_stress(P, S1)
+    d = dense.blocks_dense(P)
+    exact = np.diag(d["Q2"] @ np.linalg.solve(S1.toarray(), d["Q1"]))
+    open_ = P.state == 2
+    assert open_.any() and np.all(sk[open_] < 0) and np.all(sk[~open_] == 0)
+    assert np.all(np.abs(sk[open_]) <= np.abs(exact[open_]) * (1 + 1e-12))
+
+
+def test_fgmres_identity_preconditioner_distinct_eigenvalues():
+    """GMRES on a diagonal matrix with k distinct eigenvalues terminates in k
+    steps (minimal polynomial of degree k)."""
+    k = 5
+    d = np.repeat(np.arange(1.0, k + 1), 40)
+    b = np.random.default_rng(0).standard_normal(d.size)
+    r = fgmres(lambda v: d * v, lambda v: v, b, tol=1e-13, maxit=50)
+    assert r.iters == k
+    assert np.linalg.norm(r.x - b / d) <= 1e-12 * np.linalg.norm(b / d)
+
+
+def _parallel_mis2(W, keys):
+    """The fixed-priority parallel rule: a node joins when its key is the
+    largest among undecided nodes within distance 2; nodes within distance 2
+    of a new root drop out."""
+    n = W.shape[0]
+    A = (W != 0).astype(int).tolil()
+    A.setdiag(1)
+    A = A.tocsr()
+    deg = np.diff(W.indptr)
+    und = deg > 0
+    root = np.zeros(n, bool)
+    kf = keys.astype(np.float64)
+    while und.any():
+        m1 = np.array([kf[A.indices[A.indptr[v]:A.indptr[v + 1]]][und[A.indices[A.indptr[v]:A.indptr[v + 1]]]].max()
+                       if und[A.indices[A.indptr[v]:A.indptr[v + 1]]].any() else -1.0 for v in range(n)])
+        m2 = np.array([m1[A.indices[A.indptr[v]:A.indptr[v + 1]]].max() for v in range(n)])
+        new = und & (kf == m2)
+        root |= new
+        near = (A @ new.astype(int)) > 0
+        near2 = (A @ near.astype(int)) > 0
+        und &= ~near2
+    return root
+
+
+def test_mis2_greedy_equals_parallel_rule_and_is_maximal():
+    rs = np.random.default_rng(11)
+    for trial in range(4):
+        n = 120
+        M = sp.random(n, n, density=0.03, random_state=rs, format="csr")
+        W = (M + M.T).tocsr()
+        W.setdiag(0)
+        W.eliminate_zeros()
+        keys = oamg.priority_keys(n, trial, 0)
+        # float64 keeps the order of these 64-bit keys: top bits are random
+        assert len(np.unique(keys.astype(np.float64))) == n
+        g = oamg.mis2_greedy(W, keys)
+        p = _parallel_mis2(W, keys)
+        assert np.array_equal(g, p)
+        A = (W != 0).astype(int)
+        A2 = ((A + A @ A) > 0).astype(int).tolil()
+        A2.setdiag(0)
+        A2 = A2.tocsr()
+        r = np.nonzero(g)[0]
+        assert A2[r][:, r].nnz == 0                      # distance >= 3 apart
+        deg = np.diff(W.indptr)
+        cover = (A2 @ g.astype(int) > 0) | g
+        assert np.all(cover[deg > 0])                     # maximal
+
+
+def test_aggregates_and_tentative_prolongator():
+    P = fracgen.generate("planes64", N=6)
+    S = schur.s1(P)
+    W = oamg.strength_graph(S, 3, 0, AmgOptions())
+    root = oamg.mis2_greedy(W, oamg.priority_keys(W.shape[0], 0, 0))
+    agg, nc = oamg.aggregate(W, root)
+    deg = np.diff(W.indptr)
+    assert np.all(agg[deg > 0] >= 0) and np.all(agg[deg == 0] == -1)
+    assert nc == root.sum()
+    # every node is the root or a strong neighbour of a node assigned in round 1
+    Pt = oamg.tentative(agg, nc, 3)
+    assert np.allclose((Pt.T @ Pt).toarray(), np.eye(3 * nc), atol=1e-14)
+    ones = np.tile([1.0, 0.0, 0.0], nc)
+    v = Pt @ ones
+    has = np.repeat(agg >= 0, 3)
+    # piecewise constant per aggregate in the x component
+    vx = v[0::3]
+    for a in range(min(nc, 20)):
+        vals = vx[agg == a]
+        assert np.allclose(vals, vals[0])
+
+
+def test_chebyshev_error_polynomial_closed_form():
+    """Two Chebyshev steps on D^-1 S = diag(lam) from zero guess leave the
+    error e = T_2((theta - lam)/delta) / T_2(theta/delta) * e0."""
+    lam_true = np.linspace(0.05, 2.0, 30)
+    S = sp.diags(lam_true).tocsr()
+    a = AMG.__new__(AMG)
+    a.opt = AmgOptions()
+    L = oamg.Level(S=S, B=1, n=30, Dinv=np.ones((30, 1, 1)), lam=2.0)
+    f = np.random.default_rng(2).standard_normal(30)
+    x = a._cheb(L, f, None)
+    e0 = f / lam_true
+    e = e0 - x
+    hi = 1.1 * 2.0
+    lo = 0.1 * hi
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+    T2 = lambda z: 2 * z * z - 1
+    assert np.allclose(e, T2((theta - lam_true) / delta) / T2(theta / delta) * e0, rtol=1e-12, atol=1e-14)
+
+
+def test_vcycle_symmetric_for_symmetric_operator():
+    """With the same polynomial smoother before and after the correction and
+    R = P^T, the V-cycle is a symmetric operator when S is symmetric."""
+    P = fracgen.generate("planes64", N=8, p_stick=1.0, p_slip=0.0)
+    S = schur.s1(P)
+    amg = AMG(S, 3, AmgOptions(coarse_max=40))
+    assert len(amg.levels) >= 2
+    for L in amg.levels[1:]:
+        assert abs(L.S - L.S.T).max() <= 1e-10 * abs(L.S).max()
+    rs = np.random.default_rng(4)
+    x, y = rs.standard_normal(S.shape[0]), rs.standard_normal(S.shape[0])
+    assert np.isclose(x @ amg(y), y @ amg(x), rtol=1e-10)
+    # and it reduces the error of the pure elasticity operator
+    e = rs.standard_normal(S.shape[0])
+    for _ in range(5):
+        e = e - amg(S @ e)
+    e2 = e - amg(S @ e)
+    assert np.linalg.norm(e2) < 0.9 * np.linalg.norm(e)
