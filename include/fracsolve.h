@@ -1,0 +1,192 @@
+/*
+ * fracsolve: GB300 (sm_103a) solve phase of the stabilised 3x3 block
+ * Jacobian of frictional contact mechanics with fracture flow
+ * (A. Franceschini, L. Gazzola, M. Ferronato, "A scalable preconditioning
+ * framework for stabilized contact mechanics with hydraulically active
+ * fractures", arXiv 2112.12397).
+ *
+ *   J = [ A   C1  Q1 ]      unknowns  [u; t; p]           (Eq. JacSys)
+ *       [ C2  -H  0  ]      u: 3 per node copy, global frame
+ *       [ Q2  0   T  ]      t: 3 per fracture face, local frame (n, t1, t2)
+ *                           p: 1 per fracture face
+ *
+ * The library builds the preconditioners of Alg. 1 (t-p-u) and Alg. 3
+ * (t-u-p) on the GPU, applies them as in Alg. 2 and Alg. 4 with inner
+ * smoothed-aggregation AMG V-cycles, and solves J x = b by right-preconditioned
+ * flexible GMRES with classical Gram-Schmidt applied twice (Sec. 4: zero
+ * initial guess, stop on relative residual).
+ *
+ * Conventions for every entry point:
+ *  - Return value: an fc_status code (FC_OK on success).  Nothing throws or
+ *    aborts across this boundary.  fc_last_error() gives a message for the
+ *    most recent failure of a context.
+ *  - Pointers named d_* are DEVICE pointers on the context's device; pointers
+ *    named h_* are HOST pointers.  The caller owns every buffer it passes;
+ *    the library never frees or keeps caller memory after a call returns.
+ *  - Work is issued on the CUDA stream given to fc_create; calls that
+ *    return results to the host synchronise that stream.
+ *  - Vectors have length n = 3 n_node + 3 n_face + n_face in the order
+ *    [u; t; p] (u node-major x,y,z; t face-major N,T1,T2; p per face).
+ */
+#ifndef FRACSOLVE_H
+#define FRACSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FC_OK = 0,
+  FC_NOT_CONVERGED = 1,   /* maxit reached; iters and relres are filled */
+  FC_BREAKDOWN = 2,       /* Krylov breakdown before reaching tol */
+  FC_SINGULAR_BLOCK = 3,  /* a singular H~ block, AMG diagonal block or
+                             coarse matrix */
+  FC_NAN = 4,             /* NaN or Inf met in the input or an iterate */
+  FC_BAD_ARG = 5,         /* invalid sizes, pointers, variant or options */
+  FC_CUDA_ERROR = 6,      /* a CUDA runtime call failed */
+  FC_OOM = 7,             /* device allocation failed */
+  FC_INTERNAL = 8,        /* a capacity limit of a setup kernel was hit */
+  FC_NOT_SETUP = 9        /* fc_setup has not built what the call needs */
+} fc_status;
+
+/* Variants of the block preconditioner (Sec. 3). */
+enum { FC_TPU = 0, FC_TUP = 1 };
+
+/* Precision modes. FP64: everything in double.  MIXED: the AMG hierarchies,
+ * smoothers, H~^-1 and the coupling blocks used inside the preconditioner are
+ * stored and applied in float; the outer Krylov method (J z, Arnoldi,
+ * Givens, solution update, true residual) and the coarsest dense solve stay
+ * in double. */
+enum { FC_FP64 = 0, FC_MIXED = 1 };
+
+/* Block sparse row matrix (row-major dense blocks of br x bc), DEVICE
+ * pointers.  Columns must be sorted and unique within each block row.  Used
+ * for the seven blocks of Eq. block_def:
+ *   A  n_node x n_node 3x3;  C1 n_node x n_face 3x3;  Q1 n_node x n_face 3x1;
+ *   C2 n_face x n_node 3x3;  H  n_face x n_face 3x3;  Q2 n_face x n_node 1x3;
+ *   T  n_face x n_face 1x1. */
+typedef struct {
+  int32_t n_brows, n_bcols, br, bc;
+  int64_t nnzb;
+  const int32_t *d_row_ptr;   /* n_brows + 1 */
+  const int32_t *d_col_idx;   /* nnzb */
+  const double *d_val;        /* nnzb * br * bc */
+} fc_bsr;
+
+typedef struct {
+  fc_bsr A, C1, Q1, C2, H, Q2, T;
+  int32_t n_node, n_face;
+} fc_blocks;
+
+/* Solver options.  The AMG settings define the smoothed-aggregation
+ * hierarchy (strength threshold theta0 * theta_decay^level on block
+ * Frobenius norms, distance-2 maximal independent set roots with SplitMix64
+ * priorities drawn from amg_seed, one Jacobi smoothing step of the
+ * tentative prolongator with omega = omega_num / lambda, Galerkin coarse
+ * operators, dense coarsest solve) and its V(1,1)-cycle with a Chebyshev
+ * smoother of degree cheb_degree on [cheb_lo * cheb_hi * lambda,
+ * cheb_hi * lambda]. */
+typedef struct {
+  int32_t precision;        /* FC_FP64 or FC_MIXED */
+  int32_t variants;         /* bit FC_TPU and/or bit FC_TUP to build */
+  double theta0, theta_decay;
+  int32_t coarse_max;       /* block rows of the coarsest elasticity level */
+  int32_t coarse_max_p;     /* rows of the coarsest pressure level */
+  int32_t max_levels;
+  double max_ratio;         /* stop coarsening when n_c > max_ratio * n */
+  int32_t power_steps;
+  double omega_num;
+  int32_t cheb_degree;
+  double cheb_hi, cheb_lo;
+  uint64_t amg_seed;
+  int32_t max_restarts;     /* MIXED: true-residual restarts allowed */
+  int32_t verbose;
+} fc_options;
+
+typedef struct fc_ctx fc_ctx;
+
+/* Fill *opt with the defaults (FP64, both variants, theta0 0.08, decay 0.5,
+ * coarse_max 1000, coarse_max_p 1000, 12 levels, ratio 0.8, 15 power
+ * steps, omega_num 4/3, Chebyshev degree 2 on [0.11, 1.1] * lambda). */
+void fc_default_options(fc_options *opt);
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the new
+ * context; free it with fc_destroy. */
+int fc_create(fc_ctx **ctx, const fc_options *opt, void *cuda_stream);
+
+/* Alg. 1 (cpt_tpu) and/or Alg. 3 (cpt_tup): H~ = Bdiag(H,3) and its inverse,
+ * S1 = A + C1 H~^-1 C2 (Eq. Schur1_2), S~ = S1 - Q1 diag(T)^-1 Q2
+ * (Eq. appSchur_1), S~2 = T - FS(Q2, S1, Q1) (Eq. app_Schur2_2,
+ * Eq. FS_algebraic), and the AMG hierarchies of S~ and T (t-p-u) or S1 and
+ * S~2 (t-u-p).  The blocks are deep-copied: the caller may free them when
+ * this returns.  Calling it again replaces the operator.
+ * Errors: FC_BAD_ARG (inconsistent sizes), FC_SINGULAR_BLOCK, FC_OOM,
+ * FC_INTERNAL, FC_CUDA_ERROR. */
+int fc_setup(fc_ctx *ctx, const fc_blocks *J);
+
+/* d_y = J d_x (Eq. JacSys), double, device vectors of length n. */
+int fc_spmv(fc_ctx *ctx, const double *d_x, double *d_y);
+
+/* d_v = M^-1 d_w: app_tpu (Alg. 2) for FC_TPU, app_tup (Alg. 4) for FC_TUP,
+ * device vectors of length n. */
+int fc_apply_prec(fc_ctx *ctx, int variant, const double *d_w, double *d_v);
+
+/* Solve J x = b by right-preconditioned FGMRES-CGS2 with x0 = 0 (Sec. 4).
+ * Stops when the recurrence residual drops below tol * ||b||; returns the
+ * true relative residual ||b - J x|| / ||b|| in *relres and the number of
+ * preconditioner applications in *iters.  d_x is output only.
+ * maxit must lie in [1, 4000].  Returns FC_NOT_CONVERGED when maxit is reached
+ * (x, iters, relres filled).  In FC_MIXED mode the method restarts from the
+ * current x (at most max_restarts times) while the double-precision true
+ * residual is above tol. */
+int fc_solve(fc_ctx *ctx, int variant, const double *d_b, double *d_x, double tol,
+             int maxit, int *iters, double *relres);
+
+/* Same as fc_solve with HOST right-hand side and solution: copies h_b to the
+ * device, solves, copies the solution back to h_x.  Pinned host memory makes
+ * the copies asynchronous. */
+int fc_solve_host(fc_ctx *ctx, int variant, const double *h_b, double *h_x, double tol,
+                  int maxit, int *iters, double *relres);
+
+/* ---------------- inspection (used by the parity tests) ---------------- */
+
+/* Hierarchies: FC_H_TPU_U = AMG of S~, FC_H_TPU_P = AMG of T,
+ * FC_H_TUP_U = AMG of S1, FC_H_TUP_P = AMG of S~2. */
+enum { FC_H_TPU_U = 0, FC_H_TPU_P = 1, FC_H_TUP_U = 2, FC_H_TUP_P = 3 };
+/* Matrices: level operators of a hierarchy and the setup products. */
+enum { FC_M_LEVEL = 0, FC_M_PROLONG = 1, FC_M_S1 = 2, FC_M_STILDE = 3, FC_M_S2TILDE = 4 };
+
+/* Number of levels of hierarchy `hier` (0 if it was not built). */
+int fc_num_levels(fc_ctx *ctx, int hier, int *levels);
+
+/* Copy a matrix to HOST buffers.  kind FC_M_LEVEL / FC_M_PROLONG select the
+ * operator / prolongator of `level` of `hier` (in double, as built before any
+ * cast); FC_M_S1 / FC_M_STILDE / FC_M_S2TILDE ignore hier and level.  Pass
+ * NULL buffers to query the sizes only. */
+int fc_get_bsr(fc_ctx *ctx, int kind, int hier, int level, int32_t *n_brows,
+               int32_t *n_bcols, int32_t *br, int32_t *bc, int64_t *nnzb,
+               int32_t *h_row_ptr, int32_t *h_col_idx, double *h_val);
+
+/* Aggregate index of every block row of `level` (-1: no coarse unknown) and
+ * the power-iteration estimate lambda of D^-1 S on that level, to HOST. */
+int fc_get_aggregates(fc_ctx *ctx, int hier, int level, int32_t *h_agg, double *h_lambda);
+
+/* One V-cycle of hierarchy `hier` applied to the device vector d_f (length =
+ * scalar rows of level 0), result in d_x. */
+int fc_vcycle(fc_ctx *ctx, int hier, const double *d_f, double *d_x);
+
+/* The fixed-stress diagonal [S_K]_k of Eq. FS_algebraic to HOST (n_face). */
+int fc_get_fixed_stress(fc_ctx *ctx, double *h_sk);
+
+void fc_destroy(fc_ctx *ctx);
+const char *fc_strerror(int status);
+const char *fc_last_error(fc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,238 @@
+"""Python binding of libfracsolve (include/fracsolve.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library; this module converts torch
+tensors and numpy arrays to the plain pointers and sizes of the C-ABI and
+raises on non-zero status codes.  It fails loudly when the library or a CUDA
+device is missing: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libfracsolve.so")
+
+FC_OK, FC_NOT_CONVERGED, FC_BREAKDOWN, FC_SINGULAR_BLOCK, FC_NAN, FC_BAD_ARG, \
+    FC_CUDA_ERROR, FC_OOM, FC_INTERNAL, FC_NOT_SETUP = range(10)
+FC_TPU, FC_TUP = 0, 1
+FC_FP64, FC_MIXED = 0, 1
+FC_H_TPU_U, FC_H_TPU_P, FC_H_TUP_U, FC_H_TUP_P = range(4)
+FC_M_LEVEL, FC_M_PROLONG, FC_M_S1, FC_M_STILDE, FC_M_S2TILDE = range(5)
+VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP}
+
+# exported symbols declared by include/fracsolve.h
+SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_apply_prec", "fc_solve",
+           "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
+           "fc_get_fixed_stress", "fc_destroy", "fc_strerror", "fc_last_error"]
+
+
+class FcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fracsolve status {code}: {msg}")
+        self.code = code
+
+
+class fc_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("variants", C.c_int32), ("theta0", C.c_double),
+                ("theta_decay", C.c_double), ("coarse_max", C.c_int32), ("coarse_max_p", C.c_int32),
+                ("max_levels", C.c_int32), ("max_ratio", C.c_double), ("power_steps", C.c_int32),
+                ("omega_num", C.c_double), ("cheb_degree", C.c_int32), ("cheb_hi", C.c_double),
+                ("cheb_lo", C.c_double), ("amg_seed", C.c_uint64), ("max_restarts", C.c_int32),
+                ("verbose", C.c_int32)]
+
+
+class fc_bsr(C.Structure):
+    _fields_ = [("n_brows", C.c_int32), ("n_bcols", C.c_int32), ("br", C.c_int32), ("bc", C.c_int32),
+                ("nnzb", C.c_int64), ("d_row_ptr", C.c_void_p), ("d_col_idx", C.c_void_p),
+                ("d_val", C.c_void_p)]
+
+
+class fc_blocks(C.Structure):
+    _fields_ = [("A", fc_bsr), ("C1", fc_bsr), ("Q1", fc_bsr), ("C2", fc_bsr), ("H", fc_bsr),
+                ("Q2", fc_bsr), ("T", fc_bsr), ("n_node", C.c_int32), ("n_face", C.c_int32)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False):
+    """Load the shared library (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if build_if_missing:
+            from . import build as _b
+            _b.build()
+        else:
+            raise FileNotFoundError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    pi32, pi64, pd, pint = C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int)
+    sig = {
+        "fc_default_options": (None, [C.POINTER(fc_options)]),
+        "fc_create": (C.c_int, [C.POINTER(vp), C.POINTER(fc_options), vp]),
+        "fc_setup": (C.c_int, [vp, C.POINTER(fc_blocks)]),
+        "fc_spmv": (C.c_int, [vp, vp, vp]),
+        "fc_apply_prec": (C.c_int, [vp, C.c_int, vp, vp]),
+        "fc_solve": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
+        "fc_solve_host": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
+        "fc_num_levels": (C.c_int, [vp, C.c_int, pint]),
+        "fc_get_bsr": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, pi32, pi32, pi32, pi32, pi64, vp, vp, vp]),
+        "fc_get_aggregates": (C.c_int, [vp, C.c_int, C.c_int, vp, pd]),
+        "fc_vcycle": (C.c_int, [vp, C.c_int, vp, vp]),
+        "fc_get_fixed_stress": (C.c_int, [vp, vp]),
+        "fc_destroy": (None, [vp]),
+        "fc_strerror": (C.c_char_p, [C.c_int]),
+        "fc_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options(**over) -> fc_options:
+    o = fc_options()
+    load().fc_default_options(C.byref(o))
+    for k, v in over.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FC_FP64, "mixed": FC_MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class Context:
+    """One fc_ctx bound to the current CUDA device and a CUDA stream."""
+
+    def __init__(self, options: fc_options | None = None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("fracsolve needs a CUDA device; no CPU path exists")
+        self.lib = load()
+        self.opt = options or default_options()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        self._check(self.lib.fc_create(C.byref(h), C.byref(self.opt), C.c_void_p(self.stream.cuda_stream)), None)
+        self.h = h
+        self._keep = None
+        self.n = 0
+
+    def _check(self, rc, h, ok=(FC_OK,)):
+        if rc not in ok:
+            msg = self.lib.fc_last_error(h).decode() if h else ""
+            raise FcError(rc, (self.lib.fc_strerror(rc).decode() + (": " + msg if msg else "")))
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ setup
+    def setup(self, blocks: dict, n_node: int, n_face: int):
+        """blocks: name -> (row_ptr, col_idx, val, n_brows, n_bcols, br, bc) with
+        int32/int32/float64 CUDA tensors."""
+        J = fc_blocks()
+        for name in ("A", "C1", "Q1", "C2", "H", "Q2", "T"):
+            rp, ci, val, nbr, nbc, br, bc = blocks[name]
+            m = getattr(J, name)
+            m.n_brows, m.n_bcols, m.br, m.bc = nbr, nbc, br, bc
+            m.nnzb = int(ci.numel())
+            m.d_row_ptr, m.d_col_idx, m.d_val = _ptr(rp), _ptr(ci), _ptr(val)
+        J.n_node, J.n_face = n_node, n_face
+        self._check(self.lib.fc_setup(self.h, C.byref(J)), self.h)
+        self.n = 3 * n_node + 4 * n_face
+        self.n_node, self.n_face = n_node, n_face
+
+    # ------------------------------------------------------------ apply
+    def spmv(self, x, y):
+        self._check(self.lib.fc_spmv(self.h, _ptr(x), _ptr(y)), self.h)
+
+    def apply_prec(self, variant: str, w, v):
+        self._check(self.lib.fc_apply_prec(self.h, VARIANTS[variant], _ptr(w), _ptr(v)), self.h)
+
+    def solve(self, variant: str, b, x, tol: float = 1e-8, maxit: int = 500, allow_fail: bool = False):
+        it, rr = C.c_int(0), C.c_double(0)
+        ok = (FC_OK, FC_NOT_CONVERGED, FC_BREAKDOWN) if allow_fail else (FC_OK,)
+        rc = self._check(self.lib.fc_solve(self.h, VARIANTS[variant], _ptr(b), _ptr(x), tol, maxit,
+                                           C.byref(it), C.byref(rr)), self.h, ok)
+        return rc, it.value, rr.value
+
+    def solve_host(self, variant: str, b: np.ndarray, x: np.ndarray, tol: float = 1e-8, maxit: int = 500,
+                   allow_fail: bool = False):
+        it, rr = C.c_int(0), C.c_double(0)
+        ok = (FC_OK, FC_NOT_CONVERGED, FC_BREAKDOWN) if allow_fail else (FC_OK,)
+        bp = b.ctypes.data if isinstance(b, np.ndarray) else b.data_ptr()
+        xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+        rc = self._check(self.lib.fc_solve_host(self.h, VARIANTS[variant], C.c_void_p(bp), C.c_void_p(xp), tol,
+                                                maxit, C.byref(it), C.byref(rr)), self.h, ok)
+        return rc, it.value, rr.value
+
+    # ------------------------------------------------------------ inspection
+    def num_levels(self, hier: int) -> int:
+        n = C.c_int(0)
+        self._check(self.lib.fc_num_levels(self.h, hier, C.byref(n)), self.h)
+        return n.value
+
+    def get_bsr(self, kind: int, hier: int = 0, level: int = 0):
+        nbr, nbc, br, bc = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        nnz = C.c_int64()
+        self._check(self.lib.fc_get_bsr(self.h, kind, hier, level, C.byref(nbr), C.byref(nbc), C.byref(br),
+                                        C.byref(bc), C.byref(nnz), None, None, None), self.h)
+        rp = np.zeros(nbr.value + 1, np.int32)
+        ci = np.zeros(nnz.value, np.int32)
+        val = np.zeros(nnz.value * br.value * bc.value, np.float64)
+        self._check(self.lib.fc_get_bsr(self.h, kind, hier, level, None, None, None, None, None,
+                                        C.c_void_p(rp.ctypes.data), C.c_void_p(ci.ctypes.data),
+                                        C.c_void_p(val.ctypes.data)), self.h)
+        return rp, ci, val.reshape(nnz.value, br.value, bc.value), (nbr.value, nbc.value, br.value, bc.value)
+
+    def get_aggregates(self, hier: int, level: int, nb: int):
+        agg = np.zeros(max(nb, 1), np.int32)
+        lam = C.c_double(0)
+        self._check(self.lib.fc_get_aggregates(self.h, hier, level, C.c_void_p(agg.ctypes.data), C.byref(lam)),
+                    self.h)
+        return agg[:nb], lam.value
+
+    def vcycle(self, hier: int, f, x):
+        self._check(self.lib.fc_vcycle(self.h, hier, _ptr(f), _ptr(x)), self.h)
+
+    def fixed_stress(self) -> np.ndarray:
+        out = np.zeros(max(self.n_face, 1))
+        self._check(self.lib.fc_get_fixed_stress(self.h, C.c_void_p(out.ctypes.data)), self.h)
+        return out[:self.n_face]
+
+
+def device_blocks(problem, device="cuda"):
+    """Marshal a generated problem's numpy BSR blocks into CUDA tensors in the
+    layout fc_setup expects."""
+    import torch
+    out = {}
+    for name, B in problem.blocks().items():
+        out[name] = (torch.from_numpy(B.row_ptr).to(device), torch.from_numpy(B.col_idx).to(device),
+                     torch.from_numpy(np.ascontiguousarray(B.val).reshape(-1)).to(device),
+                     B.n_brows, B.n_bcols, B.br, B.bc)
+    return out
+
+
+def context_for(problem, options: fc_options | None = None, stream=None) -> Context:
+    ctx = Context(options, stream)
+    blocks = device_blocks(problem)
+    ctx.setup(blocks, problem.n_node, problem.n_face)
+    return ctx

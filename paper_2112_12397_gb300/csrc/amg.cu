@@ -1,0 +1,773 @@
+// Smoothed-aggregation AMG on the device.
+//
+// Setup (double precision), for each level l with block size B:
+//   1. D = B x B diagonal blocks of S, D^-1, d_i = ||S_ii||_F
+//   2. strong directed entries: ||S_ij||_F^2 > theta_l^2 d_i d_j, weight
+//      w_ij = ||S_ij||_F^2 / (d_i d_j); the undirected graph is the union of
+//      the strong pattern and its transpose with the larger weight
+//   3. roots: distance-2 maximal independent set, fixed SplitMix64 keys; a
+//      node joins when its key is the largest among undecided nodes within
+//      distance 2, which reproduces the greedy set in descending key order
+//   4. aggregates: strongest root neighbour, then strongest round-1
+//      neighbour, leftovers seed singletons; numbered by seed index
+//   5. lambda from 15 normalised power steps of D^-1 S
+//   6. P = (I - omega D^-1 S) P_tent with P_tent(i, agg i) = I / sqrt(|agg|)
+//   7. R = P^T, S_c = R (S P) by the block SpGEMM
+// The coarsest operator is inverted explicitly (Gauss-Jordan, partial
+// pivoting) in double.
+//
+// Cycle (float or double): V(1,1), zero initial guess on every level,
+// Chebyshev smoother on [cheb_lo * cheb_hi * lambda, cheb_hi * lambda]
+// (Saad, Alg. 12.1) fused with the residual in one pass over S.
+#include <cmath>
+#include <type_traits>
+
+#include "amg.cuh"
+#include "sparse.cuh"
+#include "spmv.cuh"
+
+namespace fs {
+
+namespace {
+
+constexpr int kT = 256;
+inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
+
+__device__ inline double frob2(const double *v, int bs) {
+  double s = 0.0;
+  for (int k = 0; k < bs; k++) s = __dadd_rn(s, __dmul_rn(v[k], v[k]));
+  return s;
+}
+
+// ------------------------------------------------------------ 1. diagonal
+template <int B>
+__global__ void k_diag(BsrView<double> S, double *Dinv, double *dn, int *flag) {
+  constexpr int BS = B * B;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.nbr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int s = S.rp[i], len = S.rp[i + 1] - s;
+    int p = find_sorted(S.ci + s, len, (int)i);
+    double a[BS];
+    for (int k = 0; k < BS; k++) a[k] = p >= 0 ? S.val[(int64_t)(s + p) * BS + k] : 0.0;
+    dn[i] = sqrt(frob2(a, BS));
+    double *o = Dinv + i * BS;
+    if (B == 1) {
+      if (!(a[0] != 0.0) || !isfinite(a[0])) { atomicExch(flag, 1); o[0] = 0.0; }
+      else o[0] = 1.0 / a[0];
+    } else {
+      double c00 = a[4] * a[8] - a[5] * a[7];
+      double c01 = a[5] * a[6] - a[3] * a[8];
+      double c02 = a[3] * a[7] - a[4] * a[6];
+      double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+      double sc = 0.0;
+      for (int k = 0; k < 9; k++) sc = fmax(sc, fabs(a[k]));
+      if (!(fabs(det) > 1e-14 * sc * sc * sc) || !isfinite(det)) {
+        atomicExch(flag, 1);
+        for (int k = 0; k < 9; k++) o[k] = 0.0;
+        continue;
+      }
+      double id = 1.0 / det;
+      o[0] = c00 * id;
+      o[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+      o[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+      o[3] = c01 * id;
+      o[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+      o[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+      o[6] = c02 * id;
+      o[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+      o[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+    }
+  }
+}
+
+// ------------------------------------------------------------ 2. strength
+// pass 0: count strong entries per row; pass 1: write (col, weight)
+__global__ void k_strength(BsrView<double> S, const double *dn, double theta2, int pass, int *cnt,
+                           const int *rpG, int *ciG, double *wG) {
+  const int bs = S.br * S.bc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.nbr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    int o = pass ? rpG[i] : 0;
+    const double di = dn[i];
+    for (int e = S.rp[i]; e < S.rp[i + 1]; e++) {
+      int j = S.ci[e];
+      if (j == i) continue;
+      double s = frob2(S.val + (int64_t)e * bs, bs);
+      double dd = __dmul_rn(di, dn[j]);
+      if (s > __dmul_rn(theta2, dd)) {
+        if (pass) {
+          ciG[o + n] = j;
+          wG[o + n] = __ddiv_rn(s, dd);
+        }
+        n++;
+      }
+    }
+    if (!pass) cnt[i] = n;
+  }
+}
+
+// union of two sorted weighted patterns, weight = max; pass 0 counts
+__global__ void k_union_max(int nr, const int *rpA, const int *ciA, const double *wA, const int *rpB,
+                            const int *ciB, const double *wB, int pass, int *cnt, const int *rpC,
+                            int *ciC, double *wC) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int a = rpA[i], ae = rpA[i + 1], b = rpB[i], be = rpB[i + 1];
+    int n = 0, o = pass ? rpC[i] : 0;
+    while (a < ae || b < be) {
+      int ca = a < ae ? ciA[a] : INT32_MAX;
+      int cb = b < be ? ciB[b] : INT32_MAX;
+      int c = ca < cb ? ca : cb;
+      double w = 0.0;
+      if (ca == c) { w = fmax(w, wA[a]); a++; }
+      if (cb == c) { w = fmax(w, wB[b]); b++; }
+      if (pass) { ciC[o + n] = c; wC[o + n] = w; }
+      n++;
+    }
+    if (!pass) cnt[i] = n;
+  }
+}
+
+// ------------------------------------------------------------ 3. MIS-2
+enum : int8_t { ST_UND = 0, ST_ROOT = 1, ST_OUT = 2, ST_NONE = 3 };
+
+__global__ void k_mis_init(int n, const int *rp, uint64_t seed, int level, uint64_t *key, int8_t *st) {
+  const uint64_t mask = (1ull << 26) - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t r = sm64_draw(seed, 10, ((uint64_t)level << 32) + (uint64_t)i);
+    key[i] = (r & ~mask) | (uint64_t)i;
+    st[i] = (rp[i + 1] > rp[i]) ? ST_UND : ST_NONE;
+  }
+}
+
+// m[v] = 1 + max key over undecided nodes of the closed neighbourhood (0: none)
+__global__ void k_mis_max1(int n, const int *rp, const int *ci, const uint64_t *key, const int8_t *st,
+                           uint64_t *m) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t best = st[v] == ST_UND ? key[v] + 1 : 0;
+    for (int e = rp[v]; e < rp[v + 1]; e++) {
+      int u = ci[e];
+      if (st[u] == ST_UND && key[u] + 1 > best) best = key[u] + 1;
+    }
+    m[v] = best;
+  }
+}
+
+__global__ void k_mis_max2_select(int n, const int *rp, const int *ci, const uint64_t *key, const uint64_t *m1,
+                                  int8_t *st, int8_t *newroot) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    newroot[v] = 0;
+    if (st[v] != ST_UND) continue;
+    uint64_t best = m1[v];
+    for (int e = rp[v]; e < rp[v + 1]; e++) best = m1[ci[e]] > best ? m1[ci[e]] : best;
+    if (best == key[v] + 1) newroot[v] = 1;
+  }
+}
+
+__global__ void k_mis_mark_near(int n, const int *rp, const int *ci, const int8_t *newroot, int8_t *near) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int8_t x = newroot[v];
+    for (int e = rp[v]; e < rp[v + 1] && !x; e++) x = newroot[ci[e]];
+    near[v] = x;
+  }
+}
+
+__global__ void k_mis_update(int n, const int *rp, const int *ci, const int8_t *newroot, const int8_t *near,
+                             int8_t *st, int *undecided) {
+  int local = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (st[v] != ST_UND) continue;
+    if (newroot[v]) { st[v] = ST_ROOT; continue; }
+    int8_t x = near[v];
+    for (int e = rp[v]; e < rp[v + 1] && !x; e++) x = near[ci[e]];
+    if (x) st[v] = ST_OUT;
+    else local++;
+  }
+  if (local) atomicAdd(undecided, local);
+}
+
+// ------------------------------------------------------------ 4. aggregates
+// round 1: owner = strongest root neighbour (ties: lower index); roots own themselves
+__global__ void k_agg_round1(int n, const int *rp, const int *ci, const double *w, const int8_t *st, int *owner) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (st[v] == ST_ROOT) { owner[v] = (int)v; continue; }
+    int best = -1;
+    double bw = -1.0;
+    for (int e = rp[v]; e < rp[v + 1]; e++) {
+      int u = ci[e];
+      if (st[u] != ST_ROOT) continue;
+      if (w[e] > bw || (w[e] == bw && u < best)) { bw = w[e]; best = u; }
+    }
+    owner[v] = best;
+  }
+}
+
+// round 2: unassigned nodes join the owner of their strongest assigned neighbour
+__global__ void k_agg_round2(int n, const int *rp, const int *ci, const double *w, const int *owner1,
+                             int *owner2, int8_t *seed) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int o = owner1[v];
+    seed[v] = (o == (int)v) ? 1 : 0;
+    if (o >= 0 || rp[v + 1] == rp[v]) { owner2[v] = o; continue; }
+    int best = -1;
+    double bw = -1.0;
+    for (int e = rp[v]; e < rp[v + 1]; e++) {
+      int u = ci[e];
+      if (owner1[u] < 0) continue;
+      if (w[e] > bw || (w[e] == bw && u < best)) { bw = w[e]; best = u; }
+    }
+    if (best >= 0) owner2[v] = owner1[best];
+    else { owner2[v] = (int)v; seed[v] = 1; }   // leftover seeds a singleton
+  }
+}
+
+__global__ void k_seed_flags_to_int(int n, const int8_t *seed, int *out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    out[v] = seed[v];
+}
+
+__global__ void k_agg_number(int n, const int *owner, const int *seedidx, int *agg, int *size) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int o = owner[v];
+    int a = o >= 0 ? seedidx[o] : -1;
+    agg[v] = a;
+    if (a >= 0) atomicAdd(size + a, 1);
+  }
+}
+
+// ------------------------------------------------------------ 5. power
+__global__ void k_power_start(int64_t n, uint64_t seed, int level, double *v) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    v[k] = 2.0 * sm64_uniform(seed, 11, ((uint64_t)level << 32) + (uint64_t)k) - 1.0;
+}
+
+// ------------------------------------------------------------ 6. prolongator
+constexpr int kMaxCand = 512;
+
+// sorted unique aggregates reached by row i of S; returns count or -1
+__device__ inline int row_candidates(const BsrView<double> &S, int64_t i, const int *agg, int *c) {
+  int n = 0;
+  for (int e = S.rp[i]; e < S.rp[i + 1]; e++) {
+    int a = agg[S.ci[e]];
+    if (a < 0) continue;
+    int pos = n;
+    bool dup = false;
+    for (int k = 0; k < n; k++) {
+      if (c[k] == a) { dup = true; break; }
+    }
+    if (dup) continue;
+    if (n >= kMaxCand) return -1;
+    while (pos > 0 && c[pos - 1] > a) { c[pos] = c[pos - 1]; pos--; }
+    c[pos] = a;
+    n++;
+  }
+  return n;
+}
+
+template <int B>
+__global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, const double *Dinv,
+                          double omega, int pass, int *cnt, const int *rpP, int *ciP, double *valP,
+                          int *flag) {
+  constexpr int BS = B * B;
+  int c[kMaxCand];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.nbr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int n = row_candidates(S, i, agg, c);
+    if (n < 0) { atomicExch(flag, 1); if (!pass) cnt[i] = 0; continue; }
+    if (!pass) { cnt[i] = n; continue; }
+    int o = rpP[i];
+    const double *Di = Dinv + i * BS;
+    for (int k = 0; k < n; k++) {
+      int a = c[k];
+      double acc[BS];
+      for (int q = 0; q < BS; q++) acc[q] = 0.0;
+      for (int e = S.rp[i]; e < S.rp[i + 1]; e++) {
+        if (agg[S.ci[e]] != a) continue;
+        const double *v = S.val + (int64_t)e * BS;
+        for (int q = 0; q < BS; q++) acc[q] += v[q];
+      }
+      double isz = 1.0 / sqrt((double)asize[a]);
+      double *out = valP + (int64_t)(o + k) * BS;
+      for (int r = 0; r < B; r++)
+        for (int cc = 0; cc < B; cc++) {
+          double m = 0.0;
+          for (int t = 0; t < B; t++) m += Di[r * B + t] * (acc[t * B + cc] * isz);
+          double pt = (agg[i] == a && r == cc) ? isz : 0.0;
+          out[r * B + cc] = pt - omega * m;
+        }
+      ciP[o + k] = a;
+    }
+  }
+}
+
+// ------------------------------------------------------------ 7. coarsest
+__global__ void k_bsr_to_dense(BsrView<double> S, double *Dn) {
+  const int B = S.br, n = S.nbr * B;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.nbr;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int e = S.rp[i]; e < S.rp[i + 1]; e++) {
+      int j = S.ci[e];
+      for (int r = 0; r < B; r++)
+        for (int c = 0; c < B; c++)
+          Dn[(i * B + r) * (int64_t)n + j * B + c] = S.val[(int64_t)e * B * B + r * B + c];
+    }
+}
+
+// Gauss-Jordan step k, part 1 (one block): partial pivoting (lowest index on
+// ties), row swap, scaling of the pivot row, copy of column k
+__global__ void k_gj_pivot(double *M, int n, int k, int *perm, double *colk, int *flag) {
+  __shared__ double sv[1024];
+  __shared__ int si[1024];
+  double best = -1.0;
+  int bi = n;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    double v = fabs(M[(int64_t)i * n + k]);
+    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      double v = sv[threadIdx.x + o];
+      int ii = si[threadIdx.x + o];
+      if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ii < si[threadIdx.x])) {
+        sv[threadIdx.x] = v;
+        si[threadIdx.x] = ii;
+      }
+    }
+    __syncthreads();
+  }
+  const int p = si[0];
+  if (threadIdx.x == 0) {
+    perm[k] = p;
+    if (!(sv[0] > 0.0)) atomicExch(flag, 1);
+  }
+  if (p != k && p < n)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double t = M[(int64_t)k * n + j];
+      M[(int64_t)k * n + j] = M[(int64_t)p * n + j];
+      M[(int64_t)p * n + j] = t;
+    }
+  __syncthreads();
+  double piv = M[(int64_t)k * n + k];
+  double ip = piv != 0.0 ? 1.0 / piv : 0.0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double v = (j == k) ? ip : M[(int64_t)k * n + j] * ip;
+    M[(int64_t)k * n + j] = v;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = (i == k) ? 0.0 : M[(int64_t)i * n + k];
+}
+
+// part 2: a_ij -= a_ik a_kj for i != k (column k becomes -a_ik / piv)
+__global__ void k_gj_elim(double *M, int n, int k, const double *colk) {
+  int64_t total = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t / n), j = (int)(t - (int64_t)i * n);
+    if (i == k) continue;
+    double f = colk[i];
+    double base = (j == k) ? 0.0 : M[t];
+    M[t] = base - f * M[(int64_t)k * n + j];
+  }
+}
+
+__global__ void k_gj_unpermute(double *M, int n, const int *perm) {
+  // undo the row interchanges by swapping columns in reverse order
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double *row = M + (int64_t)i * n;
+    for (int k = n - 1; k >= 0; k--) {
+      int p = perm[k];
+      if (p != k) {
+        double t = row[k];
+        row[k] = row[p];
+        row[p] = t;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ cycle kernels
+template <int B, typename TP>
+__global__ void k_cheb_zero(int64_t nb, const TP *f, const TP *Dinv, TP cr, TP *d, TP *x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    TP fi[B];
+#pragma unroll
+    for (int q = 0; q < B; q++) fi[q] = f[i * B + q];
+    const TP *D = Dinv + i * B * B;
+#pragma unroll
+    for (int a = 0; a < B; a++) {
+      TP s = 0;
+#pragma unroll
+      for (int b = 0; b < B; b++) s += D[a * B + b] * fi[b];
+      TP v = cr * s;
+      d[i * B + a] = v;
+      x[i * B + a] = v;
+    }
+  }
+}
+
+// x = Cinv f in double, one warp per row
+template <typename TP>
+__global__ void k_dense_gemv(int n, const double *__restrict__ M, const TP *__restrict__ f, TP *x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += M[i * n + j] * (double)f[j];
+    s = warp_sum(s);
+    if (lane == 0) x[i] = (TP)s;
+  }
+}
+
+}  // namespace
+
+// ============================================================ setup driver
+namespace {
+
+struct Graph {
+  DBuf<int> rp, ci;
+  DBuf<double> w;
+  int n = 0;
+  int64_t nnz = 0;
+};
+
+Graph strength_graph(const BsrView<double> &S, const double *dn, double theta, cudaStream_t s) {
+  const int n = S.nbr;
+  Graph Gd;
+  Gd.n = n;
+  Gd.rp.alloc(n + 1);
+  DBuf<int> cnt(n + 1);
+  const double th2 = theta * theta;
+  k_strength<<<grid_rows(n), kT, 0, s>>>(S, dn, th2, 0, cnt.p, nullptr, nullptr, nullptr);
+  FS_LAUNCHED();
+  Gd.nnz = exclusive_scan(cnt.p, Gd.rp.p, n, s);
+  Gd.ci.alloc(Gd.nnz);
+  Gd.w.alloc(Gd.nnz);
+  if (Gd.nnz) {
+    k_strength<<<grid_rows(n), kT, 0, s>>>(S, dn, th2, 1, nullptr, Gd.rp.p, Gd.ci.p, Gd.w.p);
+    FS_LAUNCHED();
+  }
+  // transpose of the directed strong pattern (weights as 1x1 blocks)
+  BsrView<double> gv;
+  gv.nbr = n; gv.nbc = n; gv.br = 1; gv.bc = 1; gv.nnzb = Gd.nnz;
+  gv.rp = Gd.rp.p; gv.ci = Gd.ci.p; gv.val = Gd.w.p;
+  Bsr<double> Gt = transpose(gv, s);
+  Graph G;
+  G.n = n;
+  G.rp.alloc(n + 1);
+  k_union_max<<<grid_rows(n), kT, 0, s>>>(n, Gd.rp.p, Gd.ci.p, Gd.w.p, Gt.rp.p, Gt.ci.p, Gt.val.p, 0,
+                                          cnt.p, nullptr, nullptr, nullptr);
+  FS_LAUNCHED();
+  G.nnz = exclusive_scan(cnt.p, G.rp.p, n, s);
+  G.ci.alloc(G.nnz);
+  G.w.alloc(G.nnz);
+  if (G.nnz) {
+    k_union_max<<<grid_rows(n), kT, 0, s>>>(n, Gd.rp.p, Gd.ci.p, Gd.w.p, Gt.rp.p, Gt.ci.p, Gt.val.p,
+                                            1, nullptr, G.rp.p, G.ci.p, G.w.p);
+    FS_LAUNCHED();
+  }
+  return G;
+}
+
+// returns the number of aggregates; agg filled (-1 = none), asize filled
+int aggregate(const Graph &G, uint64_t seed, int level, DBuf<int> &agg, DBuf<int> &asize, int verbose,
+              cudaStream_t s) {
+  const int n = G.n;
+  FS_REQUIRE(n < (1 << 26) - 1, FC_BAD_ARG, "AMG level too large for 26-bit node keys");
+  DBuf<uint64_t> key(n), m1(n);
+  DBuf<int8_t> st(n), newroot(n), nearf(n);
+  DBuf<int> und(1);
+  k_mis_init<<<grid_rows(n), kT, 0, s>>>(n, G.rp.p, seed, level, key.p, st.p);
+  FS_LAUNCHED();
+  int rounds = 0;
+  for (;;) {
+    FS_CUDA(cudaMemsetAsync(und.p, 0, sizeof(int), s));
+    k_mis_max1<<<grid_rows(n), kT, 0, s>>>(n, G.rp.p, G.ci.p, key.p, st.p, m1.p);
+    FS_LAUNCHED();
+    k_mis_max2_select<<<grid_rows(n), kT, 0, s>>>(n, G.rp.p, G.ci.p, key.p, m1.p, st.p, newroot.p);
+    FS_LAUNCHED();
+    k_mis_mark_near<<<grid_rows(n), kT, 0, s>>>(n, G.rp.p, G.ci.p, newroot.p, nearf.p);
+    FS_LAUNCHED();
+    k_mis_update<<<grid_rows(n), kT, 0, s>>>(n, G.rp.p, G.ci.p, newroot.p, nearf.p, st.p, und.p);
+    FS_LAUNCHED();
+    int h = 0;
+    FS_CUDA(cudaMemcpyAsync(&h, und.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+    rounds++;
+    if (h == 0) break;
+    FS_REQUIRE(rounds < 10000, FC_INTERNAL, "MIS-2 did not terminate");
+  }
+  DBuf<int> owner1(n), owner2(n), seedi(n), seedidx(n + 1);
+  DBuf<int8_t> seedf(n);
+  k_agg_round1<<<grid_rows(n), kT, 0, s>>>(n, G.rp.p, G.ci.p, G.w.p, st.p, owner1.p);
+  FS_LAUNCHED();
+  k_agg_round2<<<grid_rows(n), kT, 0, s>>>(n, G.rp.p, G.ci.p, G.w.p, owner1.p, owner2.p, seedf.p);
+  FS_LAUNCHED();
+  k_seed_flags_to_int<<<grid_rows(n), kT, 0, s>>>(n, seedf.p, seedi.p);
+  FS_LAUNCHED();
+  int nc = (int)exclusive_scan(seedi.p, seedidx.p, n, s);
+  agg.alloc(n);
+  asize.alloc(nc > 0 ? nc : 1);
+  FS_CUDA(cudaMemsetAsync(asize.p, 0, sizeof(int) * (nc > 0 ? nc : 1), s));
+  k_agg_number<<<grid_rows(n), kT, 0, s>>>(n, owner2.p, seedidx.p, agg.p, asize.p);
+  FS_LAUNCHED();
+  if (verbose) fprintf(stderr, "[fracsolve] level %d: %d nodes, %d aggregates, %d MIS rounds\n", level, n, nc, rounds);
+  return nc;
+}
+
+template <int B>
+double power_lambda(const BsrView<double> &S, const double *Dinv, uint64_t seed, int level, int steps,
+                    cudaStream_t s) {
+  const int64_t n = (int64_t)S.nbr * B;
+  DBuf<double> v(n), w(n), tmp(kRedBlocks + 1);
+  k_power_start<<<grid_rows(n), kT, 0, s>>>(n, seed, level, v.p);
+  FS_LAUNCHED();
+  double lam = 0.0;
+  for (int it = 0; it < steps; it++) {
+    EpiBlockDiag<B, double> e{w.p, Dinv};
+    spmv<B, B>(S, v.p, e, s);
+    double ww = dot(w.p, w.p, n, s, tmp.p);
+    double vv = dot(v.p, v.p, n, s, tmp.p);
+    double nw = std::sqrt(ww);
+    FS_REQUIRE(std::isfinite(nw) && nw > 0, FC_NAN, "power iteration broke down");
+    lam = nw / std::sqrt(vv);
+    scale_to(v.p, w.p, 1.0 / nw, n, s);
+  }
+  return lam;
+}
+
+template <int B>
+void build_prolongator(LevelSetup &L, const DBuf<int> &asize, int nc, double omega, cudaStream_t s) {
+  const BsrView<double> S = L.S.view();
+  Bsr<double> &P = L.P;
+  P.shape(L.nb, nc, B, B);
+  P.rp.alloc(L.nb + 1);
+  DBuf<int> cnt(L.nb + 1), flag(1);
+  FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+  k_prolong<B><<<grid_rows(L.nb), 128, 0, s>>>(S, L.agg.p, asize.p, L.Dinv.p, omega, 0, cnt.p, nullptr,
+                                               nullptr, nullptr, flag.p);
+  FS_LAUNCHED();
+  P.nnzb = exclusive_scan(cnt.p, P.rp.p, L.nb, s);
+  P.ci.alloc(P.nnzb);
+  P.val.alloc(P.nnzb * B * B);
+  if (P.nnzb)
+    k_prolong<B><<<grid_rows(L.nb), 128, 0, s>>>(S, L.agg.p, asize.p, L.Dinv.p, omega, 1, nullptr, P.rp.p,
+                                                 P.ci.p, P.val.p, flag.p);
+  FS_LAUNCHED();
+  int h = 0;
+  FS_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  FS_REQUIRE(!h, FC_INTERNAL, "prolongator row reaches more than 512 aggregates");
+}
+
+void invert_coarsest(Hierarchy &H, cudaStream_t s) {
+  LevelSetup &L = H.lev.back();
+  const int n = L.nb * L.B;
+  H.nc_scalar = n;
+  H.cinv.alloc((size_t)n * n > 0 ? (size_t)n * n : 1);
+  if (n == 0) return;
+  FS_CUDA(cudaMemsetAsync(H.cinv.p, 0, sizeof(double) * (size_t)n * n, s));
+  k_bsr_to_dense<<<grid_rows(L.nb), kT, 0, s>>>(L.S.view(), H.cinv.p);
+  FS_LAUNCHED();
+  DBuf<int> perm(n), flag(1);
+  DBuf<double> colk(n);
+  FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+  const int eg = blocks_for((int64_t)n * n, 256, kSMs * 8);
+  for (int k = 0; k < n; k++) {
+    k_gj_pivot<<<1, 1024, 0, s>>>(H.cinv.p, n, k, perm.p, colk.p, flag.p);
+    k_gj_elim<<<eg, 256, 0, s>>>(H.cinv.p, n, k, colk.p);
+  }
+  FS_LAUNCHED();
+  k_gj_unpermute<<<blocks_for(n, 128, kSMs), 128, 0, s>>>(H.cinv.p, n, perm.p);
+  FS_LAUNCHED();
+  int h = 0;
+  FS_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  FS_REQUIRE(!h, FC_SINGULAR_BLOCK, "singular coarsest-level matrix");
+}
+
+template <typename TP>
+void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s) {
+  C.clear();
+  C.resize(H.lev.size());
+  for (size_t l = 0; l < H.lev.size(); l++) {
+    LevelSetup &L = H.lev[l];
+    LevelCycle<TP> &c = C[l];
+    const int64_t n = (int64_t)L.nb * L.B;
+    const bool last = (l + 1 == H.lev.size());
+    if constexpr (std::is_same<TP, double>::value) {
+      c.S = L.S.view();
+      if (!last) { c.P = L.P.view(); c.R = L.R.view(); c.Dinv = L.Dinv.p; }
+    } else {
+      c.S_own = copy_cast<TP, double>(L.S.view(), s);
+      c.S = c.S_own.view();
+      if (!last) {
+        c.P_own = copy_cast<TP, double>(L.P.view(), s);
+        c.R_own = copy_cast<TP, double>(L.R.view(), s);
+        c.P = c.P_own.view();
+        c.R = c.R_own.view();
+        c.Dinv_own.alloc((size_t)L.nb * L.B * L.B);
+        cast(c.Dinv_own.p, L.Dinv.p, (int64_t)L.nb * L.B * L.B, s);
+        c.Dinv = c.Dinv_own.p;
+      }
+    }
+    c.f.alloc(n > 0 ? n : 1);
+    c.x.alloc(n > 0 ? n : 1);
+    c.xa.alloc(n > 0 ? n : 1);
+    c.d.alloc(n > 0 ? n : 1);
+    c.r.alloc(n > 0 ? n : 1);
+    if (!last) {
+      double hi = H.prm.cheb_hi * L.lam, lo = H.prm.cheb_lo * hi;
+      c.theta = 0.5 * (hi + lo);
+      c.delta = 0.5 * (hi - lo);
+      c.sigma = c.theta / c.delta;
+    }
+  }
+  FS_CUDA(cudaStreamSynchronize(s));
+}
+
+template <int B>
+void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s) {
+  const AmgParams &p = H.prm;
+  H.lev.clear();
+  H.lev.emplace_back();
+  H.lev[0].B = B;
+  H.lev[0].S = std::move(S0);
+  H.lev[0].nb = H.lev[0].S.nbr;
+  for (int l = 0;; l++) {
+    LevelSetup &L = H.lev[l];
+    const int nb = L.nb;
+    if (p.verbose) fprintf(stderr, "[fracsolve] AMG(B=%d) level %d: %d block rows, %lld blocks\n", B, l, nb, (long long)L.S.nnzb);
+    if (nb <= p.coarse_max || l + 1 >= p.max_levels) break;
+    // diagonal blocks
+    L.Dinv.alloc((size_t)nb * B * B);
+    DBuf<double> dn(nb);
+    DBuf<int> flag(1);
+    FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    k_diag<B><<<grid_rows(nb), kT, 0, s>>>(L.S.view(), L.Dinv.p, dn.p, flag.p);
+    FS_LAUNCHED();
+    int hf = 0;
+    FS_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+    FS_REQUIRE(!hf, FC_SINGULAR_BLOCK, "singular diagonal block in AMG level " + std::to_string(l));
+    // strength graph and aggregates
+    const double theta = p.theta0 * std::pow(p.theta_decay, l);
+    Graph G = strength_graph(L.S.view(), dn.p, theta, s);
+    DBuf<int> asize;
+    int nc = aggregate(G, p.seed, l, L.agg, asize, p.verbose, s);
+    if (nc == 0 || nc > p.max_ratio * nb) {
+      L.Dinv.release();
+      L.agg.release();
+      break;
+    }
+    L.lam = power_lambda<B>(L.S.view(), L.Dinv.p, p.seed, l, p.power_steps, s);
+    build_prolongator<B>(L, asize, nc, p.omega_num / L.lam, s);
+    L.R = transpose(L.P.view(), s);
+    Bsr<double> SP = spgemm(L.S.view(), L.P.view(), s);
+    Bsr<double> Sc = spgemm(L.R.view(), SP.view(), s);
+    LevelSetup next;
+    next.B = B;
+    next.S = std::move(Sc);
+    next.nb = nc;
+    H.lev.push_back(std::move(next));
+  }
+  const int nlast = H.lev.back().nb * B;
+  FS_REQUIRE(nlast <= 8192, FC_INTERNAL, "coarsest AMG level too large for the dense solve");
+  invert_coarsest(H, s);
+  if (precision == FC_MIXED) prepare_cycle<float>(H, H.cf, s);
+  else prepare_cycle<double>(H, H.cd, s);
+  H.built = true;
+}
+
+}  // namespace
+
+void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int precision,
+               cudaStream_t s) {
+  H.prm = prm;
+  H.B = B;
+  H.built = false;
+  if (B == 3) setup_levels<3>(H, std::move(S0), precision, s);
+  else if (B == 1) setup_levels<1>(H, std::move(S0), precision, s);
+  else throw Error(FC_BAD_ARG, "AMG block size must be 1 or 3");
+}
+
+// ============================================================ cycle
+namespace {
+template <int B, typename TP>
+void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *f, TP *xout, cudaStream_t s) {
+  const int L = (int)C.size();
+  if (l == L - 1) {
+    const int n = H.nc_scalar;
+    if (n == 0) return;
+    k_dense_gemv<TP><<<blocks_for((int64_t)n * 32, 256, kSMs * 16), 256, 0, s>>>(n, H.cinv.p, f, xout);
+    FS_LAUNCHED();
+    return;
+  }
+  LevelCycle<TP> &c = C[l];
+  const int64_t nb = c.S.nbr;
+  const int deg = H.prm.cheb_degree;
+  TP *buf[2] = {c.xa.p, xout};
+  int cur = 0;
+  // pre-smoothing from x = 0
+  double rho = 1.0 / c.sigma;
+  k_cheb_zero<B, TP><<<grid_rows(nb), kT, 0, s>>>(nb, f, c.Dinv, (TP)(1.0 / c.theta), c.d.p, buf[cur]);
+  FS_LAUNCHED();
+  for (int k = 1; k < deg; k++) {
+    double rn = 1.0 / (2.0 * c.sigma - rho);
+    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
+    spmv<B, B>(c.S, buf[cur], e, s);
+    cur ^= 1;
+    rho = rn;
+  }
+  // residual, restriction, coarse correction, prolongation
+  spmv_axpby<B, B>(c.S, buf[cur], c.r.p, -1.0, 1.0, f, s);
+  LevelCycle<TP> &cn = C[l + 1];
+  spmv_axpby<B, B>(c.R, c.r.p, cn.f.p, 1.0, 0.0, (const TP *)nullptr, s);
+  cycle_level<B, TP>(H, C, l + 1, cn.f.p, cn.x.p, s);
+  spmv_axpby<B, B>(c.P, cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
+  // post-smoothing from the corrected iterate
+  rho = 1.0 / c.sigma;
+  {
+    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)0, (TP)(1.0 / c.theta)};
+    spmv<B, B>(c.S, buf[cur], e, s);
+    cur ^= 1;
+  }
+  for (int k = 1; k < deg; k++) {
+    double rn = 1.0 / (2.0 * c.sigma - rho);
+    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
+    spmv<B, B>(c.S, buf[cur], e, s);
+    cur ^= 1;
+    rho = rn;
+  }
+}
+}  // namespace
+
+template <typename TP>
+void amg_vcycle(Hierarchy &H, const TP *f, TP *x, cudaStream_t s) {
+  FS_REQUIRE(H.built, FC_NOT_SETUP, "AMG hierarchy not built");
+  std::vector<LevelCycle<TP>> *C;
+  if constexpr (std::is_same<TP, float>::value) C = &H.cf;
+  else C = &H.cd;
+  FS_REQUIRE(!C->empty(), FC_NOT_SETUP, "AMG cycle data not prepared for this precision");
+  if (H.B == 3) cycle_level<3, TP>(H, *C, 0, f, x, s);
+  else cycle_level<1, TP>(H, *C, 0, f, x, s);
+}
+
+template void amg_vcycle<float>(Hierarchy &, const float *, float *, cudaStream_t);
+template void amg_vcycle<double>(Hierarchy &, const double *, double *, cudaStream_t);
+
+}  // namespace fs

@@ -1,0 +1,66 @@
+// Smoothed-aggregation AMG: hierarchy construction on the device (double)
+// and the V(1,1)-cycle with a Chebyshev smoother (float or double).
+#pragma once
+
+#include <memory>
+
+#include "common.cuh"
+
+namespace fs {
+
+struct AmgParams {
+  double theta0 = 0.08, theta_decay = 0.5;
+  int coarse_max = 1000, max_levels = 12;
+  double max_ratio = 0.8;
+  int power_steps = 15;
+  double omega_num = 4.0 / 3.0;
+  int cheb_degree = 2;
+  double cheb_hi = 1.1, cheb_lo = 0.1;
+  uint64_t seed = 0;
+  int verbose = 0;
+};
+
+// Per-level data built in double precision.
+struct LevelSetup {
+  int B = 3, nb = 0;
+  Bsr<double> S;        // level operator
+  Bsr<double> P, R;     // prolongator (nb x nc blocks) and R = P^T (not on the coarsest)
+  DBuf<double> Dinv;    // nb * B * B inverse diagonal blocks
+  DBuf<int> agg;        // aggregate of each block row (-1: none)
+  double lam = 0.0;     // power estimate of the largest eigenvalue of D^-1 S
+};
+
+// Per-level data of the cycle in precision TP.
+template <typename TP>
+struct LevelCycle {
+  BsrView<TP> S, P, R;
+  const TP *Dinv = nullptr;
+  Bsr<TP> S_own, P_own, R_own;   // used when TP differs from double
+  DBuf<TP> Dinv_own;
+  DBuf<TP> f, x, xa, d, r;       // right-hand side, iterate (two buffers), direction, residual
+  double theta = 0, delta = 0, sigma = 0;
+};
+
+struct Hierarchy {
+  int B = 3;
+  bool built = false;
+  AmgParams prm;
+  std::vector<LevelSetup> lev;
+  // coarsest level: explicit inverse in double, n_c x n_c row-major
+  DBuf<double> cinv;
+  int nc_scalar = 0;
+  std::vector<LevelCycle<float>> cf;
+  std::vector<LevelCycle<double>> cd;
+  int levels() const { return (int)lev.size(); }
+};
+
+// Build the hierarchy of S0 (block size B, square, sorted rows).  Takes
+// ownership of S0.  precision: FC_FP64 or FC_MIXED (casts the cycle data).
+void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int precision,
+               cudaStream_t s);
+
+// x = V-cycle(f) with zero initial guess; f and x have nb(0) * B entries.
+template <typename TP>
+void amg_vcycle(Hierarchy &H, const TP *f, TP *x, cudaStream_t s);
+
+}  // namespace fs

@@ -1,0 +1,166 @@
+// Shared device-side infrastructure: owned device buffers, BSR matrices,
+// status handling, deterministic reductions and scans.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/fracsolve.h"
+
+namespace fs {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+[[noreturn]] void cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define FS_CUDA(x)                                                   \
+  do {                                                               \
+    cudaError_t e_ = (x);                                            \
+    if (e_ != cudaSuccess) ::fs::cuda_fail(e_, #x, __FILE__, __LINE__); \
+  } while (0)
+#define FS_LAUNCHED() FS_CUDA(cudaGetLastError())
+#define FS_REQUIRE(cond, code, msg)                 \
+  do {                                              \
+    if (!(cond)) throw ::fs::Error((code), (msg));  \
+  } while (0)
+
+// ---------------------------------------------------------------- buffers
+template <typename T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  explicit DBuf(size_t n_) { alloc(n_); }
+  void alloc(size_t n_) {
+    release();
+    if (n_ == 0) return;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), n_ * sizeof(T));
+    if (e == cudaErrorMemoryAllocation) {
+      (void)cudaGetLastError();
+      p = nullptr;
+      throw Error(FC_OOM, "cudaMalloc of " + std::to_string(n_ * sizeof(T)) + " bytes failed");
+    }
+    FS_CUDA(e);
+    n = n_;
+  }
+  // grow-only reallocation (contents are not kept)
+  void ensure(size_t n_) {
+    if (n_ > n) alloc(n_);
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DBuf() { release(); }
+  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf &operator=(DBuf &&o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; n = o.n; o.p = nullptr; o.n = 0;
+    }
+    return *this;
+  }
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  T *data() const { return p; }
+  size_t size() const { return n; }
+};
+
+// Non-owning view of a block sparse row matrix on the device.
+template <typename T>
+struct BsrView {
+  int nbr = 0, nbc = 0, br = 0, bc = 0;
+  int64_t nnzb = 0;
+  const int *rp = nullptr;
+  const int *ci = nullptr;
+  const T *val = nullptr;
+};
+
+// Owned block sparse row matrix on the device; blocks row-major br x bc.
+template <typename T>
+struct Bsr {
+  int nbr = 0, nbc = 0, br = 0, bc = 0;
+  int64_t nnzb = 0;
+  DBuf<int> rp, ci;
+  DBuf<T> val;
+  BsrView<T> view() const {
+    BsrView<T> v;
+    v.nbr = nbr; v.nbc = nbc; v.br = br; v.bc = bc; v.nnzb = nnzb;
+    v.rp = rp.p; v.ci = ci.p; v.val = val.p;
+    return v;
+  }
+  void shape(int nbr_, int nbc_, int br_, int bc_) {
+    nbr = nbr_; nbc = nbc_; br = br_; bc = bc_;
+  }
+  int64_t bsz() const { return (int64_t)br * bc; }
+};
+
+// ---------------------------------------------------------------- launch
+constexpr int kSMs = 152;
+inline int blocks_for(int64_t n, int threads, int cap = 65535 * 16) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// ---------------------------------------------------------------- utilities
+// out[0..n]: exclusive prefix sum of in[0..n-1], out[n] = total.  Returns the
+// total (synchronises the stream).
+int64_t exclusive_scan(const int *d_in, int *d_out, int n, cudaStream_t s);
+
+// Deterministic dot products: fixed grid and fixed reduction order.
+template <typename T>
+double dot(const T *x, const T *y, int64_t n, cudaStream_t s, double *d_tmp);
+// sum of squares to a device scalar (no host sync)
+template <typename T>
+void nrm2sq_dev(const T *x, int64_t n, double *d_out, cudaStream_t s, double *d_partials);
+constexpr int kRedBlocks = 1024;   // partial sums of the two-stage reductions
+
+template <typename TO, typename TI>
+void cast(TO *out, const TI *in, int64_t n, cudaStream_t s);
+template <typename T>
+void fill(T *out, T v, int64_t n, cudaStream_t s);
+// y = a*x + b*y
+template <typename T>
+void axpby(T *y, const T *x, double a, double b, int64_t n, cudaStream_t s);
+// z = a*x + b*y (z may alias y)
+template <typename TZ, typename TX, typename TY>
+void axpbyz(TZ *z, const TX *x, const TY *y, double a, double b, int64_t n, cudaStream_t s);
+// y = s * x
+template <typename T>
+void scale_to(T *y, const T *x, double a, int64_t n, cudaStream_t s);
+
+// 64-bit SplitMix64 counter generator (Steele, Lea, Flood 2014).
+__host__ __device__ inline uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__host__ __device__ inline uint64_t sm64_draw(uint64_t seed, uint64_t stream, uint64_t i) {
+  const uint64_t g = 0x9E3779B97F4A7C15ULL;
+  uint64_t key = sm64_mix(seed * g + stream);
+  return sm64_mix(key + (i + 1) * g);
+}
+__host__ __device__ inline double sm64_uniform(uint64_t seed, uint64_t stream, uint64_t i) {
+  return (double)(sm64_draw(seed, stream, i) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Warp reduction (sum) over `width` lanes.
+template <typename T, int W = 32>
+__device__ inline T warp_sum(T v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, W);
+  return v;
+}
+
+}  // namespace fs

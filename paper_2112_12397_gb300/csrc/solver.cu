@@ -1,0 +1,746 @@
+// The C-ABI of libfracsolve: setup of the block preconditioners (Alg. 1, 3),
+// their application (Alg. 2, 4), the Jacobian product (Eq. JacSys) and the
+// right-preconditioned flexible GMRES with CGS2 of Sec. 4.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <type_traits>
+
+#include "amg.cuh"
+#include "schur.cuh"
+#include "sparse.cuh"
+#include "spmv.cuh"
+
+using namespace fs;
+
+namespace {
+
+template <typename TP>
+struct PrecData {
+  BsrView<TP> C1, Q1, C2, Q2;
+  const TP *Hinv = nullptr;
+  Bsr<TP> C1o, Q1o, C2o, Q2o;
+  DBuf<TP> Hinvo;
+  DBuf<TP> w, out, tt, tu, su, tp, sp, vp;
+  bool ready = false;
+};
+
+// ------------------------------------------------------------ small kernels
+template <typename TP>
+__global__ void k_face_hinv(int64_t nf, const TP *Hinv, const TP *in, TP *out) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const TP *h = Hinv + f * 9;
+    TP a = in[3 * f], b = in[3 * f + 1], c = in[3 * f + 2];
+    out[3 * f] = h[0] * a + h[1] * b + h[2] * c;
+    out[3 * f + 1] = h[3] * a + h[4] * b + h[5] * c;
+    out[3 * f + 2] = h[6] * a + h[7] * b + h[8] * c;
+  }
+}
+
+// partial[(c0+q) * gridDim.x + block] = sum over this block's elements of V_{c0+q} . w
+constexpr int kMdotBlocks = 2 * kSMs;
+constexpr int kMdotThreads = 256;
+constexpr int kMdotChunk = 8;
+
+__global__ void __launch_bounds__(kMdotThreads)
+    k_mdot(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ w, double *partial) {
+  __shared__ double sm[kMdotThreads / 32][kMdotChunk];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < m; c0 += kMdotChunk) {
+    const int nq = min(kMdotChunk, m - c0);
+    double acc[kMdotChunk];
+#pragma unroll
+    for (int q = 0; q < kMdotChunk; q++) acc[q] = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const double we = w[e];
+#pragma unroll
+      for (int q = 0; q < kMdotChunk; q++)
+        if (q < nq) acc[q] += V[(int64_t)(c0 + q) * n + e] * we;
+    }
+#pragma unroll
+    for (int q = 0; q < kMdotChunk; q++) {
+      double v = warp_sum(acc[q]);
+      if (lane == 0) sm[wid][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+      double v = 0.0;
+      for (int k = 0; k < kMdotThreads / 32; k++) v += sm[k][threadIdx.x];
+      partial[(int64_t)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// h[i] = sum_b partial[i][b]; hacc[i] (+)= h[i]
+__global__ void k_mdot_final(const double *partial, int m, int nb, double *h, double *hacc, int accumulate) {
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += (gridDim.x * blockDim.x) >> 5) {
+    double v = 0.0;
+    for (int b = lane; b < nb; b += 32) v += partial[(int64_t)i * nb + b];
+    v = warp_sum(v);
+    if (lane == 0) {
+      h[i] = v;
+      hacc[i] = accumulate ? hacc[i] + v : v;
+    }
+  }
+}
+
+// w -= sum_i V_i h_i
+__global__ void k_msub(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ h, double *w) {
+  extern __shared__ double hs[];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < m; i++) s += V[(int64_t)i * n + e] * hs[i];
+    w[e] -= s;
+  }
+}
+
+// x = sum_j Z_j y_j
+template <typename TP>
+__global__ void k_mcomb(const TP *__restrict__ Z, int k, int64_t n, const double *__restrict__ y, double *x) {
+  extern __shared__ double ys[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < k; j++) s += (double)Z[(int64_t)j * n + e] * ys[j];
+    x[e] = s;
+  }
+}
+
+// Arnoldi column j: Hessenberg entries from hacc and ||w||^2, previous Givens
+// rotations, a new rotation, the residual recurrence.  stat[0] = |g_{j+1}|/beta,
+// stat[1] = h_{j+1,j}, stat[2] = w0 (norm before orthogonalisation),
+// stat[3] = 1 / h_{j+1,j} (0 on breakdown).
+__global__ void k_givens(int j, int ld, const double *hacc, const double *w2, const double *w02, double beta,
+                         double *Hm, double *cs, double *sn, double *g, double *stat) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double *col = Hm + (int64_t)j * ld;
+  for (int i = 0; i <= j; i++) col[i] = hacc[i];
+  const double hn = sqrt(*w2);
+  const double w0 = sqrt(*w02);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; i++) {
+    double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  double r = hypot(col[j], col[j + 1]);
+  cs[j] = col[j] / r;
+  sn[j] = col[j + 1] / r;
+  col[j] = r;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  stat[0] = fabs(g[j + 1]) / beta;
+  stat[1] = hn;
+  stat[2] = w0;
+  stat[3] = (hn > 1e-14 * w0 && hn > 0.0) ? 1.0 / hn : 0.0;
+}
+
+__global__ void k_scale_by(double *v, int64_t n, const double *sc) {
+  const double a = *sc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    v[e] *= a;
+}
+
+__global__ void k_trisolve(int k, int ld, const double *Hm, const double *g, double *y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; i--) {
+    double s = g[i];
+    for (int c = i + 1; c < k; c++) s -= Hm[(int64_t)c * ld + i] * y[c];
+    y[i] = s / Hm[(int64_t)i * ld + i];
+  }
+}
+
+__global__ void k_set_scalar(double *p, double v) { *p = v; }
+
+inline int vgrid(int64_t n) { return blocks_for(n, 256, kSMs * 16); }
+
+}  // namespace
+
+// ============================================================ context
+struct fc_ctx {
+  fc_options opt;
+  cudaStream_t s = nullptr;
+  int device = 0;
+  std::string err;
+  bool ready = false;
+  int nn = 0, nf = 0;
+  int64_t n = 0, nu = 0, nt = 0;
+  Bsr<double> A, C1, Q1, C2, H, Q2, T;
+  DBuf<double> Hinv64, SK;
+  Bsr<double> S1, St, S2t;
+  bool have[2] = {false, false};
+  Hierarchy hier[4];
+  PrecData<float> pf;
+  PrecData<double> pd;
+  // Krylov workspace
+  int kcap = 0;
+  DBuf<double> V, Hm, cs, sn, g, y, hacc, htmp, partial, stat, w2, w02, red;
+  DBuf<float> Zf;
+  DBuf<double> Zd;
+  DBuf<double> xk, rk, bk, hb, hx;
+  double *stat_host = nullptr;   // pinned
+  ~fc_ctx() {
+    if (stat_host) cudaFreeHost(stat_host);
+  }
+};
+
+namespace {
+
+AmgParams amg_params(const fc_options &o, bool pressure) {
+  AmgParams p;
+  p.theta0 = o.theta0;
+  p.theta_decay = o.theta_decay;
+  p.coarse_max = pressure ? o.coarse_max_p : o.coarse_max;
+  p.max_levels = o.max_levels;
+  p.max_ratio = o.max_ratio;
+  p.power_steps = o.power_steps;
+  p.omega_num = o.omega_num;
+  p.cheb_degree = o.cheb_degree;
+  p.cheb_hi = o.cheb_hi;
+  p.cheb_lo = o.cheb_lo;
+  p.seed = o.amg_seed;
+  p.verbose = o.verbose;
+  return p;
+}
+
+void check_bsr(const fc_bsr &m, int nbr, int nbc, int br, int bc, const char *name) {
+  bool ok = m.n_brows == nbr && m.n_bcols == nbc && m.br == br && m.bc == bc && m.nnzb >= 0 &&
+            (m.nnzb == 0 || (m.d_col_idx && m.d_val)) && m.d_row_ptr;
+  FS_REQUIRE(ok, FC_BAD_ARG, std::string("block ") + name + " has inconsistent sizes or null pointers");
+}
+
+template <typename TP>
+void prepare_prec(fc_ctx &c, PrecData<TP> &P) {
+  cudaStream_t s = c.s;
+  if constexpr (std::is_same<TP, double>::value) {
+    P.C1 = c.C1.view(); P.Q1 = c.Q1.view(); P.C2 = c.C2.view(); P.Q2 = c.Q2.view();
+    P.Hinv = c.Hinv64.p;
+  } else {
+    P.C1o = copy_cast<TP, double>(c.C1.view(), s);
+    P.Q1o = copy_cast<TP, double>(c.Q1.view(), s);
+    P.C2o = copy_cast<TP, double>(c.C2.view(), s);
+    P.Q2o = copy_cast<TP, double>(c.Q2.view(), s);
+    P.C1 = P.C1o.view(); P.Q1 = P.Q1o.view(); P.C2 = P.C2o.view(); P.Q2 = P.Q2o.view();
+    P.Hinvo.alloc((size_t)c.nf * 9 > 0 ? (size_t)c.nf * 9 : 1);
+    cast(P.Hinvo.p, c.Hinv64.p, (int64_t)c.nf * 9, s);
+    P.Hinv = P.Hinvo.p;
+  }
+  const int64_t n = c.n;
+  P.w.alloc(n); P.out.alloc(n);
+  P.tt.alloc(c.nt > 0 ? c.nt : 1);
+  P.tu.alloc(c.nu); P.su.alloc(c.nu);
+  P.tp.alloc(c.nf > 0 ? c.nf : 1); P.sp.alloc(c.nf > 0 ? c.nf : 1); P.vp.alloc(c.nf > 0 ? c.nf : 1);
+  P.ready = true;
+}
+
+// z = M^-1 w, both in precision TP (Alg. 2 or Alg. 4)
+template <typename TP>
+void apply_prec(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
+  cudaStream_t s = c.s;
+  const int64_t nu = c.nu, nt = c.nt;
+  const int64_t nf = c.nf;
+  const TP *w_u = w, *w_t = w + nu, *w_p = w + nu + nt;
+  TP *z_u = z, *z_t = z + nu, *z_p = z + nu + nt;
+  if (variant == FC_TUP) {
+    Hierarchy &Hu = c.hier[FC_H_TUP_U], &Hp = c.hier[FC_H_TUP_P];
+    if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }   // 1
+    spmv_axpby<3, 3>(P.C1, P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                          // 2
+    amg_vcycle<TP>(Hu, P.tu.p, P.su.p, s);                                                            // 3
+    spmv_axpby<1, 3>(P.Q2, P.su.p, P.tp.p, -1.0, 1.0, w_p, s);                                        // 4
+    if (nf) amg_vcycle<TP>(Hp, P.tp.p, z_p, s);                                                        // 5
+    spmv_axpby<3, 1>(P.Q1, z_p, P.tu.p, 1.0, 0.0, (const TP *)nullptr, s);                           // 6
+    amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // 7
+    axpbyz(z_u, P.su.p, z_u, 1.0, -1.0, nu, s);                                                       // 8
+    if (nf) {                                                                                         // 9-10
+      EpiHinvUpdate<TP> e{z_t, P.tt.p, P.Hinv};
+      spmv<3, 3>(P.C2, z_u, e, s);
+    }
+  } else {
+    Hierarchy &Hu = c.hier[FC_H_TPU_U], &Hp = c.hier[FC_H_TPU_P];
+    if (nf) amg_vcycle<TP>(Hp, w_p, P.tp.p, s);                                                        // 1
+    if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }    // 2
+    spmv_axpby<3, 3>(P.C1, P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                          // 3
+    spmv_axpby<3, 1>(P.Q1, P.tp.p, P.tu.p, -1.0, 1.0, P.tu.p, s);
+    amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // 4
+    if (nf) {
+      spmv_axpby<1, 3>(P.Q2, z_u, P.sp.p, 1.0, 0.0, (const TP *)nullptr, s);                          // 5
+      amg_vcycle<TP>(Hp, P.sp.p, P.vp.p, s);                                                          // 7
+      axpbyz(z_p, P.tp.p, P.vp.p, 1.0, -1.0, nf, s);
+      EpiHinvUpdate<TP> e{z_t, P.tt.p, P.Hinv};                                                      // 6, 8
+      spmv<3, 3>(P.C2, z_u, e, s);
+    }
+  }
+}
+
+// y = J z (double out)
+template <typename TX>
+void jac_spmv(fc_ctx &c, const TX *z, double *y) {
+  cudaStream_t s = c.s;
+  const TX *z_u = z, *z_t = z + c.nu, *z_p = z + c.nu + c.nt;
+  double *y_u = y, *y_t = y + c.nu, *y_p = y + c.nu + c.nt;
+  spmv_axpby<3, 3>(c.A.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
+  if (c.nf) {
+    spmv_axpby<3, 3>(c.C1.view(), z_t, y_u, 1.0, 1.0, y_u, s);
+    spmv_axpby<3, 1>(c.Q1.view(), z_p, y_u, 1.0, 1.0, y_u, s);
+    spmv_axpby<3, 3>(c.C2.view(), z_u, y_t, 1.0, 0.0, (const double *)nullptr, s);
+    spmv_axpby<3, 3>(c.H.view(), z_t, y_t, -1.0, 1.0, y_t, s);
+    spmv_axpby<1, 3>(c.Q2.view(), z_u, y_p, 1.0, 0.0, (const double *)nullptr, s);
+    spmv_axpby<1, 1>(c.T.view(), z_p, y_p, 1.0, 1.0, y_p, s);
+  }
+}
+
+template <typename TP>
+PrecData<TP> &prec(fc_ctx &c);
+template <>
+PrecData<float> &prec<float>(fc_ctx &c) { return c.pf; }
+template <>
+PrecData<double> &prec<double>(fc_ctx &c) { return c.pd; }
+
+template <typename TP>
+TP *zbase(fc_ctx &c);
+template <>
+float *zbase<float>(fc_ctx &c) { return c.Zf.p; }
+template <>
+double *zbase<double>(fc_ctx &c) { return c.Zd.p; }
+
+void ensure_krylov(fc_ctx &c, int maxit) {
+  if (c.kcap >= maxit) return;
+  const int64_t n = c.n;
+  c.V.alloc((size_t)(maxit + 1) * n);
+  if (c.opt.precision == FC_MIXED) c.Zf.alloc((size_t)maxit * n);
+  else c.Zd.alloc((size_t)maxit * n);
+  c.Hm.alloc((size_t)(maxit + 1) * maxit);
+  c.cs.alloc(maxit); c.sn.alloc(maxit); c.g.alloc(maxit + 1); c.y.alloc(maxit);
+  c.hacc.alloc(maxit + 1); c.htmp.alloc(maxit + 1);
+  c.partial.alloc((size_t)(maxit + 1) * kMdotBlocks);
+  c.kcap = maxit;
+}
+
+void cgs_pass(fc_ctx &c, int m, double *w, int accumulate) {
+  const int64_t n = c.n;
+  k_mdot<<<kMdotBlocks, kMdotThreads, 0, c.s>>>(c.V.p, m, n, w, c.partial.p);
+  FS_LAUNCHED();
+  k_mdot_final<<<blocks_for((int64_t)m * 32, 256, 1024), 256, 0, c.s>>>(c.partial.p, m, kMdotBlocks, c.htmp.p,
+                                                                         c.hacc.p, accumulate);
+  FS_LAUNCHED();
+  k_msub<<<vgrid(n), 256, sizeof(double) * m, c.s>>>(c.V.p, m, n, c.htmp.p, w);
+  FS_LAUNCHED();
+}
+
+struct FgmresOut {
+  int iters = 0;
+  int status = FC_OK;
+};
+
+// one FGMRES cycle (no restart) on rhs r0 (device, double); dx written to x
+template <typename TP>
+FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rtol, int maxit) {
+  cudaStream_t s = c.s;
+  const int64_t n = c.n;
+  PrecData<TP> &P = prec<TP>(c);
+  ensure_krylov(c, maxit);
+  FgmresOut out;
+  const double beta = std::sqrt(dot(rhs, rhs, n, s, c.red.p));
+  if (!std::isfinite(beta)) { out.status = FC_NAN; return out; }
+  if (beta == 0.0) {
+    FS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    return out;
+  }
+  scale_to(c.V.p, rhs, 1.0 / beta, n, s);
+  k_set_scalar<<<1, 1, 0, s>>>(c.g.p, beta);
+  FS_LAUNCHED();
+  TP *Z = zbase<TP>(c);
+  int k = 0;
+  for (int j = 0; j < maxit; j++) {
+    double *vj = c.V.p + (int64_t)j * n;
+    double *w = c.V.p + (int64_t)(j + 1) * n;
+    TP *zj = Z + (int64_t)j * n;
+    if constexpr (std::is_same<TP, double>::value) {
+      apply_prec<TP>(c, P, variant, vj, zj);
+    } else {
+      cast(P.w.p, vj, n, s);
+      apply_prec<TP>(c, P, variant, P.w.p, zj);
+    }
+    jac_spmv<TP>(c, zj, w);
+    nrm2sq_dev(w, n, c.w02.p, s, c.red.p);
+    cgs_pass(c, j + 1, w, 0);
+    cgs_pass(c, j + 1, w, 1);
+    nrm2sq_dev(w, n, c.w2.p, s, c.red.p);
+    k_givens<<<1, 1, 0, s>>>(j, maxit + 1, c.hacc.p, c.w2.p, c.w02.p, beta, c.Hm.p, c.cs.p, c.sn.p, c.g.p, c.stat.p);
+    FS_LAUNCHED();
+    k_scale_by<<<vgrid(n), 256, 0, s>>>(w, n, c.stat.p + 3);
+    FS_LAUNCHED();
+    FS_CUDA(cudaMemcpyAsync(c.stat_host, c.stat.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+    k = j + 1;
+    const double est = c.stat_host[0];
+    if (!std::isfinite(est)) { out.status = FC_NAN; break; }
+    if (c.opt.verbose > 1) fprintf(stderr, "[fracsolve] it %d est %.3e\n", k, est);
+    const bool breakdown = c.stat_host[3] == 0.0;
+    if (est <= rtol) break;
+    if (breakdown) { out.status = FC_BREAKDOWN; break; }
+    if (k == maxit) out.status = FC_NOT_CONVERGED;
+  }
+  out.iters = k;
+  k_trisolve<<<1, 1, 0, s>>>(k, maxit + 1, c.Hm.p, c.g.p, c.y.p);
+  FS_LAUNCHED();
+  k_mcomb<TP><<<vgrid(n), 256, sizeof(double) * k, s>>>(Z, k, n, c.y.p, x);
+  FS_LAUNCHED();
+  return out;
+}
+
+template <typename TP>
+int solve_impl(fc_ctx &c, int variant, const double *b, double *x, double tol, int maxit, int *iters,
+               double *relres) {
+  cudaStream_t s = c.s;
+  const int64_t n = c.n;
+  c.xk.ensure(n); c.rk.ensure(n);
+  const double bn = std::sqrt(dot(b, b, n, s, c.red.p));
+  if (!std::isfinite(bn)) return FC_NAN;
+  int total = 0;
+  int status = FC_OK;
+  const double *rhs = b;
+  double rr = 0.0;
+  const int restarts = c.opt.precision == FC_MIXED ? std::max(0, (int)c.opt.max_restarts) : 0;
+  FS_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  if (bn == 0.0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return FC_OK;
+  }
+  for (int cycle = 0;; cycle++) {
+    if (maxit - total <= 0) break;
+    const double rn = cycle == 0 ? bn : std::sqrt(dot(rhs, rhs, n, s, c.red.p));
+    const double rtol = tol * bn / rn;
+    FgmresOut o = fgmres<TP>(c, variant, rhs, c.xk.p, rtol, maxit - total);
+    total += o.iters;
+    axpby(x, c.xk.p, 1.0, 1.0, n, s);
+    // true residual in double
+    jac_spmv<double>(c, x, c.rk.p);
+    axpbyz(c.rk.p, b, c.rk.p, 1.0, -1.0, n, s);
+    rr = std::sqrt(dot(c.rk.p, c.rk.p, n, s, c.red.p)) / bn;
+    status = o.status;
+    if (!std::isfinite(rr)) { status = FC_NAN; break; }
+    if (rr <= tol) { status = FC_OK; break; }
+    if (o.status == FC_NAN || cycle >= restarts || total >= maxit) {
+      if (status == FC_OK) status = FC_NOT_CONVERGED;
+      break;
+    }
+    rhs = c.rk.p;
+  }
+  if (iters) *iters = total;
+  if (relres) *relres = rr;
+  return status;
+}
+
+}  // namespace
+
+// ============================================================ error plumbing
+namespace {
+int run(fc_ctx *c, const std::function<int()> &fn) {
+  try {
+    if (c) {
+      c->err.clear();
+      FS_CUDA(cudaSetDevice(c->device));
+    }
+    return fn();
+  } catch (const Error &e) {
+    if (c) c->err = e.what();
+    (void)cudaGetLastError();
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    if (c) c->err = "host allocation failed";
+    return FC_OOM;
+  } catch (const std::exception &e) {
+    if (c) c->err = e.what();
+    return FC_INTERNAL;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+void fc_default_options(fc_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = FC_FP64;
+  o->variants = (1 << FC_TPU) | (1 << FC_TUP);
+  o->theta0 = 0.08;
+  o->theta_decay = 0.5;
+  o->coarse_max = 1000;
+  o->coarse_max_p = 1000;
+  o->max_levels = 12;
+  o->max_ratio = 0.8;
+  o->power_steps = 15;
+  o->omega_num = 4.0 / 3.0;
+  o->cheb_degree = 2;
+  o->cheb_hi = 1.1;
+  o->cheb_lo = 0.1;
+  o->amg_seed = 0;
+  o->max_restarts = 3;
+  o->verbose = 0;
+}
+
+int fc_create(fc_ctx **out, const fc_options *opt, void *stream) {
+  if (!out) return FC_BAD_ARG;
+  *out = nullptr;
+  std::unique_ptr<fc_ctx> c(new (std::nothrow) fc_ctx());
+  if (!c) return FC_OOM;
+  int rc = run(nullptr, [&]() {
+    if (opt) c->opt = *opt;
+    else fc_default_options(&c->opt);
+    const fc_options &o = c->opt;
+    FS_REQUIRE(o.precision == FC_FP64 || o.precision == FC_MIXED, FC_BAD_ARG, "precision");
+    FS_REQUIRE((o.variants & 3) != 0, FC_BAD_ARG, "variants");
+    FS_REQUIRE(o.cheb_degree >= 1 && o.cheb_degree <= 16, FC_BAD_ARG, "cheb_degree");
+    FS_REQUIRE(o.coarse_max >= 1 && o.coarse_max_p >= 1 && o.max_levels >= 1, FC_BAD_ARG, "levels");
+    FS_REQUIRE(o.cheb_hi > 0 && o.cheb_lo > 0 && o.cheb_lo < 1, FC_BAD_ARG, "chebyshev interval");
+    FS_CUDA(cudaGetDevice(&c->device));
+    c->s = (cudaStream_t)stream;
+    FS_CUDA(cudaMallocHost(reinterpret_cast<void **>(&c->stat_host), 8 * sizeof(double)));
+    c->stat.alloc(8);
+    c->w2.alloc(1);
+    c->w02.alloc(1);
+    c->red.alloc(kRedBlocks + 1);
+    return FC_OK;
+  });
+  if (rc == FC_OK) *out = c.release();
+  return rc;
+}
+
+int fc_setup(fc_ctx *c, const fc_blocks *J) {
+  if (!c || !J) return FC_BAD_ARG;
+  return run(c, [&]() {
+    c->ready = false;
+    const int nn = J->n_node, nf = J->n_face;
+    FS_REQUIRE(nn > 0 && nf >= 0, FC_BAD_ARG, "n_node must be positive");
+    check_bsr(J->A, nn, nn, 3, 3, "A");
+    check_bsr(J->C1, nn, nf, 3, 3, "C1");
+    check_bsr(J->Q1, nn, nf, 3, 1, "Q1");
+    check_bsr(J->C2, nf, nn, 3, 3, "C2");
+    check_bsr(J->H, nf, nf, 3, 3, "H");
+    check_bsr(J->Q2, nf, nn, 1, 3, "Q2");
+    check_bsr(J->T, nf, nf, 1, 1, "T");
+    cudaStream_t s = c->s;
+    c->nn = nn; c->nf = nf;
+    c->nu = 3LL * nn; c->nt = 3LL * nf; c->n = c->nu + c->nt + nf;
+    auto up = [&](const fc_bsr &m) {
+      return upload_bsr(m.n_brows, m.n_bcols, m.br, m.bc, m.nnzb, m.d_row_ptr, m.d_col_idx, m.d_val, s);
+    };
+    c->A = up(J->A); c->C1 = up(J->C1); c->Q1 = up(J->Q1); c->C2 = up(J->C2);
+    c->H = up(J->H); c->Q2 = up(J->Q2); c->T = up(J->T);
+    for (auto &h : c->hier) h = Hierarchy();
+    c->pf = PrecData<float>();
+    c->pd = PrecData<double>();
+    build_hinv(c->H.view(), c->Hinv64, s);                                        // Alg. 1/3 line 1
+    c->S1 = build_s1(c->A.view(), c->C1.view(), c->C2.view(), c->Hinv64.p, s);   // Alg. 3 line 2
+    const int prec = c->opt.precision;
+    c->have[FC_TPU] = (c->opt.variants >> FC_TPU) & 1;
+    c->have[FC_TUP] = (c->opt.variants >> FC_TUP) & 1;
+    if (c->have[FC_TPU]) {
+      c->St = build_stilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), s);   // Alg. 1 line 3
+      amg_setup(c->hier[FC_H_TPU_U], copy_cast<double, double>(c->St.view(), s), 3, amg_params(c->opt, false), prec, s);
+      if (nf) amg_setup(c->hier[FC_H_TPU_P], copy_cast<double, double>(c->T.view(), s), 1, amg_params(c->opt, true), prec, s);
+    }
+    if (c->have[FC_TUP]) {
+      c->S2t = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s);  // Alg. 3 line 3
+      amg_setup(c->hier[FC_H_TUP_U], copy_cast<double, double>(c->S1.view(), s), 3, amg_params(c->opt, false), prec, s);
+      if (nf) amg_setup(c->hier[FC_H_TUP_P], copy_cast<double, double>(c->S2t.view(), s), 1, amg_params(c->opt, true), prec, s);
+    }
+    if (prec == FC_MIXED) prepare_prec<float>(*c, c->pf);
+    else prepare_prec<double>(*c, c->pd);
+    c->xk.alloc(c->n); c->rk.alloc(c->n);
+    FS_CUDA(cudaStreamSynchronize(s));
+    c->ready = true;
+    return FC_OK;
+  });
+}
+
+int fc_spmv(fc_ctx *c, const double *x, double *y) {
+  if (!c || !x || !y) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_setup has not completed");
+    jac_spmv<double>(*c, x, y);
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
+}
+
+int fc_apply_prec(fc_ctx *c, int variant, const double *w, double *v) {
+  if (!c || !w || !v || (variant != FC_TPU && variant != FC_TUP)) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready && c->have[variant], FC_NOT_SETUP, "variant not built by fc_setup");
+    if (c->opt.precision == FC_MIXED) {
+      cast(c->pf.w.p, w, c->n, c->s);
+      apply_prec<float>(*c, c->pf, variant, c->pf.w.p, c->pf.out.p);
+      cast(v, c->pf.out.p, c->n, c->s);
+    } else {
+      apply_prec<double>(*c, c->pd, variant, w, v);
+    }
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
+}
+
+int fc_solve(fc_ctx *c, int variant, const double *b, double *x, double tol, int maxit, int *iters,
+             double *relres) {
+  if (!c || !b || !x || (variant != FC_TPU && variant != FC_TUP) || maxit < 1 || maxit > 4000 || !(tol > 0))
+    return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready && c->have[variant], FC_NOT_SETUP, "variant not built by fc_setup");
+    int rc = c->opt.precision == FC_MIXED ? solve_impl<float>(*c, variant, b, x, tol, maxit, iters, relres)
+                                          : solve_impl<double>(*c, variant, b, x, tol, maxit, iters, relres);
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return rc;
+  });
+}
+
+int fc_solve_host(fc_ctx *c, int variant, const double *hb, double *hx, double tol, int maxit, int *iters,
+                  double *relres) {
+  if (!c || !hb || !hx) return FC_BAD_ARG;
+  int rc = run(c, [&]() {
+    FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_setup has not completed");
+    c->bk.ensure(c->n);
+    c->hx.ensure(c->n);
+    FS_CUDA(cudaMemcpyAsync(c->bk.p, hb, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->s));
+    return FC_OK;
+  });
+  if (rc != FC_OK) return rc;
+  rc = fc_solve(c, variant, c->bk.p, c->hx.p, tol, maxit, iters, relres);
+  int rc2 = run(c, [&]() {
+    FS_CUDA(cudaMemcpyAsync(hx, c->hx.p, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->s));
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
+  return rc != FC_OK ? rc : rc2;
+}
+
+int fc_num_levels(fc_ctx *c, int hier, int *levels) {
+  if (!c || !levels || hier < 0 || hier > 3) return FC_BAD_ARG;
+  *levels = c->hier[hier].built ? c->hier[hier].levels() : 0;
+  return FC_OK;
+}
+
+int fc_get_bsr(fc_ctx *c, int kind, int hier, int level, int32_t *nbr, int32_t *nbc, int32_t *br, int32_t *bc,
+               int64_t *nnzb, int32_t *hrp, int32_t *hci, double *hval) {
+  if (!c) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_setup has not completed");
+    const Bsr<double> *m = nullptr;
+    if (kind == FC_M_S1) m = &c->S1;
+    else if (kind == FC_M_STILDE) m = &c->St;
+    else if (kind == FC_M_S2TILDE) m = &c->S2t;
+    else if (kind == FC_M_LEVEL || kind == FC_M_PROLONG) {
+      FS_REQUIRE(hier >= 0 && hier < 4 && c->hier[hier].built, FC_BAD_ARG, "hierarchy not built");
+      FS_REQUIRE(level >= 0 && level < c->hier[hier].levels(), FC_BAD_ARG, "level out of range");
+      const LevelSetup &L = c->hier[hier].lev[level];
+      m = kind == FC_M_LEVEL ? &L.S : &L.P;
+    } else {
+      throw Error(FC_BAD_ARG, "unknown matrix kind");
+    }
+    if (nbr) *nbr = m->nbr;
+    if (nbc) *nbc = m->nbc;
+    if (br) *br = m->br;
+    if (bc) *bc = m->bc;
+    if (nnzb) *nnzb = m->nnzb;
+    if (hrp || hci || hval) {
+      std::vector<int> rp, ci;
+      std::vector<double> val;
+      download_bsr(m->view(), rp, ci, val, c->s);
+      if (hrp) std::memcpy(hrp, rp.data(), sizeof(int) * rp.size());
+      if (hci && !ci.empty()) std::memcpy(hci, ci.data(), sizeof(int) * ci.size());
+      if (hval && !val.empty()) std::memcpy(hval, val.data(), sizeof(double) * val.size());
+    }
+    return FC_OK;
+  });
+}
+
+int fc_get_aggregates(fc_ctx *c, int hier, int level, int32_t *hagg, double *hlam) {
+  if (!c || hier < 0 || hier > 3) return FC_BAD_ARG;
+  return run(c, [&]() {
+    Hierarchy &H = c->hier[hier];
+    FS_REQUIRE(H.built && level >= 0 && level < H.levels(), FC_BAD_ARG, "level out of range");
+    const LevelSetup &L = H.lev[level];
+    if (hlam) *hlam = L.lam;
+    if (hagg) {
+      if (L.agg.p) {
+        FS_CUDA(cudaMemcpyAsync(hagg, L.agg.p, sizeof(int) * L.nb, cudaMemcpyDeviceToHost, c->s));
+      } else {
+        for (int i = 0; i < L.nb; i++) hagg[i] = -1;
+      }
+      FS_CUDA(cudaStreamSynchronize(c->s));
+    }
+    return FC_OK;
+  });
+}
+
+int fc_vcycle(fc_ctx *c, int hier, const double *f, double *x) {
+  if (!c || !f || !x || hier < 0 || hier > 3) return FC_BAD_ARG;
+  return run(c, [&]() {
+    Hierarchy &H = c->hier[hier];
+    FS_REQUIRE(H.built, FC_NOT_SETUP, "hierarchy not built");
+    const int64_t n = (int64_t)H.lev[0].nb * H.B;
+    if (c->opt.precision == FC_MIXED) {
+      DBuf<float> f32(n), x32(n);
+      cast(f32.p, f, n, c->s);
+      amg_vcycle<float>(H, f32.p, x32.p, c->s);
+      cast(x, x32.p, n, c->s);
+      FS_CUDA(cudaStreamSynchronize(c->s));
+    } else {
+      amg_vcycle<double>(H, f, x, c->s);
+      FS_CUDA(cudaStreamSynchronize(c->s));
+    }
+    return FC_OK;
+  });
+}
+
+int fc_get_fixed_stress(fc_ctx *c, double *hsk) {
+  if (!c || !hsk) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready && c->have[FC_TUP], FC_NOT_SETUP, "t-u-p not built");
+    if (c->nf)
+      FS_CUDA(cudaMemcpyAsync(hsk, c->SK.p, sizeof(double) * c->nf, cudaMemcpyDeviceToHost, c->s));
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
+}
+
+void fc_destroy(fc_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->s);
+  delete c;
+}
+
+const char *fc_strerror(int st) {
+  switch (st) {
+    case FC_OK: return "ok";
+    case FC_NOT_CONVERGED: return "not converged within maxit";
+    case FC_BREAKDOWN: return "Krylov breakdown before reaching the tolerance";
+    case FC_SINGULAR_BLOCK: return "singular block";
+    case FC_NAN: return "NaN or Inf encountered";
+    case FC_BAD_ARG: return "invalid argument";
+    case FC_CUDA_ERROR: return "CUDA runtime error";
+    case FC_OOM: return "out of device memory";
+    case FC_INTERNAL: return "internal capacity limit reached";
+    case FC_NOT_SETUP: return "setup has not built what the call needs";
+    default: return "unknown status";
+  }
+}
+
+const char *fc_last_error(fc_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

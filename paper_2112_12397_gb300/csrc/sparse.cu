@@ -1,0 +1,346 @@
+// Setup-phase sparse kernels: transpose, block SpGEMM, sparse add.
+#include "sparse.cuh"
+
+namespace fs {
+
+// ============================================================ transpose
+namespace {
+__global__ void k_count_cols(const int *ci, int64_t nnz, int *cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(cnt + ci[e], 1);
+}
+
+// scatter entries (row i, col j) to row j of the transpose; order inside a
+// transposed row is fixed afterwards by k_sort_rows
+__global__ void k_scatter_t(BsrView<double> A, const int *rpT, int *cursor, int *ciT, int64_t *src) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.nbr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int e = A.rp[i]; e < A.rp[i + 1]; e++) {
+      int j = A.ci[e];
+      int pos = rpT[j] + atomicAdd(cursor + j, 1);
+      ciT[pos] = (int)i;
+      src[pos] = e;
+    }
+  }
+}
+
+// insertion sort of each row by column, carrying the source index
+__global__ void k_sort_rows(int nr, const int *rp, int *ci, int64_t *src) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int s = rp[i], e = rp[i + 1];
+    for (int a = s + 1; a < e; a++) {
+      int key = ci[a];
+      int64_t ks = src[a];
+      int b = a - 1;
+      while (b >= s && ci[b] > key) {
+        ci[b + 1] = ci[b];
+        src[b + 1] = src[b];
+        b--;
+      }
+      ci[b + 1] = key;
+      src[b + 1] = ks;
+    }
+  }
+}
+
+__global__ void k_gather_t(int64_t nnz, const int64_t *src, const double *val, int br, int bc,
+                           double *valT) {
+  int bs = br * bc;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double *v = val + src[p] * bs;
+    double *o = valT + p * bs;
+    // block (br x bc) -> (bc x br)
+    for (int r = 0; r < br; r++)
+      for (int c = 0; c < bc; c++) o[c * br + r] = v[r * bc + c];
+  }
+}
+}  // namespace
+
+Bsr<double> transpose(const BsrView<double> &A, cudaStream_t s) {
+  Bsr<double> T;
+  T.shape(A.nbc, A.nbr, A.bc, A.br);
+  T.rp.alloc(A.nbc + 1);
+  DBuf<int> cnt(A.nbc + 1);
+  FS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (A.nbc + 1), s));
+  if (A.nnzb > 0) {
+    k_count_cols<<<blocks_for(A.nnzb, 256, kSMs * 8), 256, 0, s>>>(A.ci, A.nnzb, cnt.p);
+    FS_LAUNCHED();
+  }
+  int64_t nnz = exclusive_scan(cnt.p, T.rp.p, A.nbc, s);
+  T.nnzb = nnz;
+  T.ci.alloc(nnz);
+  T.val.alloc(nnz * A.br * A.bc);
+  if (nnz == 0) return T;
+  DBuf<int64_t> src(nnz);
+  FS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (A.nbc + 1), s));
+  k_scatter_t<<<blocks_for(A.nbr, 128, kSMs * 8), 128, 0, s>>>(A, T.rp.p, cnt.p, T.ci.p, src.p);
+  FS_LAUNCHED();
+  k_sort_rows<<<blocks_for(A.nbc, 128, kSMs * 8), 128, 0, s>>>(A.nbc, T.rp.p, T.ci.p, src.p);
+  FS_LAUNCHED();
+  k_gather_t<<<blocks_for(nnz, 256, kSMs * 8), 256, 0, s>>>(nnz, src.p, A.val, A.br, A.bc, T.val.p);
+  FS_LAUNCHED();
+  FS_CUDA(cudaStreamSynchronize(s));
+  return T;
+}
+
+// ============================================================ SpGEMM
+namespace {
+constexpr int kHashCap = 1024;     // per-warp hash slots (power of two)
+constexpr int kListCap = 768;      // unique columns a row may hold
+constexpr int kWarpsPerBlock = 4;
+
+struct WarpHash {
+  int *keys;   // kHashCap
+  int *list;   // kListCap
+  int *count;  // 1
+};
+
+__device__ inline void hash_clear(WarpHash &h, int lane) {
+  for (int k = lane; k < kHashCap; k += 32) h.keys[k] = -1;
+  if (lane == 0) *h.count = 0;
+  __syncwarp();
+}
+
+// returns false on overflow
+__device__ inline bool hash_insert(WarpHash &h, int key) {
+  unsigned slot = ((unsigned)key * 2654435761u) & (kHashCap - 1);
+  for (int probe = 0; probe < kHashCap; probe++) {
+    int old = atomicCAS(h.keys + slot, -1, key);
+    if (old == -1) {
+      int pos = atomicAdd(h.count, 1);
+      if (pos >= kListCap) return false;
+      h.list[pos] = key;
+      return true;
+    }
+    if (old == key) return true;
+    slot = (slot + 1) & (kHashCap - 1);
+  }
+  return false;
+}
+
+// pass 0: count unique columns per row; pass 1: write sorted columns
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_spgemm_symbolic(BsrView<double> A, BsrView<double> B, int pass, int *cnt, const int *rpC,
+                      int *ciC, int *overflow) {
+  __shared__ int s_keys[kWarpsPerBlock][kHashCap];
+  __shared__ int s_list[kWarpsPerBlock][kListCap];
+  __shared__ int s_cnt[kWarpsPerBlock];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  WarpHash h{s_keys[wid], s_list[wid], &s_cnt[wid]};
+  const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
+  for (int64_t i = blockIdx.x * (int64_t)kWarpsPerBlock + wid; i < A.nbr; i += nwarps) {
+    hash_clear(h, lane);
+    bool ok = true;
+    for (int e = A.rp[i]; e < A.rp[i + 1]; e++) {
+      int k = A.ci[e];
+      for (int f = B.rp[k] + lane; f < B.rp[k + 1]; f += 32) ok &= hash_insert(h, B.ci[f]);
+    }
+    __syncwarp();
+    ok = __all_sync(0xffffffffu, ok);
+    int u = *h.count;
+    if (!ok || u > kListCap) {
+      if (lane == 0) atomicExch(overflow, 1);
+      __syncwarp();
+      continue;
+    }
+    if (pass == 0) {
+      if (lane == 0) cnt[i] = u;
+    } else {
+      int base = rpC[i];
+      for (int a = lane; a < u; a += 32) {
+        int key = h.list[a];
+        int rank = 0;
+        for (int b = 0; b < u; b++) rank += (h.list[b] < key);
+        ciC[base + rank] = key;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int BR, int BK, int BC>
+__global__ void __launch_bounds__(128)
+    k_spgemm_numeric(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC,
+                     double *valC) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid; i < A.nbr; i += nwarps) {
+    const int cs = rpC[i], cn = rpC[i + 1] - cs;
+    for (int e = A.rp[i]; e < A.rp[i + 1]; e++) {
+      const int k = A.ci[e];
+      double a[BR * BK];
+#pragma unroll
+      for (int q = 0; q < BR * BK; q++) a[q] = A.val[(int64_t)e * BR * BK + q];
+      for (int f = B.rp[k] + lane; f < B.rp[k + 1]; f += 32) {
+        const int j = B.ci[f];
+        const int p = find_sorted(ciC + cs, cn, j);
+        if (p < 0) continue;   // cannot happen: the symbolic pass saw every j
+        const double *b = B.val + (int64_t)f * BK * BC;
+        double *c = valC + (int64_t)(cs + p) * BR * BC;
+#pragma unroll
+        for (int r = 0; r < BR; r++)
+#pragma unroll
+          for (int cc = 0; cc < BC; cc++) {
+            double s = 0.0;
+#pragma unroll
+            for (int t = 0; t < BK; t++) s += a[r * BK + t] * b[t * BC + cc];
+            c[r * BC + cc] += s;
+          }
+      }
+      __syncwarp();
+    }
+  }
+}
+}  // namespace
+
+Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s) {
+  FS_REQUIRE(A.bc == B.br && A.nbc == B.nbr, FC_BAD_ARG, "spgemm: shape mismatch");
+  Bsr<double> C;
+  C.shape(A.nbr, B.nbc, A.br, B.bc);
+  C.rp.alloc(A.nbr + 1);
+  DBuf<int> cnt(A.nbr + 1), ovf(1);
+  FS_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), s));
+  FS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (A.nbr + 1), s));
+  const int grid = kSMs * 8;
+  if (A.nbr > 0) {
+    k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 0, cnt.p, nullptr, nullptr, ovf.p);
+    FS_LAUNCHED();
+  }
+  int64_t nnz = exclusive_scan(cnt.p, C.rp.p, A.nbr, s);
+  int hovf = 0;
+  FS_CUDA(cudaMemcpy(&hovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
+  FS_REQUIRE(!hovf, FC_INTERNAL, "spgemm: a product row has more than 768 block columns");
+  C.nnzb = nnz;
+  C.ci.alloc(nnz);
+  C.val.alloc(nnz * C.br * C.bc);
+  if (nnz == 0) return C;
+  k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 1, nullptr, C.rp.p, C.ci.p, ovf.p);
+  FS_LAUNCHED();
+  FS_CUDA(cudaMemsetAsync(C.val.p, 0, sizeof(double) * nnz * C.br * C.bc, s));
+  const int sh = A.br * 100 + A.bc * 10 + B.bc;
+  switch (sh) {
+    case 333: k_spgemm_numeric<3, 3, 3><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
+    case 313: k_spgemm_numeric<3, 1, 3><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
+    case 111: k_spgemm_numeric<1, 1, 1><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
+    case 331: k_spgemm_numeric<3, 3, 1><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
+    case 133: k_spgemm_numeric<1, 3, 3><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
+    default: throw Error(FC_BAD_ARG, "spgemm: unsupported block shapes");
+  }
+  FS_LAUNCHED();
+  FS_CUDA(cudaStreamSynchronize(s));
+  return C;
+}
+
+// ============================================================ sparse add
+namespace {
+__global__ void k_spadd(BsrView<double> A, BsrView<double> B, double alpha, double beta, int pass,
+                        int *cnt, const int *rpC, int *ciC, double *valC) {
+  const int bs = A.br * A.bc;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.nbr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int a = A.rp[i], ae = A.rp[i + 1], b = B.rp[i], be = B.rp[i + 1];
+    int n = 0;
+    int o = pass ? rpC[i] : 0;
+    while (a < ae || b < be) {
+      int ca = a < ae ? A.ci[a] : INT32_MAX;
+      int cb = b < be ? B.ci[b] : INT32_MAX;
+      int c = ca < cb ? ca : cb;
+      if (pass) {
+        ciC[o + n] = c;
+        double *dst = valC + (int64_t)(o + n) * bs;
+        for (int q = 0; q < bs; q++) {
+          double v = 0.0;
+          if (ca == c) v += alpha * A.val[(int64_t)a * bs + q];
+          if (cb == c) v += beta * B.val[(int64_t)b * bs + q];
+          dst[q] = v;
+        }
+      }
+      if (ca == c) a++;
+      if (cb == c) b++;
+      n++;
+    }
+    if (!pass) cnt[i] = n;
+  }
+}
+}  // namespace
+
+Bsr<double> spadd(const BsrView<double> &A, const BsrView<double> &B, double alpha, double beta,
+                  cudaStream_t s) {
+  FS_REQUIRE(A.nbr == B.nbr && A.nbc == B.nbc && A.br == B.br && A.bc == B.bc, FC_BAD_ARG,
+             "spadd: shape mismatch");
+  Bsr<double> C;
+  C.shape(A.nbr, A.nbc, A.br, A.bc);
+  C.rp.alloc(A.nbr + 1);
+  DBuf<int> cnt(A.nbr + 1);
+  const int grid = blocks_for(A.nbr, 128, kSMs * 8);
+  if (A.nbr > 0) {
+    k_spadd<<<grid, 128, 0, s>>>(A, B, alpha, beta, 0, cnt.p, nullptr, nullptr, nullptr);
+    FS_LAUNCHED();
+  }
+  int64_t nnz = exclusive_scan(cnt.p, C.rp.p, A.nbr, s);
+  C.nnzb = nnz;
+  C.ci.alloc(nnz);
+  C.val.alloc(nnz * C.br * C.bc);
+  if (nnz) {
+    k_spadd<<<grid, 128, 0, s>>>(A, B, alpha, beta, 1, nullptr, C.rp.p, C.ci.p, C.val.p);
+    FS_LAUNCHED();
+  }
+  FS_CUDA(cudaStreamSynchronize(s));
+  return C;
+}
+
+// ============================================================ copies
+namespace {
+template <typename TO, typename TI>
+__global__ void k_cast_vals(TO *o, const TI *i, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    o[k] = (TO)i[k];
+}
+}  // namespace
+
+template <typename TO, typename TI>
+Bsr<TO> copy_cast(const BsrView<TI> &A, cudaStream_t s) {
+  Bsr<TO> C;
+  C.shape(A.nbr, A.nbc, A.br, A.bc);
+  C.nnzb = A.nnzb;
+  C.rp.alloc(A.nbr + 1);
+  C.ci.alloc(A.nnzb);
+  C.val.alloc(A.nnzb * A.br * A.bc);
+  FS_CUDA(cudaMemcpyAsync(C.rp.p, A.rp, sizeof(int) * (A.nbr + 1), cudaMemcpyDeviceToDevice, s));
+  if (A.nnzb) {
+    FS_CUDA(cudaMemcpyAsync(C.ci.p, A.ci, sizeof(int) * A.nnzb, cudaMemcpyDeviceToDevice, s));
+    int64_t n = A.nnzb * A.br * A.bc;
+    k_cast_vals<TO, TI><<<blocks_for(n, 256, kSMs * 16), 256, 0, s>>>(C.val.p, A.val, n);
+    FS_LAUNCHED();
+  }
+  return C;
+}
+template Bsr<float> copy_cast<float, double>(const BsrView<double> &, cudaStream_t);
+template Bsr<double> copy_cast<double, double>(const BsrView<double> &, cudaStream_t);
+
+Bsr<double> upload_bsr(int nbr, int nbc, int br, int bc, int64_t nnzb, const int *rp_dev,
+                       const int *ci_dev, const double *val_dev, cudaStream_t s) {
+  BsrView<double> v;
+  v.nbr = nbr; v.nbc = nbc; v.br = br; v.bc = bc; v.nnzb = nnzb;
+  v.rp = rp_dev; v.ci = ci_dev; v.val = val_dev;
+  return copy_cast<double, double>(v, s);
+}
+
+void download_bsr(const BsrView<double> &A, std::vector<int> &rp, std::vector<int> &ci,
+                  std::vector<double> &val, cudaStream_t s) {
+  rp.resize(A.nbr + 1);
+  ci.resize(A.nnzb);
+  val.resize(A.nnzb * A.br * A.bc);
+  FS_CUDA(cudaMemcpyAsync(rp.data(), A.rp, sizeof(int) * (A.nbr + 1), cudaMemcpyDeviceToHost, s));
+  if (A.nnzb) {
+    FS_CUDA(cudaMemcpyAsync(ci.data(), A.ci, sizeof(int) * A.nnzb, cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaMemcpyAsync(val.data(), A.val, sizeof(double) * val.size(), cudaMemcpyDeviceToHost, s));
+  }
+  FS_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace fs

@@ -1,0 +1,46 @@
+// Sparse matrix construction on the device (setup phase, double precision):
+// transpose, block SpGEMM (hash symbolic + Gustavson numeric), sparse add.
+#pragma once
+
+#include "common.cuh"
+
+namespace fs {
+
+// Position of `col` in the sorted column list ci[0..n), or -1.
+__device__ inline int find_sorted(const int *ci, int n, int col) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int c = ci[mid];
+    if (c == col) return mid;
+    if (c < col) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// A^T with transposed blocks; rows of the result sorted by column.
+Bsr<double> transpose(const BsrView<double> &A, cudaStream_t s);
+
+// C = A B for block shapes (A.br x A.bc) (B.br x B.bc), A.bc == B.br.
+// Supported shapes: 3x3*3x3, 3x1*1x3, 1x1*1x1, 3x3*3x1, 1x3*3x3.
+// Rows of C sorted; entries that cancel to zero are kept.
+Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s);
+
+// C = alpha A + beta B (same shape and block size), rows sorted.
+Bsr<double> spadd(const BsrView<double> &A, const BsrView<double> &B, double alpha, double beta,
+                  cudaStream_t s);
+
+// Deep copy of a BSR view into an owned matrix (same value type).
+template <typename TO, typename TI>
+Bsr<TO> copy_cast(const BsrView<TI> &A, cudaStream_t s);
+
+// Upload a host BSR (double) into an owned device matrix.
+Bsr<double> upload_bsr(int nbr, int nbc, int br, int bc, int64_t nnzb, const int *rp_dev,
+                       const int *ci_dev, const double *val_dev, cudaStream_t s);
+
+// Download to host vectors.
+void download_bsr(const BsrView<double> &A, std::vector<int> &rp, std::vector<int> &ci,
+                  std::vector<double> &val, cudaStream_t s);
+
+}  // namespace fs

@@ -1,0 +1,170 @@
+// Block sparse matrix-vector products with fused epilogues.
+//
+// One group of G lanes owns one block row.  The row's values are streamed
+// as a flat, contiguous array of nnz_row * BR * BC scalars, so consecutive
+// lanes read consecutive addresses (coalesced) whatever the block shape; each
+// lane adds value * x[col * BC + c] into the partial sum of its block-row
+// component, the group reduces with shuffles, and lane 0 hands the BR sums to
+// an epilogue that finishes the row (axpby, Chebyshev update, H~^-1 solve).
+#pragma once
+
+#include "common.cuh"
+
+namespace fs {
+
+template <int G, typename T>
+__device__ inline T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+  return v;
+}
+
+template <int BR, int BC, int G, typename TA, typename TX, typename Epi>
+__global__ void __launch_bounds__(256) k_bsr_spmv(BsrView<TA> A, const TX *__restrict__ x, Epi epi) {
+  constexpr int BS = BR * BC;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const bool valid = row < A.nbr;
+  TA acc[BR];
+#pragma unroll
+  for (int q = 0; q < BR; q++) acc[q] = TA(0);
+  if (valid) {
+    const int s = __ldg(A.rp + row), e = __ldg(A.rp + row + 1);
+    const int nel = (e - s) * BS;
+    const TA *__restrict__ v = A.val + (int64_t)s * BS;
+    const int *__restrict__ ci = A.ci + s;
+    for (int j = lane; j < nel; j += G) {
+      const int b = j / BS;
+      const int rc = j - b * BS;
+      const int r = rc / BC;
+      const int c = rc - r * BC;
+      const int col = __ldg(ci + b);
+      const TA prod = __ldg(v + j) * (TA)__ldg(x + (int64_t)col * BC + c);
+#pragma unroll
+      for (int q = 0; q < BR; q++)
+        if (q == r) acc[q] += prod;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < BR; q++) acc[q] = group_sum<G>(acc[q]);
+  if (valid && lane == 0) epi(row, acc);
+}
+
+// y[row] = alpha * (A x)[row] + beta * z[row]   (z may alias y; z unused if beta == 0)
+template <int BR, typename TA, typename TY, typename TZ>
+struct EpiAxpby {
+  TY *y;
+  const TZ *z;
+  TA alpha, beta;
+  __device__ void operator()(int64_t row, const TA *acc) const {
+#pragma unroll
+    for (int q = 0; q < BR; q++) {
+      TA v = alpha * acc[q];
+      if (beta != TA(0)) v += beta * (TA)z[row * BR + q];
+      y[row * BR + q] = (TY)v;
+    }
+  }
+};
+
+// y[row] = Dinv[row] * (A x)[row]   (power iteration on D^-1 S)
+template <int BR, typename TA>
+struct EpiBlockDiag {
+  TA *y;
+  const TA *Dinv;
+  __device__ void operator()(int64_t row, const TA *acc) const {
+    const TA *D = Dinv + row * BR * BR;
+#pragma unroll
+    for (int a = 0; a < BR; a++) {
+      TA s = 0;
+#pragma unroll
+      for (int b = 0; b < BR; b++) s += D[a * BR + b] * acc[b];
+      y[row * BR + a] = s;
+    }
+  }
+};
+
+// Chebyshev step (Saad, Alg. 12.1) fused with the residual:
+//   r = f - (S x_in)[row];  d = cd * d + cr * Dinv r;  x_out = x_in + d
+template <int BR, typename TA>
+struct EpiCheb {
+  const TA *f;
+  const TA *x_in;
+  TA *x_out;
+  TA *d;
+  const TA *Dinv;
+  TA cd, cr;
+  __device__ void operator()(int64_t row, const TA *acc) const {
+    TA r[BR];
+#pragma unroll
+    for (int q = 0; q < BR; q++) r[q] = f[row * BR + q] - acc[q];
+    const TA *D = Dinv + row * BR * BR;
+#pragma unroll
+    for (int a = 0; a < BR; a++) {
+      TA s = 0;
+#pragma unroll
+      for (int b = 0; b < BR; b++) s += D[a * BR + b] * r[b];
+      TA dn = cr * s;
+      if (cd != TA(0)) dn += cd * d[row * BR + a];
+      d[row * BR + a] = dn;
+      x_out[row * BR + a] = x_in[row * BR + a] + dn;
+    }
+  }
+};
+
+// Alg. 2 line 8 / Alg. 4 line 10 fused with the C2 product:
+//   v_t[row] = -t_t[row] + Hinv[row] * (C2 v_u)[row]
+template <typename TA>
+struct EpiHinvUpdate {
+  TA *v_t;
+  const TA *t_t;
+  const TA *Hinv;
+  __device__ void operator()(int64_t row, const TA *acc) const {
+    const TA *Hi = Hinv + row * 9;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      TA s = 0;
+#pragma unroll
+      for (int b = 0; b < 3; b++) s += Hi[a * 3 + b] * acc[b];
+      v_t[row * 3 + a] = -t_t[row * 3 + a] + s;
+    }
+  }
+};
+
+inline int lanes_for(int64_t nnzb, int nbr, int bs) {
+  double per = nbr > 0 ? (double)nnzb * bs / nbr : 0.0;
+  if (per > 48) return 32;
+  if (per > 24) return 16;
+  if (per > 10) return 8;
+  return 4;
+}
+
+template <int BR, int BC, int G, typename TA, typename TX, typename Epi>
+inline void spmv_g(const BsrView<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
+  const int threads = 256;
+  const int64_t nthreads = (int64_t)A.nbr * G;
+  const int64_t blocks = (nthreads + threads - 1) / threads;
+  k_bsr_spmv<BR, BC, G, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi);
+  FS_LAUNCHED();
+}
+
+// Launch with a lane count chosen from the mean scalar entries per row.
+template <int BR, int BC, typename TA, typename TX, typename Epi>
+inline void spmv(const BsrView<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
+  if (A.nbr <= 0) return;
+  switch (lanes_for(A.nnzb, A.nbr, BR * BC)) {
+    case 32: spmv_g<BR, BC, 32>(A, x, epi, s); break;
+    case 16: spmv_g<BR, BC, 16>(A, x, epi, s); break;
+    case 8: spmv_g<BR, BC, 8>(A, x, epi, s); break;
+    default: spmv_g<BR, BC, 4>(A, x, epi, s); break;
+  }
+}
+
+// y = alpha A x + beta z
+template <int BR, int BC, typename TA, typename TX, typename TY, typename TZ>
+inline void spmv_axpby(const BsrView<TA> &A, const TX *x, TY *y, double alpha, double beta,
+                       const TZ *z, cudaStream_t s) {
+  EpiAxpby<BR, TA, TY, TZ> e{y, z, (TA)alpha, (TA)beta};
+  spmv<BR, BC>(A, x, e, s);
+}
+
+}  // namespace fs
