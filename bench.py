@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark: time to solve the block-preconditioned contact/flow Jacobian to
+relative residual 1e-8 on one GB300, FP32-preconditioner (mixed) form against
+the all-FP64 form, plus the finest-level smoother's HBM bandwidth.
+
+One step = one system solution as the paper counts it (Sec. 4: "CPU time for
+a single system solution"): fc_setup (H~^-1, S1 / S~, fixed-stress S~2, AMG
+hierarchies; Alg. 1 / Alg. 3) followed by fc_solve (right-preconditioned
+FGMRES-CGS2 with Alg. 2 / Alg. 4 to relative residual 1e-8), on a Jacobian
+already resident in HBM.  The e2e figure repeats the step through the public
+C-ABI with host buffers: the Jacobian blocks and b are copied from pinned host
+memory, the solution is copied back.
+
+Workload (default): 128^3 unit-cube grid, ten seeded fracture rectangles,
+60/30/10 stick/slip/open, ~6.7M unknowns; synthetic seeded data standing in
+for the paper's private meshes.  Matrices are several GB, far above the
+129 MB L2, so no flush is needed between steps.
+
+--impl reference times the CPU oracle (tests' reference implementation) on a
+bounded sample of the same workload family and scales it to the full size.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solve s to rel-res 1e-8 (FP32-AMG vs FP64) at 1 GB300; V-cycle HBM GB/s % peak"
+WORKLOADS = {
+    "rects128": "128^3 grid, 10 seeded fracture rectangles, 60/30/10 stick/slip/open",
+    "planes64": "64^3 grid, three central fracture planes, 60/30/10 stick/slip/open",
+    "network96": "96^3 grid, fracture planes every 8 cells, 50/40/10 stick/slip/open",
+    "tiny8": "8^3 grid, one fracture plane, all stick",
+}
+
+
+# unknowns of each full workload (seed 0), known from the generator
+FULL_UNKNOWNS = {"rects128": 6709355, "planes64": 911640, "network96": 4995648, "tiny8": 2686}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rects128", choices=sorted(WORKLOADS))
+    ap.add_argument("--variant", default="tup", choices=["tup", "tpu"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--maxit", type=int, default=600)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-n", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import fracgen
+from oracle import sparse as osp
+from oracle.precond import BlockPreconditioner
+from oracle.fgmres import fgmres
+P = fracgen.generate({workload!r}, N={n})
+J = osp.jacobian(P)
+t0 = time.perf_counter()
+M = BlockPreconditioner(P, {variant!r})
+t1 = time.perf_counter()
+r = fgmres(lambda v: J @ v, M, P.b, {tol!r}, {maxit})
+t2 = time.perf_counter()
+print(json.dumps(dict(n=P.n, setup=t1 - t0, solve=t2 - t1, iters=r.iters, relres=r.relres)))
+"""
+
+
+def run_oracle_sample(workload, n_cells, variant, tol, maxit):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = ORACLE_SNIPPET.format(root=ROOT, workload=workload, n=n_cells, variant=variant, tol=tol, maxit=maxit)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(args, n_full):
+    s = run_oracle_sample(args.workload, args.cpu_sample_n, args.variant, args.tol, args.maxit)
+    t = s["setup"] + s["solve"]
+    scale = n_full / s["n"]
+    return {"value": t * scale, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle {args.variant} setup+solve of the same workload family at "
+                       f"{args.cpu_sample_n}^3 ({s['n']} unknowns, {s['iters']} iters, "
+                       f"{t:.2f} s) scaled linearly by unknowns to {n_full}")}
+
+
+# ------------------------------------------------------------------ reference arm
+def reference(args, rank):
+    if rank != 0:
+        return
+    import fracgen
+    fracgen.build()
+    n_full = FULL_UNKNOWNS[args.workload]
+    times = []
+    last = None
+    for k in range(args.warmup + args.steps):
+        s = run_oracle_sample(args.workload, args.cpu_sample_n, args.variant, args.tol, args.maxit)
+        last = s
+        if k >= args.warmup:
+            times.append((s["setup"] + s["solve"]) * n_full / s["n"])
+    v = statistics.mean(times)
+    sample = (f"oracle {args.variant} setup+solve at {args.cpu_sample_n}^3 ({last['n']} unknowns, "
+              f"{last['iters']} iters) per step, scaled linearly by unknowns to {n_full}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "variant": args.variant},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ our arm
+def ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import fracgen
+    import paper_2112_12397_gb300 as fs
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    fracgen.build()
+    P = fracgen.generate(args.workload, seed=rank)
+    blocks = fs.device_blocks(P)
+    b = torch.from_numpy(P.b).cuda()
+    x = torch.zeros_like(b)
+    variant_bit = 1 << fs.VARIANTS[args.variant]
+
+    def make_ctx(prec):
+        ctx = fs.Context(fs.default_options(precision=prec, variants=variant_bit))
+        return ctx
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+
+    def run_steps(ctx, nsteps, record):
+        setup_ms, solve_ms, its, rrs = [], [], [], []
+        for _ in range(nsteps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            ctx.setup(blocks, P.n_node, P.n_face)
+            e1.record(stream)
+            rc, it, rr = ctx.solve(args.variant, b, x, args.tol, args.maxit, allow_fail=True)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            if record:
+                setup_ms.append(e0.elapsed_time(e1))
+                solve_ms.append(e1.elapsed_time(e2))
+                its.append(it)
+                rrs.append(rr)
+        return setup_ms, solve_ms, its, rrs
+
+    ctx = make_ctx(args.precision)
+    run_steps(ctx, args.warmup, False)
+    peak, peak_kind = measured_peaks()
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    l0 = fs.launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    setup_ms, solve_ms, its, rrs = run_steps(ctx, args.steps, True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = fs.launch_count() - l0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    sm_launch, sm_ms, sm_bytes = ctx.kernel_stats(fs.FC_K_SMOOTH0)
+    jac = ctx.kernel_stats(fs.FC_K_JAC)
+    cgs = ctx.kernel_stats(fs.FC_K_CGS)
+    prec = ctx.kernel_stats(fs.FC_K_PREC)
+    ctx.profile(False)
+    x_mixed = x.cpu().numpy().copy()
+
+    # max over ranks
+    step_ms = total_ms / args.steps
+    if dist is not None:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    # FP64 form on the same workload for the FP32-vs-FP64 comparison
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        del ctx
+        torch.cuda.empty_cache()
+        c64 = make_ctx("fp64")
+        run_steps(c64, 1, False)
+        s64, v64, i64, r64 = run_steps(c64, args.fp64_steps, True)
+        x64 = x.cpu().numpy()
+        fp64 = {"setup_s": statistics.mean(s64) / 1e3, "solve_s": statistics.mean(v64) / 1e3,
+                "step_s": (statistics.mean(s64) + statistics.mean(v64)) / 1e3, "iters": i64[-1],
+                "relres": r64[-1],
+                "mixed_vs_fp64_rel_diff": float(np.linalg.norm(x_mixed - x64) / np.linalg.norm(x64))}
+        del c64
+        ctx = make_ctx(args.precision)
+
+    # end to end through the C-ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {}
+        h2d = 0
+        for name, t in blocks.items():
+            rp, ci, val = (a.cpu().pin_memory() for a in t[:3])
+            host[name] = (rp, ci, val) + tuple(t[3:])
+            h2d += sum(a.numel() * a.element_size() for a in (rp, ci, val))
+        hb = torch.from_numpy(P.b).pin_memory()
+        hx = torch.zeros_like(hb).pin_memory()
+        dev = {k: tuple(torch.empty_like(a, device="cuda") for a in v[:3]) + tuple(v[3:]) for k, v in host.items()}
+        h2d += hb.numel() * 8
+        d2h = hx.numel() * 8
+        times = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for name in host:
+                for dst, src in zip(dev[name][:3], host[name][:3]):
+                    dst.copy_(src, non_blocking=True)
+            ctx.setup(dev, P.n_node, P.n_face)
+            rc, it, rr = ctx.solve_host(args.variant, hb, hx, args.tol, args.maxit, allow_fail=True)
+            torch.cuda.synchronize()
+            if k > 0:
+                times.append(time.perf_counter() - t0)
+        e2e = {"value": statistics.mean(times), "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(args, P.n)
+        except Exception as e:  # noqa: BLE001
+            cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank != 0:
+        return
+    achieved = sm_bytes / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
+    roofline = {"bound": "hbm", "kernel": "fused Chebyshev step, finest level of the S1 hierarchy",
+                "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "launches": sm_launch, "avg_launch_ms": sm_ms / max(sm_launch, 1),
+                "alg_bytes_per_launch": sm_bytes / max(sm_launch, 1)}
+    mean_setup = statistics.mean(setup_ms) / 1e3
+    mean_solve = statistics.mean(solve_ms) / 1e3
+    out = {
+        "metric": METRIC, "value": step_ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "unknowns": P.n,
+                   "variant": args.variant, "precision": args.precision, "tol": args.tol,
+                   "l2": "matrices of several GB, larger than L2; no flush"},
+        "breakdown": {"setup_s": mean_setup, "solve_s": mean_solve, "iters": its[-1], "relres": rrs[-1],
+                      "prec_apply_ms": prec[1] / max(prec[0], 1), "jac_ms": jac[1] / max(jac[0], 1),
+                      "cgs_pass_ms": cgs[1] / max(cgs[0], 1),
+                      "smoother_share_of_solve": (sm_ms / (sum(solve_ms))) if solve_ms else None},
+        "fp64": fp64,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference(args, rank)
+    else:
+        ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -131,6 +131,11 @@ int fc_setup(fc_ctx *ctx, const fc_blocks *J);
 /* d_y = J d_x (Eq. JacSys), double, device vectors of length n. */
 int fc_spmv(fc_ctx *ctx, const double *d_x, double *d_y);
 
+/* d_r = d_b - J d_x (double, device vectors of length n, caller-owned) and
+ * *relres = ||d_r|| / ||d_b|| (||d_r|| when b = 0).  The reduction uses
+ * partial sums held by the context.  FC_NAN if the norm is not finite. */
+int fc_residual(fc_ctx *ctx, const double *d_b, const double *d_x, double *d_r, double *relres);
+
 /* d_v = M^-1 d_w: app_tpu (Alg. 2) for FC_TPU, app_tup (Alg. 4) for FC_TUP,
  * device vectors of length n. */
 int fc_apply_prec(fc_ctx *ctx, int variant, const double *d_w, double *d_v);
@@ -181,6 +186,26 @@ int fc_vcycle(fc_ctx *ctx, int hier, const double *d_f, double *d_x);
 
 /* The fixed-stress diagonal [S_K]_k of Eq. FS_algebraic to HOST (n_face). */
 int fc_get_fixed_stress(fc_ctx *ctx, double *h_sk);
+
+/* ---------------- measurement ---------------- */
+
+/* Kernels timed with CUDA events on the context's stream while profiling is
+ * on: FC_K_SMOOTH0 = one fused Chebyshev step on the finest level of the
+ * elasticity hierarchy (S1 or S~); FC_K_JAC = one product J z (all seven
+ * blocks); FC_K_CGS = one classical Gram-Schmidt pass (dots + update);
+ * FC_K_PREC = one preconditioner application.  (FC_K_VCYCLE is reserved.) */
+enum { FC_K_SMOOTH0 = 0, FC_K_JAC = 1, FC_K_CGS = 2, FC_K_VCYCLE = 3, FC_K_PREC = 4 };
+
+/* Turn event timing on (enable != 0) or off, clearing what was recorded. */
+int fc_profile(fc_ctx *ctx, int enable);
+
+/* Launches recorded for `kernel`, their summed duration in ms, and the sum of
+ * their algorithmic bytes (matrix values and indices plus each vector entry
+ * read or written once).  Synchronises on the recorded events. */
+int fc_kernel_stats(fc_ctx *ctx, int kernel, int64_t *launches, double *total_ms, double *bytes);
+
+/* Number of kernel launches this library has issued in the process. */
+unsigned long long fc_launch_count(void);
 
 void fc_destroy(fc_ctx *ctx);
 const char *fc_strerror(int status);

@@ -35,13 +35,15 @@ def htilde_blocks(P, Hs: sp.csr_matrix | None = None) -> np.ndarray:
 def htilde_inv(P, Hs=None) -> sp.csr_matrix:
     """H~^-1 as a block-diagonal sparse matrix (3x3 blocks)."""
     Hb = htilde_blocks(P, Hs)
+    if len(Hb) == 0:
+        return sp.csr_matrix((0, 0))
     det = np.linalg.det(Hb)
     scale = np.abs(Hb).reshape(len(Hb), -1).max(axis=1)
     bad = ~(np.abs(det) > 1e-300) | (np.abs(det) <= 1e-14 * np.maximum(scale, 1e-300) ** 3)
     if np.any(bad):
         raise SingularBlock(f"singular H~ block at faces {np.nonzero(bad)[0][:8]}")
     Hi = np.linalg.inv(Hb)
-    return sp.block_diag(list(Hi), format="csr") if len(Hi) else sp.csr_matrix((0, 0))
+    return sp.csr_matrix(sp.block_diag(list(Hi), format="csr"))
 
 
 def s1(P, blk=None) -> sp.csr_matrix:

@@ -24,9 +24,11 @@ FC_M_LEVEL, FC_M_PROLONG, FC_M_S1, FC_M_STILDE, FC_M_S2TILDE = range(5)
 VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP}
 
 # exported symbols declared by include/fracsolve.h
-SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_apply_prec", "fc_solve",
+SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_residual", "fc_apply_prec", "fc_solve",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
-           "fc_get_fixed_stress", "fc_destroy", "fc_strerror", "fc_last_error"]
+           "fc_get_fixed_stress", "fc_profile", "fc_kernel_stats", "fc_launch_count", "fc_destroy",
+           "fc_strerror", "fc_last_error"]
+FC_K_SMOOTH0, FC_K_JAC, FC_K_CGS, FC_K_VCYCLE, FC_K_PREC = range(5)
 
 
 class FcError(RuntimeError):
@@ -77,6 +79,7 @@ def load(build_if_missing: bool = False):
         "fc_create": (C.c_int, [C.POINTER(vp), C.POINTER(fc_options), vp]),
         "fc_setup": (C.c_int, [vp, C.POINTER(fc_blocks)]),
         "fc_spmv": (C.c_int, [vp, vp, vp]),
+        "fc_residual": (C.c_int, [vp, vp, vp, vp, pd]),
         "fc_apply_prec": (C.c_int, [vp, C.c_int, vp, vp]),
         "fc_solve": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
         "fc_solve_host": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
@@ -85,6 +88,9 @@ def load(build_if_missing: bool = False):
         "fc_get_aggregates": (C.c_int, [vp, C.c_int, C.c_int, vp, pd]),
         "fc_vcycle": (C.c_int, [vp, C.c_int, vp, vp]),
         "fc_get_fixed_stress": (C.c_int, [vp, vp]),
+        "fc_profile": (C.c_int, [vp, C.c_int]),
+        "fc_kernel_stats": (C.c_int, [vp, C.c_int, pi64, pd, pd]),
+        "fc_launch_count": (C.c_ulonglong, []),
         "fc_destroy": (None, [vp]),
         "fc_strerror": (C.c_char_p, [C.c_int]),
         "fc_last_error": (C.c_char_p, [vp]),
@@ -164,6 +170,11 @@ class Context:
     def spmv(self, x, y):
         self._check(self.lib.fc_spmv(self.h, _ptr(x), _ptr(y)), self.h)
 
+    def residual(self, b, x, r) -> float:
+        rr = C.c_double(0)
+        self._check(self.lib.fc_residual(self.h, _ptr(b), _ptr(x), _ptr(r), C.byref(rr)), self.h)
+        return rr.value
+
     def apply_prec(self, variant: str, w, v):
         self._check(self.lib.fc_apply_prec(self.h, VARIANTS[variant], _ptr(w), _ptr(v)), self.h)
 
@@ -213,10 +224,22 @@ class Context:
     def vcycle(self, hier: int, f, x):
         self._check(self.lib.fc_vcycle(self.h, hier, _ptr(f), _ptr(x)), self.h)
 
+    def profile(self, enable: bool = True):
+        self._check(self.lib.fc_profile(self.h, 1 if enable else 0), self.h)
+
+    def kernel_stats(self, kernel: int):
+        n, ms, b = C.c_int64(0), C.c_double(0), C.c_double(0)
+        self._check(self.lib.fc_kernel_stats(self.h, kernel, C.byref(n), C.byref(ms), C.byref(b)), self.h)
+        return n.value, ms.value, b.value
+
     def fixed_stress(self) -> np.ndarray:
         out = np.zeros(max(self.n_face, 1))
         self._check(self.lib.fc_get_fixed_stress(self.h, C.c_void_p(out.ctypes.data)), self.h)
         return out[:self.n_face]
+
+
+def launch_count() -> int:
+    return int(load().fc_launch_count())
 
 
 def device_blocks(problem, device="cuda"):

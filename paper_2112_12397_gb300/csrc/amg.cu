@@ -589,9 +589,10 @@ void invert_coarsest(Hierarchy &H, cudaStream_t s) {
   const int eg = blocks_for((int64_t)n * n, 256, kSMs * 8);
   for (int k = 0; k < n; k++) {
     k_gj_pivot<<<1, 1024, 0, s>>>(H.cinv.p, n, k, perm.p, colk.p, flag.p);
+    FS_LAUNCHED();
     k_gj_elim<<<eg, 256, 0, s>>>(H.cinv.p, n, k, colk.p);
+    FS_LAUNCHED();
   }
-  FS_LAUNCHED();
   k_gj_unpermute<<<blocks_for(n, 128, kSMs), 128, 0, s>>>(H.cinv.p, n, perm.p);
   FS_LAUNCHED();
   int h = 0;
@@ -707,6 +708,16 @@ void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int 
 
 // ============================================================ cycle
 namespace {
+// algorithmic bytes of one fused Chebyshev step: the operator (values,
+// column indices, row pointers), the iterate gathered once, f, d read and
+// written, the new iterate and the inverse diagonal blocks
+template <int B, typename TP>
+double cheb_bytes(const BsrView<TP> &S, bool read_d) {
+  const double sz = sizeof(TP);
+  return (double)S.nnzb * (B * B * sz + 4) + (double)(S.nbr + 1) * 4 +
+         (double)S.nbr * B * sz * (read_d ? 5 : 4) + (double)S.nbr * B * B * sz;
+}
+
 template <int B, typename TP>
 void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *f, TP *xout, cudaStream_t s) {
   const int L = (int)C.size();
@@ -726,10 +737,13 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
   double rho = 1.0 / c.sigma;
   k_cheb_zero<B, TP><<<grid_rows(nb), kT, 0, s>>>(nb, f, c.Dinv, (TP)(1.0 / c.theta), c.d.p, buf[cur]);
   FS_LAUNCHED();
+  Profiler *pf = (l == 0) ? H.prof : nullptr;
   for (int k = 1; k < deg; k++) {
     double rn = 1.0 / (2.0 * c.sigma - rho);
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
+    if (pf) pf->start(PK_SMOOTH0, s);
     spmv<B, B>(c.S, buf[cur], e, s);
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, true));
     cur ^= 1;
     rho = rn;
   }
@@ -743,13 +757,17 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
   rho = 1.0 / c.sigma;
   {
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)0, (TP)(1.0 / c.theta)};
+    if (pf) pf->start(PK_SMOOTH0, s);
     spmv<B, B>(c.S, buf[cur], e, s);
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, false));
     cur ^= 1;
   }
   for (int k = 1; k < deg; k++) {
     double rn = 1.0 / (2.0 * c.sigma - rho);
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
+    if (pf) pf->start(PK_SMOOTH0, s);
     spmv<B, B>(c.S, buf[cur], e, s);
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, true));
     cur ^= 1;
     rho = rn;
   }

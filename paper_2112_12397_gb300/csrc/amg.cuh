@@ -51,6 +51,7 @@ struct Hierarchy {
   int nc_scalar = 0;
   std::vector<LevelCycle<float>> cf;
   std::vector<LevelCycle<double>> cd;
+  Profiler *prof = nullptr;      // times the level-0 smoother steps when set
   int levels() const { return (int)lev.size(); }
 };
 

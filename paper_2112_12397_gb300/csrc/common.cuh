@@ -26,7 +26,15 @@ struct Error : std::runtime_error {
     cudaError_t e_ = (x);                                            \
     if (e_ != cudaSuccess) ::fs::cuda_fail(e_, #x, __FILE__, __LINE__); \
   } while (0)
-#define FS_LAUNCHED() FS_CUDA(cudaGetLastError())
+// every kernel launch is followed by FS_LAUNCHED(): checks the launch and
+// counts it (fc_launch_count)
+void count_launch();
+unsigned long long launch_count();
+#define FS_LAUNCHED()               \
+  do {                              \
+    ::fs::count_launch();           \
+    FS_CUDA(cudaGetLastError());    \
+  } while (0)
 #define FS_REQUIRE(cond, code, msg)                 \
   do {                                              \
     if (!(cond)) throw ::fs::Error((code), (msg));  \
@@ -102,6 +110,25 @@ struct Bsr {
     nbr = nbr_; nbc = nbc_; br = br_; bc = bc_;
   }
   int64_t bsz() const { return (int64_t)br * bc; }
+};
+
+// ---------------------------------------------------------------- profiling
+// CUDA-event timing of selected kernels on the launching stream.
+enum ProfKernel { PK_SMOOTH0 = 0, PK_JAC = 1, PK_CGS = 2, PK_VCYCLE = 3, PK_PREC = 4, PK_N = 5 };
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> rec[PK_N];
+  std::vector<double> bytes[PK_N];
+  cudaEvent_t open_[PK_N] = {};
+  cudaEvent_t get();
+  void start(int k, cudaStream_t s);
+  void stop(int k, cudaStream_t s, double bytes_alg);
+  void reset();
+  // sums over recorded launches (synchronises on the events)
+  void stats(int k, int64_t *launches, double *ms, double *bytes_alg);
+  ~Profiler();
 };
 
 // ---------------------------------------------------------------- launch

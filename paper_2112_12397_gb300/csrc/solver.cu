@@ -192,6 +192,7 @@ struct fc_ctx {
   DBuf<double> Zd;
   DBuf<double> xk, rk, bk, hb, hx;
   double *stat_host = nullptr;   // pinned
+  Profiler prof;
   ~fc_ctx() {
     if (stat_host) cudaFreeHost(stat_host);
   }
@@ -286,9 +287,18 @@ void apply_prec(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
 }
 
 // y = J z (double out)
+template <typename T>
+double bsr_bytes(const Bsr<double> &m) {
+  return (double)m.nnzb * (m.br * m.bc * sizeof(T) + 4) + (double)(m.nbr + 1) * 4;
+}
+
 template <typename TX>
 void jac_spmv(fc_ctx &c, const TX *z, double *y) {
   cudaStream_t s = c.s;
+  const double bytes = bsr_bytes<double>(c.A) + bsr_bytes<double>(c.C1) + bsr_bytes<double>(c.Q1) +
+                       bsr_bytes<double>(c.C2) + bsr_bytes<double>(c.H) + bsr_bytes<double>(c.Q2) +
+                       bsr_bytes<double>(c.T) + (double)c.n * (sizeof(TX) + sizeof(double));
+  c.prof.start(PK_JAC, s);
   const TX *z_u = z, *z_t = z + c.nu, *z_p = z + c.nu + c.nt;
   double *y_u = y, *y_t = y + c.nu, *y_p = y + c.nu + c.nt;
   spmv_axpby<3, 3>(c.A.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
@@ -300,6 +310,7 @@ void jac_spmv(fc_ctx &c, const TX *z, double *y) {
     spmv_axpby<1, 3>(c.Q2.view(), z_u, y_p, 1.0, 0.0, (const double *)nullptr, s);
     spmv_axpby<1, 1>(c.T.view(), z_p, y_p, 1.0, 1.0, y_p, s);
   }
+  c.prof.stop(PK_JAC, s, bytes);
 }
 
 template <typename TP>
@@ -331,6 +342,7 @@ void ensure_krylov(fc_ctx &c, int maxit) {
 
 void cgs_pass(fc_ctx &c, int m, double *w, int accumulate) {
   const int64_t n = c.n;
+  c.prof.start(PK_CGS, c.s);
   k_mdot<<<kMdotBlocks, kMdotThreads, 0, c.s>>>(c.V.p, m, n, w, c.partial.p);
   FS_LAUNCHED();
   k_mdot_final<<<blocks_for((int64_t)m * 32, 256, 1024), 256, 0, c.s>>>(c.partial.p, m, kMdotBlocks, c.htmp.p,
@@ -338,6 +350,7 @@ void cgs_pass(fc_ctx &c, int m, double *w, int accumulate) {
   FS_LAUNCHED();
   k_msub<<<vgrid(n), 256, sizeof(double) * m, c.s>>>(c.V.p, m, n, c.htmp.p, w);
   FS_LAUNCHED();
+  c.prof.stop(PK_CGS, c.s, (2.0 * m + 3.0) * n * sizeof(double));
 }
 
 struct FgmresOut {
@@ -368,12 +381,14 @@ FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rt
     double *vj = c.V.p + (int64_t)j * n;
     double *w = c.V.p + (int64_t)(j + 1) * n;
     TP *zj = Z + (int64_t)j * n;
+    c.prof.start(PK_PREC, s);
     if constexpr (std::is_same<TP, double>::value) {
       apply_prec<TP>(c, P, variant, vj, zj);
     } else {
       cast(P.w.p, vj, n, s);
       apply_prec<TP>(c, P, variant, P.w.p, zj);
     }
+    c.prof.stop(PK_PREC, s, 0.0);
     jac_spmv<TP>(c, zj, w);
     nrm2sq_dev(w, n, c.w02.p, s, c.red.p);
     cgs_pass(c, j + 1, w, 0);
@@ -560,6 +575,8 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
       amg_setup(c->hier[FC_H_TUP_U], copy_cast<double, double>(c->S1.view(), s), 3, amg_params(c->opt, false), prec, s);
       if (nf) amg_setup(c->hier[FC_H_TUP_P], copy_cast<double, double>(c->S2t.view(), s), 1, amg_params(c->opt, true), prec, s);
     }
+    c->hier[FC_H_TPU_U].prof = &c->prof;
+    c->hier[FC_H_TUP_U].prof = &c->prof;
     if (prec == FC_MIXED) prepare_prec<float>(*c, c->pf);
     else prepare_prec<double>(*c, c->pd);
     c->xk.alloc(c->n); c->rk.alloc(c->n);
@@ -576,6 +593,19 @@ int fc_spmv(fc_ctx *c, const double *x, double *y) {
     jac_spmv<double>(*c, x, y);
     FS_CUDA(cudaStreamSynchronize(c->s));
     return FC_OK;
+  });
+}
+
+int fc_residual(fc_ctx *c, const double *b, const double *x, double *r, double *relres) {
+  if (!c || !b || !x || !r) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_setup has not completed");
+    jac_spmv<double>(*c, x, r);
+    axpbyz(r, b, r, 1.0, -1.0, c->n, c->s);
+    const double rn = std::sqrt(dot(r, r, c->n, c->s, c->red.p));
+    const double bn = std::sqrt(dot(b, b, c->n, c->s, c->red.p));
+    if (relres) *relres = bn > 0 ? rn / bn : rn;
+    return std::isfinite(rn) ? FC_OK : FC_NAN;
   });
 }
 
@@ -717,6 +747,26 @@ int fc_get_fixed_stress(fc_ctx *c, double *hsk) {
     return FC_OK;
   });
 }
+
+int fc_profile(fc_ctx *c, int enable) {
+  if (!c) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    c->prof.reset();
+    c->prof.on = enable != 0;
+    return FC_OK;
+  });
+}
+
+int fc_kernel_stats(fc_ctx *c, int kernel, int64_t *launches, double *total_ms, double *bytes) {
+  if (!c || kernel < 0 || kernel >= PK_N) return FC_BAD_ARG;
+  return run(c, [&]() {
+    c->prof.stats(kernel, launches, total_ms, bytes);
+    return FC_OK;
+  });
+}
+
+unsigned long long fc_launch_count(void) { return fs::launch_count(); }
 
 void fc_destroy(fc_ctx *c) {
   if (!c) return;

@@ -1,7 +1,55 @@
 // Vector kernels, deterministic reductions and an exclusive scan.
 #include "common.cuh"
 
+#include <atomic>
+
 namespace fs {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(); }
+
+cudaEvent_t Profiler::get() {
+  if (used == pool.size()) {
+    cudaEvent_t e;
+    FS_CUDA(cudaEventCreate(&e));
+    pool.push_back(e);
+  }
+  return pool[used++];
+}
+void Profiler::start(int k, cudaStream_t s) {
+  if (!on) return;
+  open_[k] = get();
+  FS_CUDA(cudaEventRecord(open_[k], s));
+}
+void Profiler::stop(int k, cudaStream_t s, double b) {
+  if (!on || !open_[k]) return;
+  cudaEvent_t e = get();
+  FS_CUDA(cudaEventRecord(e, s));
+  rec[k].push_back({open_[k], e});
+  bytes[k].push_back(b);
+  open_[k] = nullptr;
+}
+void Profiler::reset() {
+  used = 0;
+  for (int k = 0; k < PK_N; k++) { rec[k].clear(); bytes[k].clear(); open_[k] = nullptr; }
+}
+void Profiler::stats(int k, int64_t *launches, double *ms, double *b) {
+  double t = 0.0, bb = 0.0;
+  for (size_t i = 0; i < rec[k].size(); i++) {
+    FS_CUDA(cudaEventSynchronize(rec[k][i].second));
+    float x = 0.f;
+    FS_CUDA(cudaEventElapsedTime(&x, rec[k][i].first, rec[k][i].second));
+    t += x;
+    bb += bytes[k][i];
+  }
+  if (launches) *launches = (int64_t)rec[k].size();
+  if (ms) *ms = t;
+  if (b) *b = bb;
+}
+Profiler::~Profiler() {
+  for (auto e : pool) cudaEventDestroy(e);
+}
 
 void cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
   char buf[512];

@@ -1,0 +1,310 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Tolerances (double precision path):
+* products and setup matrices (J x, S1, S~, S~2, AMG operators, P): the two
+  sides sum the same terms in different orders, so entries agree to a few
+  ulps of the largest entry: max |diff| <= 1e-12 max |entry|;
+* power estimates, V-cycles, preconditioner applications: 1e-10 relative;
+* aggregates (integer decisions): identical;
+* full solves: iteration counts within +-1, solution difference <= 1e-8
+  relative (the required agreement), true residual <= tol.
+Mixed precision (FP32 preconditioner, FP64 outer): true residual <= tol in
+double, iteration growth <= 15% over the FP64 GPU run.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fracgen
+from oracle import dense, schur
+from oracle import sparse as osp
+from oracle.amg import AMG, AmgOptions
+from oracle.fgmres import fgmres
+from oracle.precond import BlockPreconditioner
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # name: (generator preset, overrides, coarse_max, coarse_max_p)
+    "tiny8": ("tiny8", {}, 64, 16),
+    "planes8": ("planes64", dict(N=8), 32, 16),
+    "planes7_ragged": ("planes64", dict(N=7, seed=4), 24, 8),
+    "rects16": ("rects128", dict(N=16), 50, 30),
+    "network16": ("network96", dict(N=16, spacing=4), 60, 40),
+}
+
+
+@pytest.fixture(scope="module")
+def fs():
+    import paper_2112_12397_gb300 as m
+    m.load(build_if_missing=True)
+    assert torch.cuda.is_available()
+    return m
+
+
+_cache = {}
+
+
+def case(name, fs):
+    if name not in _cache:
+        preset, over, cm, cmp = CASES[name]
+        P = fracgen.generate(preset, **over)
+        ctx = fs.context_for(P, fs.default_options(coarse_max=cm, coarse_max_p=cmp))
+        _cache[name] = (P, ctx, AmgOptions(coarse_max=cm), AmgOptions(coarse_max=cmp))
+    return _cache[name]
+
+
+def to_csr(rp, ci, val, shape):
+    nbr, nbc, br, bc = shape
+    return sp.bsr_matrix((val, ci, rp), shape=(nbr * br, nbc * bc)).tocsr()
+
+
+def maxrel(A, B):
+    d = (A - B)
+    d = abs(d).max() if sp.issparse(d) else np.abs(d).max()
+    s = abs(B).max() if sp.issparse(B) else np.abs(B).max()
+    return d / s if s > 0 else d
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def cuda(v):
+    return torch.from_numpy(np.ascontiguousarray(v)).cuda()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_jacobian_product_and_residual(fs, name):
+    P, ctx, _, _ = case(name, fs)
+    J = osp.jacobian(P)
+    x = np.random.default_rng(1).standard_normal(P.n)
+    y = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    ctx.spmv(cuda(x), y)
+    assert rel(y.cpu().numpy(), J @ x) <= 1e-14
+    r = torch.zeros_like(y)
+    rr = ctx.residual(cuda(P.b), cuda(x), r)
+    ref = P.b - J @ x
+    assert rel(r.cpu().numpy(), ref) <= 1e-13
+    assert abs(rr - np.linalg.norm(ref) / np.linalg.norm(P.b)) <= 1e-12 * rr
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_schur_complements_and_fixed_stress(fs, name):
+    P, ctx, _, _ = case(name, fs)
+    S1 = schur.s1(P)
+    g = ctx.get_bsr(fs.FC_M_S1)
+    assert maxrel(to_csr(*g[:3], g[3]), S1) <= 1e-12
+    St = schur.s_tilde(P, S1=S1)
+    g = ctx.get_bsr(fs.FC_M_STILDE)
+    assert maxrel(to_csr(*g[:3], g[3]), St) <= 1e-12
+    S2 = schur.s2_tilde(P, S1)
+    g = ctx.get_bsr(fs.FC_M_S2TILDE)
+    assert maxrel(to_csr(*g[:3], g[3]), S2) <= 1e-12
+    sk = ctx.fixed_stress()
+    ref = schur.fixed_stress(P, S1)
+    assert np.array_equal(sk == 0, ref == 0)
+    nz = ref != 0
+    if nz.any():
+        assert np.max(np.abs(sk[nz] - ref[nz]) / np.abs(ref[nz])) <= 1e-10
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("hier", [0, 1, 2, 3])
+def test_amg_hierarchy_and_vcycle(fs, name, hier):
+    P, ctx, opt, optp = case(name, fs)
+    S1 = schur.s1(P)
+    M, B, o = {
+        fs.FC_H_TPU_U: (lambda: schur.s_tilde(P, S1=S1), 3, opt),
+        fs.FC_H_TPU_P: (lambda: osp.csr(P.T), 1, optp),
+        fs.FC_H_TUP_U: (lambda: S1, 3, opt),
+        fs.FC_H_TUP_P: (lambda: schur.s2_tilde(P, S1), 1, optp),
+    }[hier]
+    M = M()
+    ref = AMG(M, B, o)
+    nl = ctx.num_levels(hier)
+    assert nl == len(ref.levels)
+    for l, L in enumerate(ref.levels):
+        g = ctx.get_bsr(fs.FC_M_LEVEL, hier, l)
+        assert maxrel(to_csr(*g[:3], g[3]), L.S) <= 1e-11
+        if l < nl - 1:
+            agg, lam = ctx.get_aggregates(hier, l, L.n)
+            assert np.array_equal(agg, L.agg)
+            assert abs(lam - L.lam) <= 1e-10 * L.lam
+            g = ctx.get_bsr(fs.FC_M_PROLONG, hier, l)
+            assert maxrel(to_csr(*g[:3], g[3]), L.P) <= 1e-11
+    f = np.random.default_rng(hier).standard_normal(M.shape[0])
+    x = torch.zeros(M.shape[0], dtype=torch.float64, device="cuda")
+    ctx.vcycle(hier, cuda(f), x)
+    assert rel(x.cpu().numpy(), ref(f)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("variant", ["tpu", "tup"])
+def test_preconditioner_and_solve(fs, name, variant):
+    P, ctx, opt, optp = case(name, fs)
+    J = osp.jacobian(P)
+    M = BlockPreconditioner(P, variant, opt=opt, opt_p=optp)
+    w = np.random.default_rng(7).standard_normal(P.n)
+    v = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    ctx.apply_prec(variant, cuda(w), v)
+    assert rel(v.cpu().numpy(), M(w)) <= 1e-10
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    rc, it, rr = ctx.solve(variant, b, x, tol=1e-8, maxit=400)
+    ref = fgmres(lambda q: J @ q, M, P.b, 1e-8, 400)
+    assert abs(it - ref.iters) <= 1
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-8
+    true = np.linalg.norm(P.b - J @ x.cpu().numpy()) / np.linalg.norm(P.b)
+    assert rr <= 1e-8 and abs(true - rr) <= 1e-3 * rr
+
+
+def test_solve_matches_dense_solution(fs):
+    P, ctx, _, _ = case("tiny8", fs)
+    xs = dense.solve(P)
+    for variant in ("tpu", "tup"):
+        b = cuda(P.b)
+        x = torch.zeros_like(b)
+        ctx.solve(variant, b, x, tol=1e-12, maxit=400, allow_fail=True)
+        assert rel(x.cpu().numpy(), xs) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["planes8", "rects16", "network16"])
+@pytest.mark.parametrize("variant", ["tpu", "tup"])
+def test_mixed_precision_solve(fs, name, variant):
+    P, ctx64, _, _ = case(name, fs)
+    preset, over, cm, cmp = CASES[name]
+    ctx = fs.context_for(P, fs.default_options(precision="mixed", coarse_max=cm, coarse_max_p=cmp))
+    J = osp.jacobian(P)
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    rc, it, rr = ctx.solve(variant, b, x, tol=1e-8, maxit=400)
+    xm = x.cpu().numpy()
+    true = np.linalg.norm(P.b - J @ xm) / np.linalg.norm(P.b)
+    assert true <= 1e-8
+    x64 = torch.zeros_like(b)
+    _, it64, _ = ctx64.solve(variant, b, x64, tol=1e-8, maxit=400)
+    assert it <= 1.15 * it64 + 1
+    # error against the FP64 oracle solution: bounded by the residual level
+    ref = fgmres(lambda q: J @ q, BlockPreconditioner(P, variant, opt=AmgOptions(coarse_max=cm),
+                                                       opt_p=AmgOptions(coarse_max=cmp)), P.b, 1e-8, 400)
+    assert rel(xm, ref.x) <= 1e-6
+    # mixed vector application: FP32 preconditioner within single-precision error
+    w = np.random.default_rng(3).standard_normal(P.n)
+    v32 = torch.zeros_like(b)
+    v64 = torch.zeros_like(b)
+    ctx.apply_prec(variant, cuda(w), v32)
+    ctx64.apply_prec(variant, cuda(w), v64)
+    assert rel(v32.cpu().numpy(), v64.cpu().numpy()) <= 1e-3
+    ctx.close()
+
+
+def test_solve_host_equals_device(fs):
+    P, ctx, _, _ = case("rects16", fs)
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    _, it, rr = ctx.solve("tup", b, x, 1e-8, 400)
+    hx = np.zeros(P.n)
+    _, ith, rrh = ctx.solve_host("tup", np.ascontiguousarray(P.b), hx, 1e-8, 400)
+    assert it == ith and np.array_equal(hx, x.cpu().numpy())
+
+
+# ------------------------------------------------------------------ edge cases
+def test_zero_rhs_nan_rhs_and_maxit(fs):
+    P, ctx, _, _ = case("planes8", fs)
+    b = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    x = torch.ones_like(b)
+    rc, it, rr = ctx.solve("tup", b, x, 1e-8, 50)
+    assert rc == fs.FC_OK and it == 0 and float(x.abs().max()) == 0.0
+    bn = cuda(P.b).clone()
+    bn[5] = float("nan")
+    with pytest.raises(fs.FcError) as e:
+        ctx.solve("tup", bn, x, 1e-8, 50)
+    assert e.value.code == fs.FC_NAN
+    rc, it, rr = ctx.solve("tpu", cuda(P.b), x, 1e-8, 3, allow_fail=True)
+    assert rc == fs.FC_NOT_CONVERGED and it == 3 and rr > 1e-8
+
+
+def test_singular_htilde_block_is_reported(fs):
+    P = fracgen.generate("planes64", N=6)
+    blocks = fs.device_blocks(P)
+    rp, ci, val = (t.clone() for t in blocks["H"][:3])
+    v = val.view(-1, 3, 3)
+    f = 3
+    k = int(torch.nonzero(ci[int(rp[f]):int(rp[f + 1])] == f)[0]) + int(rp[f])
+    v[k] = 0.0
+    blocks["H"] = (rp, ci, val) + tuple(blocks["H"][3:])
+    ctx = fs.Context(fs.default_options())
+    with pytest.raises(fs.FcError) as e:
+        ctx.setup(blocks, P.n_node, P.n_face)
+    assert e.value.code == fs.FC_SINGULAR_BLOCK
+    ctx.close()
+
+
+def test_bad_sizes_rejected(fs):
+    P = fracgen.generate("planes64", N=6)
+    blocks = fs.device_blocks(P)
+    ctx = fs.Context(fs.default_options())
+    with pytest.raises(fs.FcError) as e:
+        ctx.setup(blocks, P.n_node + 1, P.n_face)
+    assert e.value.code == fs.FC_BAD_ARG
+    ctx.close()
+
+
+def test_no_fractures_pure_elasticity(fs):
+    P = fracgen.generate("rects128", N=10, n_rect=0)
+    assert P.n_face == 0
+    ctx = fs.context_for(P, fs.default_options(coarse_max=40))
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    for variant in ("tpu", "tup"):
+        rc, it, rr = ctx.solve(variant, b, x, 1e-8, 300)
+        ref = fgmres(lambda q: osp.csr(P.A) @ q,
+                     BlockPreconditioner(P, variant, opt=AmgOptions(coarse_max=40)), P.b, 1e-8, 300)
+        assert abs(it - ref.iters) <= 1 and rel(x.cpu().numpy(), ref.x) <= 1e-8
+    ctx.close()
+
+
+# ------------------------------------------------------------------ full sizes
+def test_full_size_bench_configuration(fs):
+    """128^3 workload of bench.py, mixed precision, t-u-p: the true residual
+    checked by the oracle's product at full size, and sampled rows of S1
+    against the oracle's S1 restricted to those rows."""
+    P = fracgen.generate("rects128")
+    ctx = fs.context_for(P, fs.default_options(precision="mixed", variants=2))
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    rc, it, rr = ctx.solve("tup", b, x, 1e-8, 600)
+    J = osp.jacobian(P)
+    true = np.linalg.norm(P.b - J @ x.cpu().numpy()) / np.linalg.norm(P.b)
+    assert true <= 1e-8 and abs(true - rr) <= 1e-3 * true
+    rows = np.sort(np.random.default_rng(0).choice(P.n_node, 2000, replace=False))
+    srows = (3 * rows[:, None] + np.arange(3)).ravel()
+    blk = osp.blocks(P)
+    Hi = schur.htilde_inv(P, blk["H"])
+    ref = (blk["A"][srows] + blk["C1"][srows] @ Hi @ blk["C2"]).tocsr()
+    g = ctx.get_bsr(fs.FC_M_S1)
+    got = to_csr(*g[:3], g[3])[srows]
+    assert maxrel(got, ref) <= 1e-12
+    ctx.close()
+
+
+def test_full_size_planes64_fp64(fs):
+    """64^3, three intersecting planes, FP64: true residual at full size and
+    the finest aggregation of S1 identical to the oracle's."""
+    from oracle import amg as oamg
+    P = fracgen.generate("planes64")
+    ctx = fs.context_for(P, fs.default_options(variants=2))
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    rc, it, rr = ctx.solve("tup", b, x, 1e-8, 600)
+    J = osp.jacobian(P)
+    true = np.linalg.norm(P.b - J @ x.cpu().numpy()) / np.linalg.norm(P.b)
+    assert true <= 1e-8
+    S1 = schur.s1(P)
+    W = oamg.strength_graph(S1, 3, 0, AmgOptions())
+    agg_ref, nc = oamg.aggregate(W, oamg.mis2_greedy(W, oamg.priority_keys(W.shape[0], 0, 0)))
+    agg, lam = ctx.get_aggregates(fs.FC_H_TUP_U, 0, P.n_node)
+    assert np.array_equal(agg, agg_ref)
+    ctx.close()
