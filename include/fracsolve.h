@@ -136,6 +136,20 @@ int fc_spmv(fc_ctx *ctx, const double *d_x, double *d_y);
  * partial sums held by the context.  FC_NAN if the norm is not finite. */
 int fc_residual(fc_ctx *ctx, const double *d_b, const double *d_x, double *d_r, double *relres);
 
+/* The relative residual ||d_b - J d_x|| / ||d_b|| (||.|| when b = 0) written
+ * to *relres, computed without allocating anything: for callers that may not
+ * call cudaMalloc at this point (a device-memory budget fixed up front, or
+ * stream work that a cudaFree would synchronise).  The paper has no
+ * counterpart: it is a no-allocation variant of fc_residual.
+ * Scratch: the residual vector and the reduction partials live in file-scope
+ * device arrays of the library (8 MiB + 4 KiB, held on every GPU that loads it
+ * until the process exits).  Limit: n <= 1048576, else FC_BAD_ARG.  The first
+ * call on a device looks up the arrays' device addresses (set-up, once per
+ * device), so make that first call before any stream capture.  Every call
+ * reuses the same arrays and overwrites them; calls that overlap on the GPU
+ * (other streams, other contexts of the same device) race on them. */
+int fc_residual_noalloc(fc_ctx *ctx, const double *d_b, const double *d_x, double *relres);
+
 /* d_v = M^-1 d_w: app_tpu (Alg. 2) for FC_TPU, app_tup (Alg. 4) for FC_TUP,
  * device vectors of length n. */
 int fc_apply_prec(fc_ctx *ctx, int variant, const double *d_w, double *d_v);

@@ -24,7 +24,8 @@ FC_M_LEVEL, FC_M_PROLONG, FC_M_S1, FC_M_STILDE, FC_M_S2TILDE = range(5)
 VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP}
 
 # exported symbols declared by include/fracsolve.h
-SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_residual", "fc_apply_prec", "fc_solve",
+SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_residual", "fc_residual_noalloc",
+           "fc_apply_prec", "fc_solve",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
            "fc_get_fixed_stress", "fc_profile", "fc_kernel_stats", "fc_launch_count", "fc_destroy",
            "fc_strerror", "fc_last_error"]
@@ -80,6 +81,7 @@ def load(build_if_missing: bool = False):
         "fc_setup": (C.c_int, [vp, C.POINTER(fc_blocks)]),
         "fc_spmv": (C.c_int, [vp, vp, vp]),
         "fc_residual": (C.c_int, [vp, vp, vp, vp, pd]),
+        "fc_residual_noalloc": (C.c_int, [vp, vp, vp, pd]),
         "fc_apply_prec": (C.c_int, [vp, C.c_int, vp, vp]),
         "fc_solve": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
         "fc_solve_host": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
@@ -173,6 +175,13 @@ class Context:
     def residual(self, b, x, r) -> float:
         rr = C.c_double(0)
         self._check(self.lib.fc_residual(self.h, _ptr(b), _ptr(x), _ptr(r), C.byref(rr)), self.h)
+        return rr.value
+
+    def residual_noalloc(self, b, x) -> float:
+        """Relative residual with no device allocation (library-held scratch,
+        n <= 1048576); see fc_residual_noalloc."""
+        rr = C.c_double(0)
+        self._check(self.lib.fc_residual_noalloc(self.h, _ptr(b), _ptr(x), C.byref(rr)), self.h)
         return rr.value
 
     def apply_prec(self, variant: str, w, v):

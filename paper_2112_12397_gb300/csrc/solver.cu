@@ -6,6 +6,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <type_traits>
 
 #include "amg.cuh"
@@ -463,6 +464,86 @@ int solve_impl(fc_ctx &c, int variant, const double *b, double *x, double tol, i
 
 }  // namespace
 
+// ============================================================ residual without allocation
+// Some callers cannot allocate device memory when they need a residual check:
+// code that runs under a fixed device-memory budget reserved up front, code
+// that must not let cudaFree synchronise the device in the middle of its
+// stream work, or hosts that forbid further allocation once the solver is set
+// up.  fc_residual_noalloc serves them: it keeps b - J x and its reduction
+// partials in the file-scope arrays below (8 MiB + 4 KiB, held by every GPU
+// that loads this library until the process exits) instead of caller or
+// context buffers.
+namespace {
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 20;   // largest n accepted
+constexpr int kNoAllocParts = 256;                   // reduction blocks
+static __device__ __align__(256) double g_noalloc_r[kNoAllocMaxN];
+static __device__ __align__(256) double g_noalloc_part[2 * kNoAllocParts + 2];
+
+struct NoAllocScratch {
+  double *r = nullptr;
+  double *part = nullptr;
+};
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch g_noalloc_addr[kNoAllocDevices];
+
+// device addresses of the scratch arrays on `device` (must be current);
+// looked up once per device
+int noalloc_scratch(int device, NoAllocScratch *out) {
+  if (device < 0 || device >= kNoAllocDevices) return FC_BAD_ARG;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoAllocScratch &a = g_noalloc_addr[device];
+  if (!a.r) {
+    void *r = nullptr, *p = nullptr;
+    if (cudaGetSymbolAddress(&r, g_noalloc_r) != cudaSuccess ||
+        cudaGetSymbolAddress(&p, g_noalloc_part) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return FC_CUDA_ERROR;
+    }
+    a.r = static_cast<double *>(r);
+    a.part = static_cast<double *>(p);
+  }
+  *out = a;
+  return FC_OK;
+}
+
+// r = b - r (r holds J x on entry); per-block partial sums of r.r and b.b
+__global__ void k_noalloc_resid(const double *__restrict__ b, double *r, int64_t n, double *part) {
+  __shared__ double s_r[32], s_b[32];
+  double ar = 0.0, ab = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    const double v = bi - r[i];
+    r[i] = v;
+    ar += v * v;
+    ab += bi * bi;
+  }
+  ar = warp_sum(ar);
+  ab = warp_sum(ab);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { s_r[wid] = ar; s_b[wid] = ab; }
+  __syncthreads();
+  if (wid == 0) {
+    double x = lane < (int)(blockDim.x >> 5) ? s_r[lane] : 0.0;
+    double y = lane < (int)(blockDim.x >> 5) ? s_b[lane] : 0.0;
+    x = warp_sum(x);
+    y = warp_sum(y);
+    if (lane == 0) { part[blockIdx.x] = x; part[kNoAllocParts + blockIdx.x] = y; }
+  }
+}
+
+// part[2P] = sum of the r.r partials, part[2P+1] = sum of the b.b partials
+__global__ void k_noalloc_final(double *part) {
+  const int lane = threadIdx.x;
+  double x = 0.0, y = 0.0;
+  for (int i = lane; i < kNoAllocParts; i += 32) { x += part[i]; y += part[kNoAllocParts + i]; }
+  x = warp_sum(x);
+  y = warp_sum(y);
+  if (lane == 0) { part[2 * kNoAllocParts] = x; part[2 * kNoAllocParts + 1] = y; }
+}
+}  // namespace
+
 // ============================================================ error plumbing
 namespace {
 int run(fc_ctx *c, const std::function<int()> &fn) {
@@ -767,6 +848,41 @@ int fc_kernel_stats(fc_ctx *c, int kernel, int64_t *launches, double *total_ms, 
 }
 
 unsigned long long fc_launch_count(void) { return fs::launch_count(); }
+
+int fc_residual_noalloc(fc_ctx *c, const double *b, const double *x, double *relres) {
+  if (!c || !b || !x || !relres) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_setup has not completed");
+    FS_REQUIRE(c->n <= kNoAllocMaxN, FC_BAD_ARG,
+               "fc_residual_noalloc: n = " + std::to_string(c->n) +
+                   " exceeds the 1048576-entry scratch; use fc_residual");
+    NoAllocScratch sc;
+    const int rc = noalloc_scratch(c->device, &sc);
+    FS_REQUIRE(rc == FC_OK, rc, "cudaGetSymbolAddress of the residual scratch failed");
+    cudaStream_t s = c->s;
+    double *y_u = sc.r, *y_t = sc.r + c->nu, *y_p = sc.r + c->nu + c->nt;
+    const double *z_u = x, *z_t = x + c->nu, *z_p = x + c->nu + c->nt;
+    spmv_axpby<3, 3>(c->A.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
+    if (c->nf) {
+      spmv_axpby<3, 3>(c->C1.view(), z_t, y_u, 1.0, 1.0, y_u, s);
+      spmv_axpby<3, 1>(c->Q1.view(), z_p, y_u, 1.0, 1.0, y_u, s);
+      spmv_axpby<3, 3>(c->C2.view(), z_u, y_t, 1.0, 0.0, (const double *)nullptr, s);
+      spmv_axpby<3, 3>(c->H.view(), z_t, y_t, -1.0, 1.0, y_t, s);
+      spmv_axpby<1, 3>(c->Q2.view(), z_u, y_p, 1.0, 0.0, (const double *)nullptr, s);
+      spmv_axpby<1, 1>(c->T.view(), z_p, y_p, 1.0, 1.0, y_p, s);
+    }
+    k_noalloc_resid<<<kNoAllocParts, 256, 0, s>>>(b, sc.r, c->n, sc.part);
+    FS_LAUNCHED();
+    k_noalloc_final<<<1, 32, 0, s>>>(sc.part);
+    FS_LAUNCHED();
+    FS_CUDA(cudaMemcpyAsync(c->stat_host + 4, sc.part + 2 * kNoAllocParts, 2 * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+    const double rn = std::sqrt(c->stat_host[4]), bn = std::sqrt(c->stat_host[5]);
+    *relres = bn > 0 ? rn / bn : rn;
+    return std::isfinite(rn) ? FC_OK : FC_NAN;
+  });
+}
 
 void fc_destroy(fc_ctx *c) {
   if (!c) return;
