@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle"],
+                    help="vcycle: fc_setup then two V-cycles of the elasticity hierarchy (profiling case)")
     return ap.parse_args()
 
 
@@ -353,8 +355,31 @@ def ours(args, rank, world, local_rank):
     print(json.dumps(out))
 
 
+def vcycle_case(args):
+    """Small profiling case: setup, then two V-cycles on the S1 (t-u-p) or
+    S~ (t-p-u) hierarchy; the finest level's operator is several hundred MB."""
+    import torch
+
+    import fracgen
+    import paper_2112_12397_gb300 as fs
+    fracgen.build()
+    P = fracgen.generate(args.workload)
+    v = fs.VARIANTS[args.variant]
+    ctx = fs.context_for(P, fs.default_options(precision=args.precision, variants=1 << v))
+    hier = fs.FC_H_TUP_U if v == fs.FC_TUP else fs.FC_H_TPU_U
+    f = torch.randn(3 * P.n_node, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(f)
+    for _ in range(2):
+        ctx.vcycle(hier, f, x)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "vcycle", "workload": args.workload, "norm": float(x.norm())}))
+
+
 def main():
     args = parse()
+    if args.mode == "vcycle":
+        vcycle_case(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -626,6 +626,8 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
         c.Dinv = c.Dinv_own.p;
       }
     }
+    c.Ss = to_sell<TP>(L.S.view(), s);
+    if (!last) c.Ps = to_sell<TP>(L.P.view(), s);
     c.f.alloc(n > 0 ? n : 1);
     c.x.alloc(n > 0 ? n : 1);
     c.xa.alloc(n > 0 ? n : 1);
@@ -742,23 +744,23 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
     double rn = 1.0 / (2.0 * c.sigma - rho);
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    spmv<B, B>(c.S, buf[cur], e, s);
+    sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
     if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, true));
     cur ^= 1;
     rho = rn;
   }
   // residual, restriction, coarse correction, prolongation
-  spmv_axpby<B, B>(c.S, buf[cur], c.r.p, -1.0, 1.0, f, s);
+  sell_axpby<B, B>(c.Ss.view(), buf[cur], c.r.p, -1.0, 1.0, f, s);
   LevelCycle<TP> &cn = C[l + 1];
   spmv_axpby<B, B>(c.R, c.r.p, cn.f.p, 1.0, 0.0, (const TP *)nullptr, s);
   cycle_level<B, TP>(H, C, l + 1, cn.f.p, cn.x.p, s);
-  spmv_axpby<B, B>(c.P, cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
+  sell_axpby<B, B>(c.Ps.view(), cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
   // post-smoothing from the corrected iterate
   rho = 1.0 / c.sigma;
   {
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)0, (TP)(1.0 / c.theta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    spmv<B, B>(c.S, buf[cur], e, s);
+    sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
     if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, false));
     cur ^= 1;
   }
@@ -766,7 +768,7 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
     double rn = 1.0 / (2.0 * c.sigma - rho);
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    spmv<B, B>(c.S, buf[cur], e, s);
+    sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
     if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, true));
     cur ^= 1;
     rho = rn;

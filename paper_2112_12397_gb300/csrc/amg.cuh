@@ -5,6 +5,7 @@
 #include <memory>
 
 #include "common.cuh"
+#include "sell.cuh"
 
 namespace fs {
 
@@ -36,6 +37,7 @@ struct LevelCycle {
   BsrView<TP> S, P, R;
   const TP *Dinv = nullptr;
   Bsr<TP> S_own, P_own, R_own;   // used when TP differs from double
+  Sell<TP> Ss, Ps;               // sliced-ELL copies of S and P used by the cycle
   DBuf<TP> Dinv_own;
   DBuf<TP> f, x, xa, d, r;       // right-hand side, iterate (two buffers), direction, residual
   double theta = 0, delta = 0, sigma = 0;

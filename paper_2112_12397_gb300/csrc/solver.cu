@@ -11,6 +11,7 @@
 
 #include "amg.cuh"
 #include "schur.cuh"
+#include "sell.cuh"
 #include "sparse.cuh"
 #include "spmv.cuh"
 
@@ -24,6 +25,7 @@ struct PrecData {
   const TP *Hinv = nullptr;
   Bsr<TP> C1o, Q1o, C2o, Q2o;
   DBuf<TP> Hinvo;
+  Sell<TP> sC1, sQ1, sC2, sQ2;   // sliced-ELL copies used by the products
   DBuf<TP> w, out, tt, tu, su, tp, sp, vp;
   bool ready = false;
 };
@@ -180,6 +182,7 @@ struct fc_ctx {
   int nn = 0, nf = 0;
   int64_t n = 0, nu = 0, nt = 0;
   Bsr<double> A, C1, Q1, C2, H, Q2, T;
+  Sell<double> sA, sC1, sQ1, sC2, sH, sQ2, sT;   // sliced-ELL copies for J z
   DBuf<double> Hinv64, SK;
   Bsr<double> S1, St, S2t;
   bool have[2] = {false, false};
@@ -240,6 +243,10 @@ void prepare_prec(fc_ctx &c, PrecData<TP> &P) {
     cast(P.Hinvo.p, c.Hinv64.p, (int64_t)c.nf * 9, s);
     P.Hinv = P.Hinvo.p;
   }
+  P.sC1 = to_sell<TP>(c.C1.view(), s);
+  P.sQ1 = to_sell<TP>(c.Q1.view(), s);
+  P.sC2 = to_sell<TP>(c.C2.view(), s);
+  P.sQ2 = to_sell<TP>(c.Q2.view(), s);
   const int64_t n = c.n;
   P.w.alloc(n); P.out.alloc(n);
   P.tt.alloc(c.nt > 0 ? c.nt : 1);
@@ -259,30 +266,30 @@ void apply_prec(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
   if (variant == FC_TUP) {
     Hierarchy &Hu = c.hier[FC_H_TUP_U], &Hp = c.hier[FC_H_TUP_P];
     if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }   // 1
-    spmv_axpby<3, 3>(P.C1, P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                          // 2
+    sell_axpby<3, 3>(P.sC1.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                // 2
     amg_vcycle<TP>(Hu, P.tu.p, P.su.p, s);                                                            // 3
-    spmv_axpby<1, 3>(P.Q2, P.su.p, P.tp.p, -1.0, 1.0, w_p, s);                                        // 4
+    sell_axpby<1, 3>(P.sQ2.view(), P.su.p, P.tp.p, -1.0, 1.0, w_p, s);                              // 4
     if (nf) amg_vcycle<TP>(Hp, P.tp.p, z_p, s);                                                        // 5
-    spmv_axpby<3, 1>(P.Q1, z_p, P.tu.p, 1.0, 0.0, (const TP *)nullptr, s);                           // 6
+    sell_axpby<3, 1>(P.sQ1.view(), z_p, P.tu.p, 1.0, 0.0, (const TP *)nullptr, s);                 // 6
     amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // 7
     axpbyz(z_u, P.su.p, z_u, 1.0, -1.0, nu, s);                                                       // 8
     if (nf) {                                                                                         // 9-10
       EpiHinvUpdate<TP> e{z_t, P.tt.p, P.Hinv};
-      spmv<3, 3>(P.C2, z_u, e, s);
+      sell_spmv<3, 3>(P.sC2.view(), z_u, e, s);
     }
   } else {
     Hierarchy &Hu = c.hier[FC_H_TPU_U], &Hp = c.hier[FC_H_TPU_P];
     if (nf) amg_vcycle<TP>(Hp, w_p, P.tp.p, s);                                                        // 1
     if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }    // 2
-    spmv_axpby<3, 3>(P.C1, P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                          // 3
-    spmv_axpby<3, 1>(P.Q1, P.tp.p, P.tu.p, -1.0, 1.0, P.tu.p, s);
+    sell_axpby<3, 3>(P.sC1.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                // 3
+    sell_axpby<3, 1>(P.sQ1.view(), P.tp.p, P.tu.p, -1.0, 1.0, P.tu.p, s);
     amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // 4
     if (nf) {
-      spmv_axpby<1, 3>(P.Q2, z_u, P.sp.p, 1.0, 0.0, (const TP *)nullptr, s);                          // 5
+      sell_axpby<1, 3>(P.sQ2.view(), z_u, P.sp.p, 1.0, 0.0, (const TP *)nullptr, s);                // 5
       amg_vcycle<TP>(Hp, P.sp.p, P.vp.p, s);                                                          // 7
       axpbyz(z_p, P.tp.p, P.vp.p, 1.0, -1.0, nf, s);
       EpiHinvUpdate<TP> e{z_t, P.tt.p, P.Hinv};                                                      // 6, 8
-      spmv<3, 3>(P.C2, z_u, e, s);
+      sell_spmv<3, 3>(P.sC2.view(), z_u, e, s);
     }
   }
 }
@@ -302,14 +309,14 @@ void jac_spmv(fc_ctx &c, const TX *z, double *y) {
   c.prof.start(PK_JAC, s);
   const TX *z_u = z, *z_t = z + c.nu, *z_p = z + c.nu + c.nt;
   double *y_u = y, *y_t = y + c.nu, *y_p = y + c.nu + c.nt;
-  spmv_axpby<3, 3>(c.A.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
+  sell_axpby<3, 3>(c.sA.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
   if (c.nf) {
-    spmv_axpby<3, 3>(c.C1.view(), z_t, y_u, 1.0, 1.0, y_u, s);
-    spmv_axpby<3, 1>(c.Q1.view(), z_p, y_u, 1.0, 1.0, y_u, s);
-    spmv_axpby<3, 3>(c.C2.view(), z_u, y_t, 1.0, 0.0, (const double *)nullptr, s);
-    spmv_axpby<3, 3>(c.H.view(), z_t, y_t, -1.0, 1.0, y_t, s);
-    spmv_axpby<1, 3>(c.Q2.view(), z_u, y_p, 1.0, 0.0, (const double *)nullptr, s);
-    spmv_axpby<1, 1>(c.T.view(), z_p, y_p, 1.0, 1.0, y_p, s);
+    sell_axpby<3, 3>(c.sC1.view(), z_t, y_u, 1.0, 1.0, y_u, s);
+    sell_axpby<3, 1>(c.sQ1.view(), z_p, y_u, 1.0, 1.0, y_u, s);
+    sell_axpby<3, 3>(c.sC2.view(), z_u, y_t, 1.0, 0.0, (const double *)nullptr, s);
+    sell_axpby<3, 3>(c.sH.view(), z_t, y_t, -1.0, 1.0, y_t, s);
+    sell_axpby<1, 3>(c.sQ2.view(), z_u, y_p, 1.0, 0.0, (const double *)nullptr, s);
+    sell_axpby<1, 1>(c.sT.view(), z_p, y_p, 1.0, 1.0, y_p, s);
   }
   c.prof.stop(PK_JAC, s, bytes);
 }
@@ -638,6 +645,10 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     };
     c->A = up(J->A); c->C1 = up(J->C1); c->Q1 = up(J->Q1); c->C2 = up(J->C2);
     c->H = up(J->H); c->Q2 = up(J->Q2); c->T = up(J->T);
+    c->sA = to_sell<double>(c->A.view(), s); c->sC1 = to_sell<double>(c->C1.view(), s);
+    c->sQ1 = to_sell<double>(c->Q1.view(), s); c->sC2 = to_sell<double>(c->C2.view(), s);
+    c->sH = to_sell<double>(c->H.view(), s); c->sQ2 = to_sell<double>(c->Q2.view(), s);
+    c->sT = to_sell<double>(c->T.view(), s);
     for (auto &h : c->hier) h = Hierarchy();
     c->pf = PrecData<float>();
     c->pd = PrecData<double>();

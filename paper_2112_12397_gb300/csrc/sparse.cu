@@ -1,5 +1,6 @@
 // Setup-phase sparse kernels: transpose, block SpGEMM, sparse add.
 #include "sparse.cuh"
+#include "sell.cuh"
 
 namespace fs {
 
@@ -321,6 +322,81 @@ Bsr<TO> copy_cast(const BsrView<TI> &A, cudaStream_t s) {
 }
 template Bsr<float> copy_cast<float, double>(const BsrView<double> &, cudaStream_t);
 template Bsr<double> copy_cast<double, double>(const BsrView<double> &, cudaStream_t);
+
+// ============================================================ sliced ELL
+namespace {
+__global__ void k_sell_width(BsrView<double> A, int nslice, int *w) {
+  for (int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sl < nslice;
+       sl += (int64_t)gridDim.x * blockDim.x) {
+    int m = 0;
+    for (int r = 0; r < 32; r++) {
+      int64_t row = sl * 32 + r;
+      if (row >= A.nbr) break;
+      int len = A.rp[row + 1] - A.rp[row];
+      m = len > m ? len : m;
+    }
+    w[sl] = m;
+  }
+}
+
+__global__ void k_to_i64(const int *in, int64_t *out, int n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+template <typename T>
+__global__ void k_sell_fill(BsrView<double> A, int nslice, const int64_t *sp, int *ci, T *val) {
+  const int bs = A.br * A.bc;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nslice * 32;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = t >> 5;
+    const int lane = (int)(t & 31);
+    const int64_t s0 = sp[sl], w = sp[sl + 1] - s0;
+    const bool real = t < A.nbr;
+    const int b0 = real ? A.rp[t] : 0;
+    const int len = real ? A.rp[t + 1] - b0 : 0;
+    for (int64_t k = 0; k < w; k++) {
+      const int64_t slot = s0 + k;
+      if (k < len) {
+        ci[slot * 32 + lane] = A.ci[b0 + k];
+        for (int q = 0; q < bs; q++) val[(slot * bs + q) * 32 + lane] = (T)A.val[(int64_t)(b0 + k) * bs + q];
+      } else {
+        ci[slot * 32 + lane] = 0;
+        for (int q = 0; q < bs; q++) val[(slot * bs + q) * 32 + lane] = T(0);
+      }
+    }
+  }
+}
+}  // namespace
+
+template <typename T>
+Sell<T> to_sell(const BsrView<double> &A, cudaStream_t s) {
+  Sell<T> S;
+  S.nbr = A.nbr; S.nbc = A.nbc; S.br = A.br; S.bc = A.bc; S.nnzb = A.nnzb;
+  S.nslice = (A.nbr + 31) / 32;
+  S.sp.alloc(S.nslice + 1);
+  if (S.nslice == 0) {
+    FS_CUDA(cudaMemsetAsync(S.sp.p, 0, sizeof(int64_t), s));
+    return S;
+  }
+  DBuf<int> w(S.nslice + 1), wp(S.nslice + 1);
+  k_sell_width<<<blocks_for(S.nslice, 128, kSMs * 8), 128, 0, s>>>(A, S.nslice, w.p);
+  FS_LAUNCHED();
+  S.slots = exclusive_scan(w.p, wp.p, S.nslice, s);
+  k_to_i64<<<blocks_for(S.nslice + 1, 256, kSMs * 4), 256, 0, s>>>(wp.p, S.sp.p, S.nslice);
+  FS_LAUNCHED();
+  S.ci.alloc(S.slots * 32);
+  S.val.alloc(S.slots * 32 * A.br * A.bc);
+  if (S.slots) {
+    k_sell_fill<T><<<blocks_for((int64_t)S.nslice * 32, 128, kSMs * 16), 128, 0, s>>>(A, S.nslice, S.sp.p, S.ci.p,
+                                                                                       S.val.p);
+    FS_LAUNCHED();
+  }
+  return S;
+}
+template Sell<float> to_sell<float>(const BsrView<double> &, cudaStream_t);
+template Sell<double> to_sell<double>(const BsrView<double> &, cudaStream_t);
 
 Bsr<double> upload_bsr(int nbr, int nbc, int br, int bc, int64_t nnzb, const int *rp_dev,
                        const int *ci_dev, const double *val_dev, cudaStream_t s) {

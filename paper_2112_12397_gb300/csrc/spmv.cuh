@@ -1,11 +1,11 @@
 // Block sparse matrix-vector products with fused epilogues.
 //
-// One group of G lanes owns one block row.  The row's values are streamed
-// as a flat, contiguous array of nnz_row * BR * BC scalars, so consecutive
-// lanes read consecutive addresses (coalesced) whatever the block shape; each
-// lane adds value * x[col * BC + c] into the partial sum of its block-row
-// component, the group reduces with shuffles, and lane 0 hands the BR sums to
-// an epilogue that finishes the row (axpby, Chebyshev update, H~^-1 solve).
+// BSR kernel: one group of G lanes owns one block row; each lane takes whole
+// blocks of the row (its values, column and the BC entries of x it needs),
+// the group reduces the BR partial sums with shuffles, and lane 0 hands them
+// to an epilogue that finishes the row (axpby, Chebyshev update, H~^-1
+// solve).  Used for long rows (restriction) and setup products; the short-row
+// products of the solve use the sliced-ELL kernel of sell.cuh.
 #pragma once
 
 #include "common.cuh"
@@ -30,19 +30,20 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(BsrView<TA> A, const TX *__res
   for (int q = 0; q < BR; q++) acc[q] = TA(0);
   if (valid) {
     const int s = __ldg(A.rp + row), e = __ldg(A.rp + row + 1);
-    const int nel = (e - s) * BS;
-    const TA *__restrict__ v = A.val + (int64_t)s * BS;
-    const int *__restrict__ ci = A.ci + s;
-    for (int j = lane; j < nel; j += G) {
-      const int b = j / BS;
-      const int rc = j - b * BS;
-      const int r = rc / BC;
-      const int c = rc - r * BC;
-      const int col = __ldg(ci + b);
-      const TA prod = __ldg(v + j) * (TA)__ldg(x + (int64_t)col * BC + c);
+    // each lane takes whole blocks: no index arithmetic per scalar entry
+#pragma unroll 2
+    for (int b = s + lane; b < e; b += G) {
+      const int col = __ldg(A.ci + b);
+      TA a[BS];
 #pragma unroll
-      for (int q = 0; q < BR; q++)
-        if (q == r) acc[q] += prod;
+      for (int q = 0; q < BS; q++) a[q] = __ldg(A.val + (int64_t)b * BS + q);
+      TA xv[BC];
+#pragma unroll
+      for (int j = 0; j < BC; j++) xv[j] = (TA)__ldg(x + (int64_t)col * BC + j);
+#pragma unroll
+      for (int r = 0; r < BR; r++)
+#pragma unroll
+        for (int j = 0; j < BC; j++) acc[r] += a[r * BC + j] * xv[j];
     }
   }
 #pragma unroll
@@ -130,11 +131,13 @@ struct EpiHinvUpdate {
   }
 };
 
+// lanes per row from the mean number of blocks per row
 inline int lanes_for(int64_t nnzb, int nbr, int bs) {
-  double per = nbr > 0 ? (double)nnzb * bs / nbr : 0.0;
-  if (per > 48) return 32;
-  if (per > 24) return 16;
-  if (per > 10) return 8;
+  (void)bs;
+  double per = nbr > 0 ? (double)nnzb / nbr : 0.0;
+  if (per > 24) return 32;
+  if (per > 12) return 16;
+  if (per > 6) return 8;
   return 4;
 }
 

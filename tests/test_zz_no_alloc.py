@@ -36,11 +36,14 @@ def test_noalloc_residual_matches_fc_residual_twice(fs):
         if call == 1:   # the first call may load the library's device module
             assert torch.cuda.mem_get_info()[0] == free0
         assert abs(got - ref) <= 1e-12 * ref, (call, got, ref)
-    # a solved system: the no-allocation check agrees with the solver's residual
+    # a solved system: b - J x is a difference of nearly equal vectors, so two
+    # summation orders of J x agree only to eps * || |J| |x| || / ||b - J x||
+    # (about 1e-4 relative here); both must certify the 1e-8 solve
     x = torch.zeros_like(b)
     rc, it, rr = ctx.solve("tup", b, x, 1e-8, 400)
+    ref = ctx.residual(b, x, r)
     got = ctx.residual_noalloc(b, x)
-    assert abs(got - rr) <= 1e-6 * rr and got <= 1e-8
+    assert abs(got - ref) <= 1e-3 * ref and ref <= 1e-8 and got <= 1e-8 * (1 + 1e-3)
     ctx.close()
 
 
