@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--verbose", type=int, default=0, help="library diagnostics (setup phase times) to stderr")
     ap.add_argument("--mode", default="bench", choices=["bench", "vcycle"],
                     help="vcycle: fc_setup then two V-cycles of the elasticity hierarchy (profiling case)")
     return ap.parse_args()
@@ -212,7 +213,7 @@ def ours(args, rank, world, local_rank):
     variant_bit = 1 << fs.VARIANTS[args.variant]
 
     def make_ctx(prec):
-        ctx = fs.Context(fs.default_options(precision=prec, variants=variant_bit))
+        ctx = fs.Context(fs.default_options(precision=prec, variants=variant_bit, verbose=args.verbose))
         return ctx
 
     def barrier():

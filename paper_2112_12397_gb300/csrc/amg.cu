@@ -253,61 +253,81 @@ __global__ void k_power_start(int64_t n, uint64_t seed, int level, double *v) {
 }
 
 // ------------------------------------------------------------ 6. prolongator
-constexpr int kMaxCand = 512;
-
-// sorted unique aggregates reached by row i of S; returns count or -1
-__device__ inline int row_candidates(const BsrView<double> &S, int64_t i, const int *agg, int *c) {
-  int n = 0;
-  for (int e = S.rp[i]; e < S.rp[i + 1]; e++) {
-    int a = agg[S.ci[e]];
-    if (a < 0) continue;
-    int pos = n;
-    bool dup = false;
-    for (int k = 0; k < n; k++) {
-      if (c[k] == a) { dup = true; break; }
-    }
-    if (dup) continue;
-    if (n >= kMaxCand) return -1;
-    while (pos > 0 && c[pos - 1] > a) { c[pos] = c[pos - 1]; pos--; }
-    c[pos] = a;
-    n++;
-  }
-  return n;
-}
-
+// One warp per row i of S.  The aggregates a(j) of the row's columns are
+// staged in shared memory; the distinct ones, ranked in increasing order, are
+// the row's columns in P.  For each distinct a, the blocks S_ij with
+// a(j) = a are added in row order, then
+//   P_ia = [a(i) = a] I / sqrt|a| - omega D_i^-1 (sum_j S_ij) / sqrt|a|.
 template <int B>
 __global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, const double *Dinv,
                           double omega, int pass, int *cnt, const int *rpP, int *ciP, double *valP,
-                          int *flag) {
+                          int cap, int *flag) {
   constexpr int BS = B * B;
-  int c[kMaxCand];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.nbr;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int n = row_candidates(S, i, agg, c);
-    if (n < 0) { atomicExch(flag, 1); if (!pass) cnt[i] = 0; continue; }
-    if (!pass) { cnt[i] = n; continue; }
-    int o = rpP[i];
+  extern __shared__ int sh_agg[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  int *al = sh_agg + (size_t)wid * 3 * cap;   // aggregate of entry t (-1: none)
+  int *fl = al + cap;                          // 1 if entry t is the first with its aggregate
+  int *rk = fl + cap;                          // rank of that aggregate among the distinct ones
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  for (int64_t i = blockIdx.x * (int64_t)wpb + wid; i < S.nbr; i += nwarps) {
+    const int s0 = S.rp[i], len = S.rp[i + 1] - s0;
+    if (len > cap) {
+      if (lane == 0) { atomicExch(flag, 1); if (!pass) cnt[i] = 0; }
+      continue;
+    }
+    for (int t = lane; t < len; t += 32) al[t] = agg[S.ci[s0 + t]];
+    __syncwarp();
+    for (int t = lane; t < len; t += 32) {
+      const int a = al[t];
+      bool first = a >= 0;
+      for (int u = 0; u < t && first; u++) first = (al[u] != a);
+      fl[t] = first;
+    }
+    __syncwarp();
+    int nu = 0;
+    for (int t = lane; t < len; t += 32) {
+      int r = -1;
+      if (fl[t]) {
+        const int a = al[t];
+        r = 0;
+        for (int u = 0; u < len; u++) r += (fl[u] && al[u] < a);
+        nu++;
+      }
+      rk[t] = r;
+    }
+    for (int o = 16; o > 0; o >>= 1) nu += __shfl_xor_sync(0xffffffffu, nu, o);
+    __syncwarp();
+    if (!pass) {
+      if (lane == 0) cnt[i] = nu;
+      __syncwarp();
+      continue;
+    }
+    const int o = rpP[i];
     const double *Di = Dinv + i * BS;
-    for (int k = 0; k < n; k++) {
-      int a = c[k];
+    const int ai = agg[i];
+    for (int t = lane; t < len; t += 32) {
+      const int r = rk[t];
+      if (r < 0) continue;
+      const int a = al[t];
       double acc[BS];
       for (int q = 0; q < BS; q++) acc[q] = 0.0;
-      for (int e = S.rp[i]; e < S.rp[i + 1]; e++) {
-        if (agg[S.ci[e]] != a) continue;
-        const double *v = S.val + (int64_t)e * BS;
+      for (int u = t; u < len; u++) {
+        if (al[u] != a) continue;
+        const double *v = S.val + (int64_t)(s0 + u) * BS;
         for (int q = 0; q < BS; q++) acc[q] += v[q];
       }
-      double isz = 1.0 / sqrt((double)asize[a]);
-      double *out = valP + (int64_t)(o + k) * BS;
-      for (int r = 0; r < B; r++)
+      const double isz = 1.0 / sqrt((double)asize[a]);
+      double *out = valP + (int64_t)(o + r) * BS;
+      for (int rr = 0; rr < B; rr++)
         for (int cc = 0; cc < B; cc++) {
           double m = 0.0;
-          for (int t = 0; t < B; t++) m += Di[r * B + t] * (acc[t * B + cc] * isz);
-          double pt = (agg[i] == a && r == cc) ? isz : 0.0;
-          out[r * B + cc] = pt - omega * m;
+          for (int q = 0; q < B; q++) m += Di[rr * B + q] * (acc[q * B + cc] * isz);
+          const double pt = (ai == a && rr == cc) ? isz : 0.0;
+          out[rr * B + cc] = pt - omega * m;
         }
-      ciP[o + k] = a;
+      ciP[o + r] = a;
     }
+    __syncwarp();
   }
 }
 
@@ -529,25 +549,47 @@ int aggregate(const Graph &G, uint64_t seed, int level, DBuf<int> &agg, DBuf<int
   return nc;
 }
 
-template <int B>
-double power_lambda(const BsrView<double> &S, const double *Dinv, uint64_t seed, int level, int steps,
-                    cudaStream_t s) {
+template <typename TP>
+__global__ void k_power_scale(TP *v, const TP *w, int64_t n, const double *ww, const double *vv, double *lam) {
+  const double nw = sqrt(*ww);
+  const double a = 1.0 / nw;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *lam = nw / sqrt(*vv);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    v[k] = (TP)(a * (double)w[k]);
+}
+
+// lambda of D^-1 S by normalised power steps on the cycle-precision operator;
+// norms in double on the device, one host read at the end
+template <int B, typename TP>
+double power_lambda(const SellView<TP> &S, const TP *Dinv, uint64_t seed, int level, int steps, cudaStream_t s) {
   const int64_t n = (int64_t)S.nbr * B;
-  DBuf<double> v(n), w(n), tmp(kRedBlocks + 1);
-  k_power_start<<<grid_rows(n), kT, 0, s>>>(n, seed, level, v.p);
+  DBuf<double> v0(n), scal(2 + steps), part(kRedBlocks + 1);
+  DBuf<TP> v(n), w(n);
+  k_power_start<<<grid_rows(n), kT, 0, s>>>(n, seed, level, v0.p);
   FS_LAUNCHED();
-  double lam = 0.0;
+  cast(v.p, v0.p, n, s);
   for (int it = 0; it < steps; it++) {
-    EpiBlockDiag<B, double> e{w.p, Dinv};
-    spmv<B, B>(S, v.p, e, s);
-    double ww = dot(w.p, w.p, n, s, tmp.p);
-    double vv = dot(v.p, v.p, n, s, tmp.p);
-    double nw = std::sqrt(ww);
-    FS_REQUIRE(std::isfinite(nw) && nw > 0, FC_NAN, "power iteration broke down");
-    lam = nw / std::sqrt(vv);
-    scale_to(v.p, w.p, 1.0 / nw, n, s);
+    EpiBlockDiag<B, TP> e{w.p, Dinv};
+    sell_spmv<B, B>(S, v.p, e, s);
+    nrm2sq_dev(w.p, n, scal.p, s, part.p);
+    nrm2sq_dev(v.p, n, scal.p + 1, s, part.p);
+    k_power_scale<TP><<<grid_rows(n), kT, 0, s>>>(v.p, w.p, n, scal.p, scal.p + 1, scal.p + 2 + it);
+    FS_LAUNCHED();
   }
+  double lam = 0.0;
+  FS_CUDA(cudaMemcpyAsync(&lam, scal.p + 1 + steps, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  FS_REQUIRE(std::isfinite(lam) && lam > 0, FC_NAN, "power iteration broke down");
   return lam;
+}
+
+__global__ void k_max_len_rows(const int *rp, int n, int *out) {
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, rp[i + 1] - rp[i]);
+  atomicMax(out, m);
 }
 
 template <int B>
@@ -556,22 +598,34 @@ void build_prolongator(LevelSetup &L, const DBuf<int> &asize, int nc, double ome
   Bsr<double> &P = L.P;
   P.shape(L.nb, nc, B, B);
   P.rp.alloc(L.nb + 1);
-  DBuf<int> cnt(L.nb + 1), flag(1);
-  FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
-  k_prolong<B><<<grid_rows(L.nb), 128, 0, s>>>(S, L.agg.p, asize.p, L.Dinv.p, omega, 0, cnt.p, nullptr,
-                                               nullptr, nullptr, flag.p);
+  DBuf<int> cnt(L.nb + 1), flag(2);
+  FS_CUDA(cudaMemsetAsync(flag.p, 0, 2 * sizeof(int), s));
+  k_max_len_rows<<<blocks_for(L.nb, 256, kSMs * 4), 256, 0, s>>>(S.rp, L.nb, flag.p + 1);
+  FS_LAUNCHED();
+  int hl[2] = {0, 0};
+  FS_CUDA(cudaMemcpyAsync(hl, flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  const int cap = hl[1] > 0 ? hl[1] : 1;
+  FS_REQUIRE(cap <= 4096, FC_INTERNAL, "level operator row longer than 4096 blocks");
+  int wpb = 8;
+  while (wpb > 1 && (size_t)wpb * 3 * cap * sizeof(int) > 96 * 1024) wpb >>= 1;
+  const size_t shm = (size_t)wpb * 3 * cap * sizeof(int);
+  FS_CUDA(cudaFuncSetAttribute(k_prolong<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  const int grid = kSMs * 8;
+  k_prolong<B><<<grid, wpb * 32, shm, s>>>(S, L.agg.p, asize.p, L.Dinv.p, omega, 0, cnt.p, nullptr, nullptr,
+                                            nullptr, cap, flag.p);
   FS_LAUNCHED();
   P.nnzb = exclusive_scan(cnt.p, P.rp.p, L.nb, s);
   P.ci.alloc(P.nnzb);
   P.val.alloc(P.nnzb * B * B);
-  if (P.nnzb)
-    k_prolong<B><<<grid_rows(L.nb), 128, 0, s>>>(S, L.agg.p, asize.p, L.Dinv.p, omega, 1, nullptr, P.rp.p,
-                                                 P.ci.p, P.val.p, flag.p);
-  FS_LAUNCHED();
-  int h = 0;
-  FS_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (P.nnzb) {
+    k_prolong<B><<<grid, wpb * 32, shm, s>>>(S, L.agg.p, asize.p, L.Dinv.p, omega, 1, nullptr, P.rp.p, P.ci.p,
+                                              P.val.p, cap, flag.p);
+    FS_LAUNCHED();
+  }
+  FS_CUDA(cudaMemcpyAsync(hl, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   FS_CUDA(cudaStreamSynchronize(s));
-  FS_REQUIRE(!h, FC_INTERNAL, "prolongator row reaches more than 512 aggregates");
+  FS_REQUIRE(!hl[0], FC_INTERNAL, "prolongator row exceeds the shared capacity");
 }
 
 void invert_coarsest(Hierarchy &H, cudaStream_t s) {
@@ -613,20 +667,21 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
     if constexpr (std::is_same<TP, double>::value) {
       c.S = L.S.view();
       if (!last) { c.P = L.P.view(); c.R = L.R.view(); c.Dinv = L.Dinv.p; }
+      c.Ss = L.Ssd.nbr == L.nb && L.Ssd.sp.p ? std::move(L.Ssd) : to_sell<TP>(L.S.view(), s);
     } else {
-      c.S_own = copy_cast<TP, double>(L.S.view(), s);
-      c.S = c.S_own.view();
       if (!last) {
-        c.P_own = copy_cast<TP, double>(L.P.view(), s);
         c.R_own = copy_cast<TP, double>(L.R.view(), s);
-        c.P = c.P_own.view();
         c.R = c.R_own.view();
-        c.Dinv_own.alloc((size_t)L.nb * L.B * L.B);
-        cast(c.Dinv_own.p, L.Dinv.p, (int64_t)L.nb * L.B * L.B, s);
+        if (L.Dinvf.p) {
+          c.Dinv_own = std::move(L.Dinvf);
+        } else {
+          c.Dinv_own.alloc((size_t)L.nb * L.B * L.B);
+          cast(c.Dinv_own.p, L.Dinv.p, (int64_t)L.nb * L.B * L.B, s);
+        }
         c.Dinv = c.Dinv_own.p;
       }
+      c.Ss = L.Ssf.nbr == L.nb && L.Ssf.sp.p ? std::move(L.Ssf) : to_sell<TP>(L.S.view(), s);
     }
-    c.Ss = to_sell<TP>(L.S.view(), s);
     if (!last) c.Ps = to_sell<TP>(L.P.view(), s);
     c.f.alloc(n > 0 ? n : 1);
     c.x.alloc(n > 0 ? n : 1);
@@ -651,6 +706,7 @@ void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s)
   H.lev[0].B = B;
   H.lev[0].S = std::move(S0);
   H.lev[0].nb = H.lev[0].S.nbr;
+  PhaseTimer pt(p.verbose > 0, s, B == 3 ? "amg3" : "amg1");
   for (int l = 0;; l++) {
     LevelSetup &L = H.lev[l];
     const int nb = L.nb;
@@ -667,21 +723,37 @@ void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s)
     FS_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     FS_CUDA(cudaStreamSynchronize(s));
     FS_REQUIRE(!hf, FC_SINGULAR_BLOCK, "singular diagonal block in AMG level " + std::to_string(l));
+    pt.mark("diag");
     // strength graph and aggregates
     const double theta = p.theta0 * std::pow(p.theta_decay, l);
     Graph G = strength_graph(L.S.view(), dn.p, theta, s);
+    pt.mark("strength");
     DBuf<int> asize;
     int nc = aggregate(G, p.seed, l, L.agg, asize, p.verbose, s);
+    pt.mark("aggregate");
     if (nc == 0 || nc > p.max_ratio * nb) {
       L.Dinv.release();
       L.agg.release();
       break;
     }
-    L.lam = power_lambda<B>(L.S.view(), L.Dinv.p, p.seed, l, p.power_steps, s);
+    if (precision == FC_MIXED) {
+      L.Ssf = to_sell<float>(L.S.view(), s);
+      L.Dinvf.alloc((size_t)nb * B * B);
+      cast(L.Dinvf.p, L.Dinv.p, (int64_t)nb * B * B, s);
+      L.lam = power_lambda<B, float>(L.Ssf.view(), L.Dinvf.p, p.seed, l, p.power_steps, s);
+    } else {
+      L.Ssd = to_sell<double>(L.S.view(), s);
+      L.lam = power_lambda<B, double>(L.Ssd.view(), L.Dinv.p, p.seed, l, p.power_steps, s);
+    }
+    pt.mark("power");
     build_prolongator<B>(L, asize, nc, p.omega_num / L.lam, s);
+    pt.mark("prolongator");
     L.R = transpose(L.P.view(), s);
+    pt.mark("transpose");
     Bsr<double> SP = spgemm(L.S.view(), L.P.view(), s);
+    pt.mark("spgemm S P");
     Bsr<double> Sc = spgemm(L.R.view(), SP.view(), s);
+    pt.mark("spgemm R (S P)");
     LevelSetup next;
     next.B = B;
     next.S = std::move(Sc);
@@ -691,8 +763,10 @@ void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s)
   const int nlast = H.lev.back().nb * B;
   FS_REQUIRE(nlast <= 8192, FC_INTERNAL, "coarsest AMG level too large for the dense solve");
   invert_coarsest(H, s);
+  pt.mark("coarsest inverse");
   if (precision == FC_MIXED) prepare_cycle<float>(H, H.cf, s);
   else prepare_cycle<double>(H, H.cd, s);
+  pt.mark("cycle data");
   H.built = true;
 }
 
@@ -714,7 +788,7 @@ namespace {
 // column indices, row pointers), the iterate gathered once, f, d read and
 // written, the new iterate and the inverse diagonal blocks
 template <int B, typename TP>
-double cheb_bytes(const BsrView<TP> &S, bool read_d) {
+double cheb_bytes(const Sell<TP> &S, bool read_d) {
   const double sz = sizeof(TP);
   return (double)S.nnzb * (B * B * sz + 4) + (double)(S.nbr + 1) * 4 +
          (double)S.nbr * B * sz * (read_d ? 5 : 4) + (double)S.nbr * B * B * sz;
@@ -731,7 +805,7 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
     return;
   }
   LevelCycle<TP> &c = C[l];
-  const int64_t nb = c.S.nbr;
+  const int64_t nb = c.Ss.nbr;
   const int deg = H.prm.cheb_degree;
   TP *buf[2] = {c.xa.p, xout};
   int cur = 0;
@@ -745,7 +819,7 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
     if (pf) pf->start(PK_SMOOTH0, s);
     sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
-    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, true));
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, true));
     cur ^= 1;
     rho = rn;
   }
@@ -761,7 +835,7 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)0, (TP)(1.0 / c.theta)};
     if (pf) pf->start(PK_SMOOTH0, s);
     sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
-    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, false));
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, false));
     cur ^= 1;
   }
   for (int k = 1; k < deg; k++) {
@@ -769,7 +843,7 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
     if (pf) pf->start(PK_SMOOTH0, s);
     sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
-    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.S, true));
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, true));
     cur ^= 1;
     rho = rn;
   }

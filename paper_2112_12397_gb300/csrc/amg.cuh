@@ -29,6 +29,11 @@ struct LevelSetup {
   DBuf<double> Dinv;    // nb * B * B inverse diagonal blocks
   DBuf<int> agg;        // aggregate of each block row (-1: none)
   double lam = 0.0;     // power estimate of the largest eigenvalue of D^-1 S
+  // sliced-ELL operator and D^-1 in the cycle precision, built during setup
+  // (the power iteration runs on them) and handed to the cycle
+  Sell<float> Ssf;
+  Sell<double> Ssd;
+  DBuf<float> Dinvf;
 };
 
 // Per-level data of the cycle in precision TP.

@@ -131,6 +131,20 @@ struct Profiler {
   ~Profiler();
 };
 
+// library diagnostics level (set from fc_options.verbose by fc_setup)
+extern int g_verbose;
+
+// Wall-clock phase timer for setup diagnostics (verbose only): synchronises
+// the stream at each mark.
+struct PhaseTimer {
+  bool on;
+  cudaStream_t s;
+  double t0;
+  const char *tag;
+  PhaseTimer(bool on_, cudaStream_t s_, const char *tag_);
+  void mark(const char *what);
+};
+
 // ---------------------------------------------------------------- launch
 constexpr int kSMs = 152;
 inline int blocks_for(int64_t n, int threads, int cap = 65535 * 16) {

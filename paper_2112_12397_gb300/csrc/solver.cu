@@ -640,6 +640,8 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     cudaStream_t s = c->s;
     c->nn = nn; c->nf = nf;
     c->nu = 3LL * nn; c->nt = 3LL * nf; c->n = c->nu + c->nt + nf;
+    fs::g_verbose = c->opt.verbose;
+    PhaseTimer pt(c->opt.verbose > 0, s, "setup");
     auto up = [&](const fc_bsr &m) {
       return upload_bsr(m.n_brows, m.n_bcols, m.br, m.bc, m.nnzb, m.d_row_ptr, m.d_col_idx, m.d_val, s);
     };
@@ -649,11 +651,14 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     c->sQ1 = to_sell<double>(c->Q1.view(), s); c->sC2 = to_sell<double>(c->C2.view(), s);
     c->sH = to_sell<double>(c->H.view(), s); c->sQ2 = to_sell<double>(c->Q2.view(), s);
     c->sT = to_sell<double>(c->T.view(), s);
+    pt.mark("upload + sell");
     for (auto &h : c->hier) h = Hierarchy();
     c->pf = PrecData<float>();
     c->pd = PrecData<double>();
+    pt.mark("free old");
     build_hinv(c->H.view(), c->Hinv64, s);                                        // Alg. 1/3 line 1
     c->S1 = build_s1(c->A.view(), c->C1.view(), c->C2.view(), c->Hinv64.p, s);   // Alg. 3 line 2
+    pt.mark("S1");
     const int prec = c->opt.precision;
     c->have[FC_TPU] = (c->opt.variants >> FC_TPU) & 1;
     c->have[FC_TUP] = (c->opt.variants >> FC_TUP) & 1;
@@ -664,14 +669,17 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     }
     if (c->have[FC_TUP]) {
       c->S2t = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s);  // Alg. 3 line 3
+      pt.mark("S2tilde (fixed stress)");
       amg_setup(c->hier[FC_H_TUP_U], copy_cast<double, double>(c->S1.view(), s), 3, amg_params(c->opt, false), prec, s);
       if (nf) amg_setup(c->hier[FC_H_TUP_P], copy_cast<double, double>(c->S2t.view(), s), 1, amg_params(c->opt, true), prec, s);
     }
     c->hier[FC_H_TPU_U].prof = &c->prof;
     c->hier[FC_H_TUP_U].prof = &c->prof;
+    pt.mark("hierarchies");
     if (prec == FC_MIXED) prepare_prec<float>(*c, c->pf);
     else prepare_prec<double>(*c, c->pd);
     c->xk.alloc(c->n); c->rk.alloc(c->n);
+    pt.mark("prec data");
     FS_CUDA(cudaStreamSynchronize(s));
     c->ready = true;
     return FC_OK;

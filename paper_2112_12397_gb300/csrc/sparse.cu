@@ -26,24 +26,54 @@ __global__ void k_scatter_t(BsrView<double> A, const int *rpT, int *cursor, int 
   }
 }
 
-// insertion sort of each row by column, carrying the source index
-__global__ void k_sort_rows(int nr, const int *rp, int *ci, int64_t *src) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int s = rp[i], e = rp[i + 1];
-    for (int a = s + 1; a < e; a++) {
-      int key = ci[a];
-      int64_t ks = src[a];
-      int b = a - 1;
-      while (b >= s && ci[b] > key) {
-        ci[b + 1] = ci[b];
-        src[b + 1] = src[b];
-        b--;
+// Sort each row by column, carrying the source index: one warp per row ranks
+// its entries in shared memory (rank = number of smaller columns; columns in
+// a transposed row are distinct); rows above the shared capacity fall back
+// to an insertion sort by one lane.
+__global__ void k_sort_rows(int nr, const int *rp, int *ci, int64_t *src, int cap) {
+  extern __shared__ int64_t sh_src[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  int64_t *ws = sh_src + (size_t)wid * cap;
+  int *wc = reinterpret_cast<int *>(sh_src + (size_t)wpb * cap) + (size_t)wid * cap;
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  for (int64_t i = blockIdx.x * (int64_t)wpb + wid; i < nr; i += nwarps) {
+    const int s = rp[i], e = rp[i + 1], len = e - s;
+    if (len <= 1) continue;
+    if (len <= cap) {
+      for (int t = lane; t < len; t += 32) { wc[t] = ci[s + t]; ws[t] = src[s + t]; }
+      __syncwarp();
+      for (int t = lane; t < len; t += 32) {
+        const int key = wc[t];
+        int rank = 0;
+        for (int u = 0; u < len; u++) rank += (wc[u] < key);
+        ci[s + rank] = key;
+        src[s + rank] = ws[t];
       }
-      ci[b + 1] = key;
-      src[b + 1] = ks;
+      __syncwarp();
+    } else if (lane == 0) {
+      for (int a = s + 1; a < e; a++) {
+        int key = ci[a];
+        int64_t ks = src[a];
+        int b = a - 1;
+        while (b >= s && ci[b] > key) {
+          ci[b + 1] = ci[b];
+          src[b + 1] = src[b];
+          b--;
+        }
+        ci[b + 1] = key;
+        src[b + 1] = ks;
+      }
     }
+    __syncwarp();
   }
+}
+
+__global__ void k_max_len(const int *rp, int n, int *out) {
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, rp[i + 1] - rp[i]);
+  atomicMax(out, m);
 }
 
 __global__ void k_gather_t(int64_t nnz, const int64_t *src, const double *val, int br, int bc,
@@ -79,8 +109,23 @@ Bsr<double> transpose(const BsrView<double> &A, cudaStream_t s) {
   FS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (A.nbc + 1), s));
   k_scatter_t<<<blocks_for(A.nbr, 128, kSMs * 8), 128, 0, s>>>(A, T.rp.p, cnt.p, T.ci.p, src.p);
   FS_LAUNCHED();
-  k_sort_rows<<<blocks_for(A.nbc, 128, kSMs * 8), 128, 0, s>>>(A.nbc, T.rp.p, T.ci.p, src.p);
-  FS_LAUNCHED();
+  {
+    DBuf<int> mx(1);
+    FS_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
+    k_max_len<<<blocks_for(A.nbc, 256, kSMs * 4), 256, 0, s>>>(T.rp.p, A.nbc, mx.p);
+    FS_LAUNCHED();
+    int umax = 0;
+    FS_CUDA(cudaMemcpyAsync(&umax, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+    const size_t per = sizeof(int64_t) + sizeof(int);
+    int cap = umax > 1 ? umax : 2, wpb = 8;
+    while (wpb > 1 && (size_t)wpb * cap * per > 192 * 1024) wpb >>= 1;
+    if ((size_t)wpb * cap * per > 192 * 1024) cap = (int)(192 * 1024 / per);
+    const size_t shm = (size_t)wpb * cap * per;
+    FS_CUDA(cudaFuncSetAttribute(k_sort_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_sort_rows<<<kSMs * 4, wpb * 32, shm, s>>>(A.nbc, T.rp.p, T.ci.p, src.p, cap);
+    FS_LAUNCHED();
+  }
   k_gather_t<<<blocks_for(nnz, 256, kSMs * 8), 256, 0, s>>>(nnz, src.p, A.val, A.br, A.bc, T.val.p);
   FS_LAUNCHED();
   FS_CUDA(cudaStreamSynchronize(s));
@@ -162,14 +207,120 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
+// Numeric pass, one warp per row of C, FP64 work spread over all lanes.
+// The row's sorted columns and accumulators live in shared memory.  The
+// products (e, f) of the row (e: entry k of A's row, f: entry j of B's row
+// k) are enumerated in order, in chunks; each product adds BR block-row
+// contributions, and the unit (slot p of column j, block row r) is owned by
+// lane (p * BR + r) mod 32.  Each lane gathers the products that touch its
+// units (in enumeration order) and computes them, so every entry of C is
+// summed in the same order on every run, with no atomics.
+constexpr int kProdChunk = 256;
+
+template <int BR, int BK, int BC>
+__global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC,
+                                    double *valC, int ucap) {
+  constexpr int BS = BR * BC;
+  extern __shared__ double smem[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  double *acc = smem + (size_t)wid * ucap * BS;
+  int *ibase = reinterpret_cast<int *>(smem + (size_t)wpb * ucap * BS);
+  int *cols = ibase + (size_t)wid * (ucap + 4 * kProdChunk * BR);
+  int *ch_e = cols + ucap;
+  int *ch_f = ch_e + kProdChunk;
+  int *ch_p = ch_f + kProdChunk;
+  int *list = ch_p + kProdChunk;              // kProdChunk * BR unit-product slots
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  for (int64_t i = blockIdx.x * (int64_t)wpb + wid; i < A.nbr; i += nwarps) {
+    const int cs = rpC[i], cn = rpC[i + 1] - cs;
+    if (cn > ucap) continue;   // handled by the global-memory kernel
+    for (int t = lane; t < cn; t += 32) cols[t] = ciC[cs + t];
+    for (int t = lane; t < cn * BS; t += 32) acc[t] = 0.0;
+    __syncwarp();
+    int cnt = 0;
+    auto flush = [&]() {
+      // units owned by this lane: u = p * BR + r with (u & 31) == lane
+      int mine = 0;
+      for (int t = 0; t < cnt; t++) {
+        const int p = ch_p[t];
+        if (p < 0) continue;
+#pragma unroll
+        for (int r = 0; r < BR; r++) mine += (((p * BR + r) & 31) == lane);
+      }
+      int off = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += y;
+      }
+      off -= mine;
+      int mx = mine;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int w = off;
+      for (int t = 0; t < cnt; t++) {
+        const int p = ch_p[t];
+        if (p < 0) continue;
+#pragma unroll
+        for (int r = 0; r < BR; r++)
+          if (((p * BR + r) & 31) == lane) list[w++] = t * BR + r;
+      }
+      __syncwarp();
+      for (int q = 0; q < mx; q++) {
+        if (q < mine) {
+          const int code = list[off + q];
+          const int t = code / BR, r = code - t * BR;
+          const double *a = A.val + (int64_t)ch_e[t] * BR * BK + r * BK;
+          const double *b = B.val + (int64_t)ch_f[t] * BK * BC;
+          double *c = acc + ch_p[t] * BS + r * BC;
+          double av[BK];
+#pragma unroll
+          for (int tt = 0; tt < BK; tt++) av[tt] = a[tt];
+#pragma unroll
+          for (int cc = 0; cc < BC; cc++) {
+            double sum = 0.0;
+#pragma unroll
+            for (int tt = 0; tt < BK; tt++) sum += av[tt] * b[tt * BC + cc];
+            c[cc] += sum;
+          }
+        }
+      }
+      __syncwarp();
+      cnt = 0;
+    };
+    for (int e = A.rp[i]; e < A.rp[i + 1]; e++) {
+      const int k = A.ci[e];
+      const int f0 = B.rp[k], f1 = B.rp[k + 1];
+      for (int fb = f0; fb < f1; fb += 32) {
+        const int len = min(32, f1 - fb);
+        if (cnt + len > kProdChunk) flush();
+        if (lane < len) {
+          const int f = fb + lane;
+          ch_e[cnt + lane] = e;
+          ch_f[cnt + lane] = f;
+          ch_p[cnt + lane] = find_sorted(cols, cn, B.ci[f]);
+        }
+        __syncwarp();
+        cnt += len;
+      }
+    }
+    if (cnt) flush();
+    for (int t = lane; t < cn * BS; t += 32) valC[(int64_t)cs * BS + t] = acc[t];
+    __syncwarp();
+  }
+}
+
+// Fallback for rows longer than the shared capacity: same order, global slots.
 template <int BR, int BK, int BC>
 __global__ void __launch_bounds__(128)
     k_spgemm_numeric(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC,
-                     double *valC) {
+                     double *valC, int ucap) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid; i < A.nbr; i += nwarps) {
     const int cs = rpC[i], cn = rpC[i + 1] - cs;
+    if (cn <= ucap) continue;
     for (int e = A.rp[i]; e < A.rp[i + 1]; e++) {
       const int k = A.ci[e];
       double a[BR * BK];
@@ -195,6 +346,44 @@ __global__ void __launch_bounds__(128)
     }
   }
 }
+
+__global__ void k_max_row_len(const int *rp, int n, int *out) {
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, rp[i + 1] - rp[i]);
+  atomicMax(out, m);
+}
+
+template <int BR, int BK, int BC>
+void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s) {
+  constexpr int BS = BR * BC;
+  DBuf<int> mx(1);
+  FS_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
+  k_max_row_len<<<blocks_for(C.nbr, 256, kSMs * 4), 256, 0, s>>>(C.rp.p, C.nbr, mx.p);
+  FS_LAUNCHED();
+  int umax = 0;
+  FS_CUDA(cudaMemcpyAsync(&umax, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  // shared per warp: ucap slots (accumulator + column) and the product chunk;
+  // fit up to 8 warps in ~200 KB
+  const size_t per_slot = BS * sizeof(double) + sizeof(int);
+  const size_t fixed = (size_t)4 * kProdChunk * BR * sizeof(int);
+  int ucap = umax > 0 ? umax : 1;
+  int wpb = 8;
+  while (wpb > 1 && (size_t)wpb * (ucap * per_slot + fixed) > 200 * 1024) wpb >>= 1;
+  if ((size_t)wpb * (ucap * per_slot + fixed) > 200 * 1024) ucap = (int)((200 * 1024 - fixed) / per_slot);
+  const size_t shm = (size_t)wpb * (ucap * per_slot + fixed);
+  auto kern = k_spgemm_numeric_sh<BR, BK, BC>;
+  FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  kern<<<kSMs * 4, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, ucap);
+  FS_LAUNCHED();
+  if (umax > ucap) {
+    k_spgemm_numeric<BR, BK, BC><<<kSMs * 8, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, ucap);
+    FS_LAUNCHED();
+  }
+}
+
 }  // namespace
 
 Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s) {
@@ -206,10 +395,12 @@ Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStrea
   FS_CUDA(cudaMemsetAsync(ovf.p, 0, sizeof(int), s));
   FS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (A.nbr + 1), s));
   const int grid = kSMs * 8;
+  PhaseTimer pt(g_verbose > 1, s, "spgemm");
   if (A.nbr > 0) {
     k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 0, cnt.p, nullptr, nullptr, ovf.p);
     FS_LAUNCHED();
   }
+  pt.mark("symbolic count");
   int64_t nnz = exclusive_scan(cnt.p, C.rp.p, A.nbr, s);
   int hovf = 0;
   FS_CUDA(cudaMemcpy(&hovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
@@ -218,19 +409,25 @@ Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStrea
   C.ci.alloc(nnz);
   C.val.alloc(nnz * C.br * C.bc);
   if (nnz == 0) return C;
+  pt.mark("scan + alloc");
   k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 1, nullptr, C.rp.p, C.ci.p, ovf.p);
   FS_LAUNCHED();
+  pt.mark("symbolic fill");
+  // rows longer than the shared capacity accumulate in place in C.val
   FS_CUDA(cudaMemsetAsync(C.val.p, 0, sizeof(double) * nnz * C.br * C.bc, s));
   const int sh = A.br * 100 + A.bc * 10 + B.bc;
   switch (sh) {
-    case 333: k_spgemm_numeric<3, 3, 3><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
-    case 313: k_spgemm_numeric<3, 1, 3><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
-    case 111: k_spgemm_numeric<1, 1, 1><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
-    case 331: k_spgemm_numeric<3, 3, 1><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
-    case 133: k_spgemm_numeric<1, 3, 3><<<grid, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p); break;
+    case 333: numeric<3, 3, 3>(A, B, C, s); break;
+    case 313: numeric<3, 1, 3>(A, B, C, s); break;
+    case 111: numeric<1, 1, 1>(A, B, C, s); break;
+    case 331: numeric<3, 3, 1>(A, B, C, s); break;
+    case 133: numeric<1, 3, 3>(A, B, C, s); break;
     default: throw Error(FC_BAD_ARG, "spgemm: unsupported block shapes");
   }
-  FS_LAUNCHED();
+  pt.mark("numeric");
+  if (g_verbose > 1)
+    fprintf(stderr, "[fracsolve] spgemm %d x %d blocks (%dx%d * %dx%d): A %lld, B %lld, C %lld blocks\n", A.nbr, B.nbc,
+            A.br, A.bc, B.br, B.bc, (long long)A.nnzb, (long long)B.nnzb, (long long)nnz);
   FS_CUDA(cudaStreamSynchronize(s));
   return C;
 }

@@ -2,9 +2,11 @@
 #include "common.cuh"
 
 #include <atomic>
+#include <ctime>
 
 namespace fs {
 
+int g_verbose = 0;
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(); }
@@ -49,6 +51,25 @@ void Profiler::stats(int k, int64_t *launches, double *ms, double *b) {
 }
 Profiler::~Profiler() {
   for (auto e : pool) cudaEventDestroy(e);
+}
+
+static double wall_ms() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return ts.tv_sec * 1e3 + ts.tv_nsec * 1e-6;
+}
+PhaseTimer::PhaseTimer(bool on_, cudaStream_t s_, const char *tag_) : on(on_), s(s_), t0(0), tag(tag_) {
+  if (on) {
+    cudaStreamSynchronize(s);
+    t0 = wall_ms();
+  }
+}
+void PhaseTimer::mark(const char *what) {
+  if (!on) return;
+  cudaStreamSynchronize(s);
+  double t = wall_ms();
+  fprintf(stderr, "[fracsolve] %s %-28s %9.2f ms\n", tag, what, t - t0);
+  t0 = t;
 }
 
 void cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
