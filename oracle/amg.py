@@ -298,5 +298,50 @@ class AMG:
     def __call__(self, f: np.ndarray) -> np.ndarray:
         return self.vcycle(np.asarray(f, dtype=np.float64))
 
+    # -------------------------------------------------------------- transpose
+    # The V-cycle is a linear operator B(S).  With the same polynomial
+    # smoother before and after the correction and R = P^T, its transpose is
+    # the same cycle run on the transposed level operators S_l^T (the
+    # Galerkin coarse operators transpose accordingly: R S^T P = (R S P)^T),
+    # with the transposed diagonal blocks and the transposed coarsest solve.
+    def _cheb_t(self, L: Level, f: np.ndarray, x0):
+        St = L.S.T.tocsr()
+        DinvT = np.transpose(L.Dinv, (0, 2, 1))
+        hi = self.opt.cheb_hi * L.lam
+        lo = self.opt.cheb_lo * hi
+        theta = 0.5 * (hi + lo)
+        delta = 0.5 * (hi - lo)
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        if x0 is None:
+            r = f
+            x = np.zeros_like(f)
+        else:
+            r = f - St @ x0
+            x = x0
+        d = apply_blockdiag(DinvT, r) / theta
+        x = x + d
+        for _ in range(1, self.opt.cheb_degree):
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            r = f - St @ x
+            d = (rho_new * rho) * d + (2.0 * rho_new / delta) * apply_blockdiag(DinvT, r)
+            x = x + d
+            rho = rho_new
+        return x
+
+    def vcycle_t(self, f: np.ndarray, lvl: int = 0) -> np.ndarray:
+        """Apply B^T, the transpose of the V-cycle operator."""
+        f = np.asarray(f, dtype=np.float64)
+        L = self.levels[lvl]
+        if lvl == len(self.levels) - 1:
+            if L.S.shape[0] == 0:
+                return np.zeros_like(f)
+            return sla.lu_solve(self.lu, f, trans=1)
+        x = self._cheb_t(L, f, None)
+        r = f - L.S.T @ x
+        ec = self.vcycle_t(L.R @ r, lvl + 1)
+        x = x + L.P @ ec
+        return self._cheb_t(L, f, x)
+
     def describe(self) -> list[tuple[int, int]]:
         return [(L.n, L.S.nnz) for L in self.levels]
