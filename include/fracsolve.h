@@ -171,6 +171,25 @@ int fc_solve(fc_ctx *ctx, int variant, const double *d_b, double *d_x, double to
 int fc_solve_host(fc_ctx *ctx, int variant, const double *h_b, double *h_x, double tol,
                   int maxit, int *iters, double *relres);
 
+/* ---------------- adjoint (transposed system) ---------------- */
+/* The adjoint data (transposed blocks, transposed preconditioner blocks and
+ * transposed AMG cycles) is built on the first adjoint call after fc_setup. */
+
+/* d_y = J^T d_x (double, device, length n). */
+int fc_spmv_adjoint(fc_ctx *ctx, const double *d_x, double *d_y);
+
+/* d_v = M^-T d_w: the transposes of the block factorisations of Eq. P1
+ * (FC_TPU) or Eq. P2 (FC_TUP), factors applied in reverse order, with the
+ * transposed V-cycle for S~ / S1 (the V-cycles of the symmetric T and S~2 are
+ * symmetric). */
+int fc_apply_prec_adjoint(fc_ctx *ctx, int variant, const double *d_w, double *d_v);
+
+/* Solve J^T lambda = g by right-preconditioned FGMRES-CGS2 with M^-T, same
+ * stopping rule and return values as fc_solve.  The Krylov basis of the
+ * forward solve is not used (it is recomputed, not stored). */
+int fc_solve_adjoint(fc_ctx *ctx, int variant, const double *d_g, double *d_lambda, double tol,
+                     int maxit, int *iters, double *relres);
+
 /* ---------------- inspection (used by the parity tests) ---------------- */
 
 /* Hierarchies: FC_H_TPU_U = AMG of S~, FC_H_TPU_P = AMG of T,
@@ -197,6 +216,9 @@ int fc_get_aggregates(fc_ctx *ctx, int hier, int level, int32_t *h_agg, double *
 /* One V-cycle of hierarchy `hier` applied to the device vector d_f (length =
  * scalar rows of level 0), result in d_x. */
 int fc_vcycle(fc_ctx *ctx, int hier, const double *d_f, double *d_x);
+
+/* One transposed V-cycle (B^T) of hierarchy `hier` on device vectors. */
+int fc_vcycle_adjoint(fc_ctx *ctx, int hier, const double *d_f, double *d_x);
 
 /* The fixed-stress diagonal [S_K]_k of Eq. FS_algebraic to HOST (n_face). */
 int fc_get_fixed_stress(fc_ctx *ctx, double *h_sk);

@@ -25,7 +25,8 @@ VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP}
 
 # exported symbols declared by include/fracsolve.h
 SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_residual", "fc_residual_noalloc",
-           "fc_apply_prec", "fc_solve",
+           "fc_apply_prec", "fc_solve", "fc_spmv_adjoint", "fc_apply_prec_adjoint", "fc_solve_adjoint",
+           "fc_vcycle_adjoint",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
            "fc_get_fixed_stress", "fc_profile", "fc_kernel_stats", "fc_launch_count", "fc_destroy",
            "fc_strerror", "fc_last_error"]
@@ -85,6 +86,10 @@ def load(build_if_missing: bool = False):
         "fc_apply_prec": (C.c_int, [vp, C.c_int, vp, vp]),
         "fc_solve": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
         "fc_solve_host": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
+        "fc_spmv_adjoint": (C.c_int, [vp, vp, vp]),
+        "fc_apply_prec_adjoint": (C.c_int, [vp, C.c_int, vp, vp]),
+        "fc_solve_adjoint": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
+        "fc_vcycle_adjoint": (C.c_int, [vp, C.c_int, vp, vp]),
         "fc_num_levels": (C.c_int, [vp, C.c_int, pint]),
         "fc_get_bsr": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, pi32, pi32, pi32, pi32, pi64, vp, vp, vp]),
         "fc_get_aggregates": (C.c_int, [vp, C.c_int, C.c_int, vp, pd]),
@@ -203,6 +208,23 @@ class Context:
         rc = self._check(self.lib.fc_solve_host(self.h, VARIANTS[variant], C.c_void_p(bp), C.c_void_p(xp), tol,
                                                 maxit, C.byref(it), C.byref(rr)), self.h, ok)
         return rc, it.value, rr.value
+
+    # ------------------------------------------------------------ adjoint
+    def spmv_adjoint(self, x, y):
+        self._check(self.lib.fc_spmv_adjoint(self.h, _ptr(x), _ptr(y)), self.h)
+
+    def apply_prec_adjoint(self, variant: str, w, v):
+        self._check(self.lib.fc_apply_prec_adjoint(self.h, VARIANTS[variant], _ptr(w), _ptr(v)), self.h)
+
+    def solve_adjoint(self, variant: str, g, lam, tol: float = 1e-8, maxit: int = 500, allow_fail: bool = False):
+        it, rr = C.c_int(0), C.c_double(0)
+        ok = (FC_OK, FC_NOT_CONVERGED, FC_BREAKDOWN) if allow_fail else (FC_OK,)
+        rc = self._check(self.lib.fc_solve_adjoint(self.h, VARIANTS[variant], _ptr(g), _ptr(lam), tol, maxit,
+                                                   C.byref(it), C.byref(rr)), self.h, ok)
+        return rc, it.value, rr.value
+
+    def vcycle_adjoint(self, hier: int, f, x):
+        self._check(self.lib.fc_vcycle_adjoint(self.h, hier, _ptr(f), _ptr(x)), self.h)
 
     # ------------------------------------------------------------ inspection
     def num_levels(self, hier: int) -> int:

@@ -794,55 +794,58 @@ double cheb_bytes(const Sell<TP> &S, bool read_d) {
          (double)S.nbr * B * sz * (read_d ? 5 : 4) + (double)S.nbr * B * B * sz;
 }
 
-template <int B, typename TP>
+template <int B, typename TP, bool TR = false>
 void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *f, TP *xout, cudaStream_t s) {
   const int L = (int)C.size();
   if (l == L - 1) {
     const int n = H.nc_scalar;
     if (n == 0) return;
-    k_dense_gemv<TP><<<blocks_for((int64_t)n * 32, 256, kSMs * 16), 256, 0, s>>>(n, H.cinv.p, f, xout);
+    k_dense_gemv<TP><<<blocks_for((int64_t)n * 32, 256, kSMs * 16), 256, 0, s>>>(n, TR ? H.cinvT.p : H.cinv.p,
+                                                                                 f, xout);
     FS_LAUNCHED();
     return;
   }
   LevelCycle<TP> &c = C[l];
+  const SellView<TP> Sop = TR ? c.SsT.view() : c.Ss.view();
+  const TP *Dv = TR ? c.DinvT.p : c.Dinv;
   const int64_t nb = c.Ss.nbr;
   const int deg = H.prm.cheb_degree;
   TP *buf[2] = {c.xa.p, xout};
   int cur = 0;
   // pre-smoothing from x = 0
   double rho = 1.0 / c.sigma;
-  k_cheb_zero<B, TP><<<grid_rows(nb), kT, 0, s>>>(nb, f, c.Dinv, (TP)(1.0 / c.theta), c.d.p, buf[cur]);
+  k_cheb_zero<B, TP><<<grid_rows(nb), kT, 0, s>>>(nb, f, Dv, (TP)(1.0 / c.theta), c.d.p, buf[cur]);
   FS_LAUNCHED();
-  Profiler *pf = (l == 0) ? H.prof : nullptr;
+  Profiler *pf = (l == 0 && !TR) ? H.prof : nullptr;
   for (int k = 1; k < deg; k++) {
     double rn = 1.0 / (2.0 * c.sigma - rho);
-    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
+    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, Dv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
+    sell_spmv<B, B>(Sop, buf[cur], e, s);
     if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, true));
     cur ^= 1;
     rho = rn;
   }
   // residual, restriction, coarse correction, prolongation
-  sell_axpby<B, B>(c.Ss.view(), buf[cur], c.r.p, -1.0, 1.0, f, s);
+  sell_axpby<B, B>(Sop, buf[cur], c.r.p, -1.0, 1.0, f, s);
   LevelCycle<TP> &cn = C[l + 1];
   spmv_axpby<B, B>(c.R, c.r.p, cn.f.p, 1.0, 0.0, (const TP *)nullptr, s);
-  cycle_level<B, TP>(H, C, l + 1, cn.f.p, cn.x.p, s);
+  cycle_level<B, TP, TR>(H, C, l + 1, cn.f.p, cn.x.p, s);
   sell_axpby<B, B>(c.Ps.view(), cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
   // post-smoothing from the corrected iterate
   rho = 1.0 / c.sigma;
   {
-    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)0, (TP)(1.0 / c.theta)};
+    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, Dv, (TP)0, (TP)(1.0 / c.theta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
+    sell_spmv<B, B>(Sop, buf[cur], e, s);
     if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, false));
     cur ^= 1;
   }
   for (int k = 1; k < deg; k++) {
     double rn = 1.0 / (2.0 * c.sigma - rho);
-    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, c.Dinv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
+    EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, Dv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    sell_spmv<B, B>(c.Ss.view(), buf[cur], e, s);
+    sell_spmv<B, B>(Sop, buf[cur], e, s);
     if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, true));
     cur ^= 1;
     rho = rn;
@@ -863,5 +866,66 @@ void amg_vcycle(Hierarchy &H, const TP *f, TP *x, cudaStream_t s) {
 
 template void amg_vcycle<float>(Hierarchy &, const float *, float *, cudaStream_t);
 template void amg_vcycle<double>(Hierarchy &, const double *, double *, cudaStream_t);
+
+namespace {
+template <typename T>
+__global__ void k_transpose_blocks(int64_t nb, int B, const T *in, T *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nb;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int r = 0; r < B; r++)
+      for (int c = 0; c < B; c++) out[i * B * B + c * B + r] = in[i * B * B + r * B + c];
+}
+__global__ void k_transpose_dense(int n, const double *in, double *out) {
+  int64_t total = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t / n), j = (int)(t - (int64_t)i * n);
+    out[(int64_t)j * n + i] = in[t];
+  }
+}
+
+template <typename TP>
+void prepare_transpose(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s) {
+  for (size_t l = 0; l < H.lev.size(); l++) {
+    LevelSetup &L = H.lev[l];
+    LevelCycle<TP> &c = C[l];
+    if (l + 1 == H.lev.size()) break;   // the coarsest level uses cinvT
+    Bsr<double> St = transpose(L.S.view(), s);
+    c.SsT = to_sell<TP>(St.view(), s);
+    const int64_t nb = L.nb;
+    c.DinvT.alloc((size_t)nb * L.B * L.B);
+    k_transpose_blocks<TP><<<blocks_for(nb, 256, kSMs * 8), 256, 0, s>>>(nb, L.B, c.Dinv, c.DinvT.p);
+    FS_LAUNCHED();
+  }
+  const int n = H.nc_scalar;
+  H.cinvT.alloc((size_t)n * n > 0 ? (size_t)n * n : 1);
+  if (n) {
+    k_transpose_dense<<<blocks_for((int64_t)n * n, 256, kSMs * 8), 256, 0, s>>>(n, H.cinv.p, H.cinvT.p);
+    FS_LAUNCHED();
+  }
+  FS_CUDA(cudaStreamSynchronize(s));
+}
+}  // namespace
+
+void amg_prepare_transpose(Hierarchy &H, int precision, cudaStream_t s) {
+  FS_REQUIRE(H.built, FC_NOT_SETUP, "AMG hierarchy not built");
+  if (H.have_t) return;
+  if (precision == FC_MIXED) prepare_transpose<float>(H, H.cf, s);
+  else prepare_transpose<double>(H, H.cd, s);
+  H.have_t = true;
+}
+
+template <typename TP>
+void amg_vcycle_t(Hierarchy &H, const TP *f, TP *x, cudaStream_t s) {
+  FS_REQUIRE(H.built && H.have_t, FC_NOT_SETUP, "transposed AMG cycle not prepared");
+  std::vector<LevelCycle<TP>> *C;
+  if constexpr (std::is_same<TP, float>::value) C = &H.cf;
+  else C = &H.cd;
+  FS_REQUIRE(!C->empty(), FC_NOT_SETUP, "AMG cycle data not prepared for this precision");
+  if (H.B == 3) cycle_level<3, TP, true>(H, *C, 0, f, x, s);
+  else cycle_level<1, TP, true>(H, *C, 0, f, x, s);
+}
+template void amg_vcycle_t<float>(Hierarchy &, const float *, float *, cudaStream_t);
+template void amg_vcycle_t<double>(Hierarchy &, const double *, double *, cudaStream_t);
 
 }  // namespace fs

@@ -43,6 +43,8 @@ struct LevelCycle {
   const TP *Dinv = nullptr;
   Bsr<TP> S_own, P_own, R_own;   // used when TP differs from double
   Sell<TP> Ss, Ps;               // sliced-ELL copies of S and P used by the cycle
+  Sell<TP> SsT;                  // S^T for the transposed cycle (adjoint solves)
+  DBuf<TP> DinvT;                // transposed diagonal blocks
   DBuf<TP> Dinv_own;
   DBuf<TP> f, x, xa, d, r;       // right-hand side, iterate (two buffers), direction, residual
   double theta = 0, delta = 0, sigma = 0;
@@ -59,6 +61,8 @@ struct Hierarchy {
   std::vector<LevelCycle<float>> cf;
   std::vector<LevelCycle<double>> cd;
   Profiler *prof = nullptr;      // times the level-0 smoother steps when set
+  bool have_t = false;           // transposed cycle data built
+  DBuf<double> cinvT;            // transposed coarsest inverse
   int levels() const { return (int)lev.size(); }
 };
 
@@ -70,5 +74,14 @@ void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int 
 // x = V-cycle(f) with zero initial guess; f and x have nb(0) * B entries.
 template <typename TP>
 void amg_vcycle(Hierarchy &H, const TP *f, TP *x, cudaStream_t s);
+
+// Data of the transposed cycle: S_l^T, transposed diagonal blocks and
+// coarsest inverse (P and R are shared with the forward cycle).
+void amg_prepare_transpose(Hierarchy &H, int precision, cudaStream_t s);
+
+// x = B^T f: the transpose of the V-cycle operator, i.e. the same cycle on
+// the transposed level operators.
+template <typename TP>
+void amg_vcycle_t(Hierarchy &H, const TP *f, TP *x, cudaStream_t s);
 
 }  // namespace fs

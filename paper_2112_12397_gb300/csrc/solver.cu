@@ -26,6 +26,9 @@ struct PrecData {
   Bsr<TP> C1o, Q1o, C2o, Q2o;
   DBuf<TP> Hinvo;
   Sell<TP> sC1, sQ1, sC2, sQ2;   // sliced-ELL copies used by the products
+  Sell<TP> tC1, tQ1, tC2, tQ2;   // transposes, for the adjoint preconditioner
+  DBuf<TP> HinvT;                // transposed H~^-1 blocks
+  bool ready_t = false;
   DBuf<TP> w, out, tt, tu, su, tp, sp, vp;
   bool ready = false;
 };
@@ -183,6 +186,8 @@ struct fc_ctx {
   int64_t n = 0, nu = 0, nt = 0;
   Bsr<double> A, C1, Q1, C2, H, Q2, T;
   Sell<double> sA, sC1, sQ1, sC2, sH, sQ2, sT;   // sliced-ELL copies for J z
+  Sell<double> tA, tC1, tQ1, tC2, tH, tQ2, tT;   // transposed blocks for J^T z
+  bool have_adj = false;
   DBuf<double> Hinv64, SK;
   Bsr<double> S1, St, S2t;
   bool have[2] = {false, false};
@@ -321,6 +326,64 @@ void jac_spmv(fc_ctx &c, const TX *z, double *y) {
   c.prof.stop(PK_JAC, s, bytes);
 }
 
+// y = J^T z (double out): rows u [A^T C2^T Q2^T], rows t [C1^T -H^T 0],
+// rows p [Q1^T 0 T^T]
+template <typename TX>
+void jac_spmv_t(fc_ctx &c, const TX *z, double *y) {
+  cudaStream_t s = c.s;
+  const TX *z_u = z, *z_t = z + c.nu, *z_p = z + c.nu + c.nt;
+  double *y_u = y, *y_t = y + c.nu, *y_p = y + c.nu + c.nt;
+  sell_axpby<3, 3>(c.tA.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
+  if (c.nf) {
+    sell_axpby<3, 3>(c.tC2.view(), z_t, y_u, 1.0, 1.0, y_u, s);
+    sell_axpby<3, 1>(c.tQ2.view(), z_p, y_u, 1.0, 1.0, y_u, s);
+    sell_axpby<3, 3>(c.tC1.view(), z_u, y_t, 1.0, 0.0, (const double *)nullptr, s);
+    sell_axpby<3, 3>(c.tH.view(), z_t, y_t, -1.0, 1.0, y_t, s);
+    sell_axpby<1, 3>(c.tQ1.view(), z_u, y_p, 1.0, 0.0, (const double *)nullptr, s);
+    sell_axpby<1, 1>(c.tT.view(), z_p, y_p, 1.0, 1.0, y_p, s);
+  }
+}
+
+// z = M^-T w in precision TP: the transposed block factorisations of Eq. P1 /
+// Eq. P2 applied in reverse order (transposed V-cycles for S~ / S1; T and
+// S~2 are symmetric and so are their scalar V-cycles)
+template <typename TP>
+void apply_prec_t(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
+  cudaStream_t s = c.s;
+  const int64_t nu = c.nu, nt = c.nt, nf = c.nf;
+  const TP *w_u = w, *w_t = w + nu, *w_p = w + nu + nt;
+  TP *z_u = z, *z_t = z + nu, *z_p = z + nu + nt;
+  if (variant == FC_TUP) {
+    Hierarchy &Hu = c.hier[FC_H_TUP_U], &Hp = c.hier[FC_H_TUP_P];
+    if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.HinvT.p, w_t, P.tt.p); FS_LAUNCHED(); }
+    sell_axpby<3, 3>(P.tC2.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);        // t_u = w_u + C2^T H~^-T w_t
+    amg_vcycle_t<TP>(Hu, P.tu.p, P.su.p, s);                                  // s_u = AMG^T(S1, t_u)
+    sell_axpby<1, 3>(P.tQ1.view(), P.su.p, P.tp.p, -1.0, 1.0, w_p, s);       // t_p = w_p - Q1^T s_u
+    if (nf) amg_vcycle<TP>(Hp, P.tp.p, z_p, s);                               // v_p = S~2^-T t_p
+    sell_axpby<3, 1>(P.tQ2.view(), z_p, P.tu.p, 1.0, 0.0, (const TP *)nullptr, s);
+    amg_vcycle_t<TP>(Hu, P.tu.p, z_u, s);                                     // AMG^T(S1, Q2^T v_p)
+    axpbyz(z_u, P.su.p, z_u, 1.0, -1.0, nu, s);                               // v_u = s_u - ...
+    if (nf) {                                                                 // v_t = H~^-T (C1^T v_u - w_t)
+      EpiHinvUpdate<TP> e{z_t, P.tt.p, P.HinvT.p};
+      sell_spmv<3, 3>(P.tC1.view(), z_u, e, s);
+    }
+  } else {
+    Hierarchy &Hu = c.hier[FC_H_TPU_U], &Hp = c.hier[FC_H_TPU_P];
+    if (nf) amg_vcycle<TP>(Hp, w_p, P.tp.p, s);                               // t_p = T^-T w_p
+    if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.HinvT.p, w_t, P.tt.p); FS_LAUNCHED(); }
+    sell_axpby<3, 3>(P.tC2.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);
+    sell_axpby<3, 1>(P.tQ2.view(), P.tp.p, P.tu.p, -1.0, 1.0, P.tu.p, s);  // t_u
+    amg_vcycle_t<TP>(Hu, P.tu.p, z_u, s);                                     // v_u = AMG^T(S~, t_u)
+    if (nf) {
+      sell_axpby<1, 3>(P.tQ1.view(), z_u, P.sp.p, 1.0, 0.0, (const TP *)nullptr, s);
+      amg_vcycle<TP>(Hp, P.sp.p, P.vp.p, s);
+      axpbyz(z_p, P.tp.p, P.vp.p, 1.0, -1.0, nf, s);                          // v_p = t_p - T^-T Q1^T v_u
+      EpiHinvUpdate<TP> e{z_t, P.tt.p, P.HinvT.p};                           // v_t = H~^-T (C1^T v_u - w_t)
+      sell_spmv<3, 3>(P.tC1.view(), z_u, e, s);
+    }
+  }
+}
+
 template <typename TP>
 PrecData<TP> &prec(fc_ctx &c);
 template <>
@@ -367,7 +430,7 @@ struct FgmresOut {
 };
 
 // one FGMRES cycle (no restart) on rhs r0 (device, double); dx written to x
-template <typename TP>
+template <typename TP, bool ADJ = false>
 FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rtol, int maxit) {
   cudaStream_t s = c.s;
   const int64_t n = c.n;
@@ -390,14 +453,18 @@ FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rt
     double *w = c.V.p + (int64_t)(j + 1) * n;
     TP *zj = Z + (int64_t)j * n;
     c.prof.start(PK_PREC, s);
+    const TP *win;
     if constexpr (std::is_same<TP, double>::value) {
-      apply_prec<TP>(c, P, variant, vj, zj);
+      win = vj;
     } else {
       cast(P.w.p, vj, n, s);
-      apply_prec<TP>(c, P, variant, P.w.p, zj);
+      win = P.w.p;
     }
+    if constexpr (ADJ) apply_prec_t<TP>(c, P, variant, win, zj);
+    else apply_prec<TP>(c, P, variant, win, zj);
     c.prof.stop(PK_PREC, s, 0.0);
-    jac_spmv<TP>(c, zj, w);
+    if constexpr (ADJ) jac_spmv_t<TP>(c, zj, w);
+    else jac_spmv<TP>(c, zj, w);
     nrm2sq_dev(w, n, c.w02.p, s, c.red.p);
     cgs_pass(c, j + 1, w, 0);
     cgs_pass(c, j + 1, w, 1);
@@ -425,7 +492,7 @@ FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rt
   return out;
 }
 
-template <typename TP>
+template <typename TP, bool ADJ = false>
 int solve_impl(fc_ctx &c, int variant, const double *b, double *x, double tol, int maxit, int *iters,
                double *relres) {
   cudaStream_t s = c.s;
@@ -448,11 +515,12 @@ int solve_impl(fc_ctx &c, int variant, const double *b, double *x, double tol, i
     if (maxit - total <= 0) break;
     const double rn = cycle == 0 ? bn : std::sqrt(dot(rhs, rhs, n, s, c.red.p));
     const double rtol = tol * bn / rn;
-    FgmresOut o = fgmres<TP>(c, variant, rhs, c.xk.p, rtol, maxit - total);
+    FgmresOut o = fgmres<TP, ADJ>(c, variant, rhs, c.xk.p, rtol, maxit - total);
     total += o.iters;
     axpby(x, c.xk.p, 1.0, 1.0, n, s);
     // true residual in double
-    jac_spmv<double>(c, x, c.rk.p);
+    if constexpr (ADJ) jac_spmv_t<double>(c, x, c.rk.p);
+    else jac_spmv<double>(c, x, c.rk.p);
     axpbyz(c.rk.p, b, c.rk.p, 1.0, -1.0, n, s);
     rr = std::sqrt(dot(c.rk.p, c.rk.p, n, s, c.red.p)) / bn;
     status = o.status;
@@ -467,6 +535,53 @@ int solve_impl(fc_ctx &c, int variant, const double *b, double *x, double tol, i
   if (iters) *iters = total;
   if (relres) *relres = rr;
   return status;
+}
+
+template <typename TP>
+__global__ void k_transpose3(int64_t nf, const double *in, TP *out) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+       f += (int64_t)gridDim.x * blockDim.x)
+    for (int r = 0; r < 3; r++)
+      for (int q = 0; q < 3; q++) out[f * 9 + q * 3 + r] = (TP)in[f * 9 + r * 3 + q];
+}
+
+template <typename TP>
+void prepare_prec_t(fc_ctx &c, PrecData<TP> &P, const Bsr<double> &C1t, const Bsr<double> &C2t,
+                    const Bsr<double> &Q1t, const Bsr<double> &Q2t) {
+  cudaStream_t s = c.s;
+  P.tC1 = to_sell<TP>(C1t.view(), s);
+  P.tC2 = to_sell<TP>(C2t.view(), s);
+  P.tQ1 = to_sell<TP>(Q1t.view(), s);
+  P.tQ2 = to_sell<TP>(Q2t.view(), s);
+  P.HinvT.alloc((size_t)c.nf * 9 > 0 ? (size_t)c.nf * 9 : 1);
+  if (c.nf) {
+    k_transpose3<TP><<<vgrid(c.nf), 256, 0, s>>>(c.nf, c.Hinv64.p, P.HinvT.p);
+    FS_LAUNCHED();
+  }
+  P.ready_t = true;
+}
+
+// transposed blocks, transposed preconditioner data and transposed AMG
+// cycles, built on the first adjoint call
+void ensure_adjoint(fc_ctx &c) {
+  if (c.have_adj) return;
+  cudaStream_t s = c.s;
+  Bsr<double> At = transpose(c.A.view(), s), C1t = transpose(c.C1.view(), s), Q1t = transpose(c.Q1.view(), s),
+              C2t = transpose(c.C2.view(), s), Ht = transpose(c.H.view(), s), Q2t = transpose(c.Q2.view(), s),
+              Tt = transpose(c.T.view(), s);
+  c.tA = to_sell<double>(At.view(), s);
+  c.tC1 = to_sell<double>(C1t.view(), s);
+  c.tQ1 = to_sell<double>(Q1t.view(), s);
+  c.tC2 = to_sell<double>(C2t.view(), s);
+  c.tH = to_sell<double>(Ht.view(), s);
+  c.tQ2 = to_sell<double>(Q2t.view(), s);
+  c.tT = to_sell<double>(Tt.view(), s);
+  if (c.opt.precision == FC_MIXED) prepare_prec_t<float>(c, c.pf, C1t, C2t, Q1t, Q2t);
+  else prepare_prec_t<double>(c, c.pd, C1t, C2t, Q1t, Q2t);
+  for (int h : {FC_H_TPU_U, FC_H_TUP_U})
+    if (c.hier[h].built) amg_prepare_transpose(c.hier[h], c.opt.precision, s);
+  FS_CUDA(cudaStreamSynchronize(s));
+  c.have_adj = true;
 }
 
 }  // namespace
@@ -652,6 +767,7 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     c->sH = to_sell<double>(c->H.view(), s); c->sQ2 = to_sell<double>(c->Q2.view(), s);
     c->sT = to_sell<double>(c->T.view(), s);
     pt.mark("upload + sell");
+    c->have_adj = false;
     for (auto &h : c->hier) h = Hierarchy();
     c->pf = PrecData<float>();
     c->pd = PrecData<double>();
@@ -756,6 +872,70 @@ int fc_solve_host(fc_ctx *c, int variant, const double *hb, double *hx, double t
     return FC_OK;
   });
   return rc != FC_OK ? rc : rc2;
+}
+
+int fc_spmv_adjoint(fc_ctx *c, const double *x, double *y) {
+  if (!c || !x || !y) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_setup has not completed");
+    ensure_adjoint(*c);
+    jac_spmv_t<double>(*c, x, y);
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
+}
+
+int fc_apply_prec_adjoint(fc_ctx *c, int variant, const double *w, double *v) {
+  if (!c || !w || !v || (variant != FC_TPU && variant != FC_TUP)) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready && c->have[variant], FC_NOT_SETUP, "variant not built by fc_setup");
+    ensure_adjoint(*c);
+    if (c->opt.precision == FC_MIXED) {
+      cast(c->pf.w.p, w, c->n, c->s);
+      apply_prec_t<float>(*c, c->pf, variant, c->pf.w.p, c->pf.out.p);
+      cast(v, c->pf.out.p, c->n, c->s);
+    } else {
+      apply_prec_t<double>(*c, c->pd, variant, w, v);
+    }
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
+}
+
+int fc_solve_adjoint(fc_ctx *c, int variant, const double *g, double *lambda, double tol, int maxit, int *iters,
+                     double *relres) {
+  if (!c || !g || !lambda || (variant != FC_TPU && variant != FC_TUP) || maxit < 1 || maxit > 4000 ||
+      !(tol > 0))
+    return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready && c->have[variant], FC_NOT_SETUP, "variant not built by fc_setup");
+    ensure_adjoint(*c);
+    int rc = c->opt.precision == FC_MIXED
+                 ? solve_impl<float, true>(*c, variant, g, lambda, tol, maxit, iters, relres)
+                 : solve_impl<double, true>(*c, variant, g, lambda, tol, maxit, iters, relres);
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return rc;
+  });
+}
+
+int fc_vcycle_adjoint(fc_ctx *c, int hier, const double *f, double *x) {
+  if (!c || !f || !x || hier < 0 || hier > 3) return FC_BAD_ARG;
+  return run(c, [&]() {
+    Hierarchy &H = c->hier[hier];
+    FS_REQUIRE(H.built, FC_NOT_SETUP, "hierarchy not built");
+    amg_prepare_transpose(H, c->opt.precision, c->s);
+    const int64_t n = (int64_t)H.lev[0].nb * H.B;
+    if (c->opt.precision == FC_MIXED) {
+      DBuf<float> f32(n), x32(n);
+      cast(f32.p, f, n, c->s);
+      amg_vcycle_t<float>(H, f32.p, x32.p, c->s);
+      cast(x, x32.p, n, c->s);
+    } else {
+      amg_vcycle_t<double>(H, f, x, c->s);
+    }
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
 }
 
 int fc_num_levels(fc_ctx *c, int hier, int *levels) {

@@ -1,0 +1,148 @@
+"""GPU parity of the adjoint path (transposed products, transposed V-cycles,
+M^-T, FGMRES on J^T) against the oracle, the dense adjoint on the 8^3 case,
+and the gradient of 0.5 ||p - p_obs||^2 w.r.t. b through
+torch.autograd (central differences)."""
+import numpy as np
+import pytest
+
+import fracgen
+from oracle import adjoint, schur
+from oracle import sparse as osp
+from oracle.amg import AMG, AmgOptions
+from oracle.precond import BlockPreconditioner
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "tiny8": ("tiny8", {}, 64, 16),
+    "planes8": ("planes64", dict(N=8), 32, 16),
+    "rects16": ("rects128", dict(N=16), 50, 30),
+}
+
+
+@pytest.fixture(scope="module")
+def fs():
+    import paper_2112_12397_gb300 as m
+    m.load(build_if_missing=True)
+    return m
+
+
+_cache = {}
+
+
+def case(name, fs):
+    if name not in _cache:
+        preset, over, cm, cmp = CASES[name]
+        P = fracgen.generate(preset, **over)
+        ctx = fs.context_for(P, fs.default_options(coarse_max=cm, coarse_max_p=cmp))
+        _cache[name] = (P, ctx, AmgOptions(coarse_max=cm), AmgOptions(coarse_max=cmp))
+    return _cache[name]
+
+
+def cuda(v):
+    return torch.from_numpy(np.ascontiguousarray(v)).cuda()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_transposed_products(fs, name):
+    P, ctx, opt, optp = case(name, fs)
+    JT = osp.jacobian(P).T.tocsr()
+    x = np.random.default_rng(0).standard_normal(P.n)
+    y = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    ctx.spmv_adjoint(cuda(x), y)
+    assert rel(y.cpu().numpy(), JT @ x) <= 1e-14
+    S1 = schur.s1(P)
+    for hier, M in ((fs.FC_H_TUP_U, S1), (fs.FC_H_TPU_U, schur.s_tilde(P, S1=S1))):
+        ref = AMG(M, 3, opt)
+        f = np.random.default_rng(hier).standard_normal(M.shape[0])
+        xo = torch.zeros(M.shape[0], dtype=torch.float64, device="cuda")
+        ctx.vcycle_adjoint(hier, cuda(f), xo)
+        assert rel(xo.cpu().numpy(), ref.vcycle_t(f)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("variant", ["tpu", "tup"])
+def test_adjoint_preconditioner_and_solve(fs, name, variant):
+    P, ctx, opt, optp = case(name, fs)
+    M = BlockPreconditioner(P, variant, opt=opt, opt_p=optp)
+    Mt = adjoint.AdjointPreconditioner(M)
+    w = np.random.default_rng(9).standard_normal(P.n)
+    v = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    ctx.apply_prec_adjoint(variant, cuda(w), v)
+    assert rel(v.cpu().numpy(), Mt(w)) <= 1e-10
+    g = np.zeros(P.n)
+    g[-P.n_face:] = np.random.default_rng(4).standard_normal(P.n_face)
+    lam = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+    rc, it, rr = ctx.solve_adjoint(variant, cuda(g), lam, 1e-8, 400)
+    ref = adjoint.solve_adjoint(P, M, g, 1e-8, 400)
+    assert abs(it - ref.iters) <= 1
+    assert rel(lam.cpu().numpy(), ref.x) <= 1e-8
+    JT = osp.jacobian(P).T.tocsr()
+    assert np.linalg.norm(g - JT @ lam.cpu().numpy()) / np.linalg.norm(g) <= 1e-8
+
+
+def test_adjoint_matches_dense_on_8cubed(fs):
+    P, ctx, _, _ = case("tiny8", fs)
+    g = np.zeros(P.n)
+    g[-P.n_face:] = np.random.default_rng(1).standard_normal(P.n_face)
+    lam_d = adjoint.dense_adjoint(P, g)
+    for variant in ("tpu", "tup"):
+        lam = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+        ctx.solve_adjoint(variant, cuda(g), lam, 1e-12, 400, allow_fail=True)
+        assert rel(lam.cpu().numpy(), lam_d) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autograd_gradient_wrt_rhs(fs, precision):
+    from paper_2112_12397_gb300.autograd import frac_solve
+    P = fracgen.generate("planes64", N=8, seed=3)
+    ctx = fs.context_for(P, fs.default_options(precision=precision, coarse_max=32, coarse_max_p=16))
+    b = cuda(P.b).requires_grad_(True)
+    p_obs = cuda(np.random.default_rng(5).standard_normal(P.n_face))
+
+    def loss_of(bb, grad=False):
+        x = frac_solve(bb, ctx, "tup", 1e-8, 600)
+        return 0.5 * ((x[-P.n_face:] - p_obs) ** 2).sum()
+
+    L = loss_of(b)
+    L.backward()
+    grad = b.grad.detach().cpu().numpy()
+    rs = np.random.default_rng(6)
+    with torch.no_grad():
+        for _ in range(5):
+            d = rs.standard_normal(P.n)
+            d[:3 * P.n_node][P.dirichlet] = 0.0
+            # the loss is quadratic in b, so central differences carry no
+            # truncation error; a unit step keeps the solves' 1e-8 residual
+            # error far below the 1e-5 tolerance
+            h = 1.0
+            lp = float(loss_of(b + h * cuda(d)))
+            lm = float(loss_of(b - h * cuda(d)))
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - grad @ d) <= 1e-5 * abs(grad @ d)
+    ctx.close()
+
+
+def test_full_size_adjoint_planes64(fs):
+    """64^3 three-plane workload in FP64: forward solve, then the adjoint of
+    0.5 ||p - p_obs||^2; the adjoint residual checked by the oracle's J^T."""
+    P = fracgen.generate("planes64")
+    ctx = fs.context_for(P, fs.default_options(variants=2))
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    ctx.solve("tup", b, x, 1e-8, 600)
+    p = x[-P.n_face:].cpu().numpy()
+    p_obs = p * (1 + 0.1 * np.random.default_rng(12).standard_normal(P.n_face))
+    g = np.zeros(P.n)
+    g[-P.n_face:] = p - p_obs
+    lam = torch.zeros_like(b)
+    rc, it, rr = ctx.solve_adjoint("tup", cuda(g), lam, 1e-8, 600)
+    JT = osp.jacobian(P).T.tocsr()
+    true = np.linalg.norm(g - JT @ lam.cpu().numpy()) / np.linalg.norm(g)
+    assert true <= 1e-8 and abs(true - rr) <= 1e-3 * true
+    ctx.close()
