@@ -61,7 +61,10 @@ class _Prob(C.Structure):
                 ("aperture", C.POINTER(C.c_double)), ("pl", C.POINTER(C.c_double)),
                 ("E_cell", C.POINTER(C.c_double)), ("Ebar_face", C.POINTER(C.c_double)),
                 ("ups_face", C.POINTER(C.c_double)), ("rects", C.POINTER(C.c_int32)),
-                ("rects_q1", C.POINTER(C.c_int32))]
+                ("rects_q1", C.POINTER(C.c_int32)),
+                ("n_dk", C.c_int64), ("dk_face", C.POINTER(C.c_int32)), ("dk_row", C.POINTER(C.c_int32)),
+                ("dk_col", C.POINTER(C.c_int32)), ("dk_block", C.POINTER(C.c_int8)),
+                ("dk_comp", C.POINTER(C.c_int8)), ("dk_val", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -176,6 +179,7 @@ class Problem:
     Ebar_face: np.ndarray
     ups_face: np.ndarray
     rects: np.ndarray
+    dk: dict = field(default_factory=dict)      # derivative entries d K / d a_face
     extra: dict = field(default_factory=dict)
 
     @property
@@ -258,6 +262,9 @@ def generate(cfg: Config | str, aperture: np.ndarray | None = None, **over) -> P
             Ebar_face=_arr(p.Ebar_face, nf, np.float64),
             ups_face=_arr(p.ups_face, nf, np.float64),
             rects=rects,
+            dk=dict(face=_arr(p.dk_face, int(p.n_dk), np.int32), block=_arr(p.dk_block, int(p.n_dk), np.int8),
+                    row=_arr(p.dk_row, int(p.n_dk), np.int32), col=_arr(p.dk_col, int(p.n_dk), np.int32),
+                    comp=_arr(p.dk_comp, int(p.n_dk), np.int8), val=_arr(p.dk_val, int(p.n_dk), np.float64)),
         )
     finally:
         lib.fg_free(C.byref(p))

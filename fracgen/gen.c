@@ -108,6 +108,15 @@ typedef struct {
   int32_t *rects;        /* 5 per fracture: axis, m, p0, q0, p1, (q1 in
                             rects_q1) */
   int32_t *rects_q1;
+  /* derivatives of the Jacobian with respect to the apertures: entry e says
+   * d K[row, col] / d a_face = val, where for block 0 (T) row and col are
+   * faces (comp = 0) and for block 1 (Q2) row is a face and (col, comp) a
+   * displacement dof (copy, component).  Sorted by (face, block, row, col,
+   * comp), duplicates summed. */
+  int64_t n_dk;
+  int32_t *dk_face, *dk_row, *dk_col;
+  int8_t *dk_block, *dk_comp;
+  double *dk_val;
 } fg_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -202,6 +211,50 @@ static void coo_to_bsr(coo_t *q, int32_t nr, int32_t nc, int br, int bc,
 static void bsr_free(fg_bsr *m) {
   free(m->row_ptr); free(m->col_idx); free(m->val);
   m->row_ptr = NULL; m->col_idx = NULL; m->val = NULL;
+}
+
+/* ------------------------------------------------------------------------ */
+/* derivative entries d K / d a_face                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t n, cap;
+  int32_t *face, *row, *col;
+  int8_t *block, *comp;
+  double *val;
+} dk_t;
+
+static void dk_init(dk_t *d) {
+  d->n = 0; d->cap = 1024;
+  d->face = (int32_t *)malloc(sizeof(int32_t) * d->cap);
+  d->row = (int32_t *)malloc(sizeof(int32_t) * d->cap);
+  d->col = (int32_t *)malloc(sizeof(int32_t) * d->cap);
+  d->block = (int8_t *)malloc(d->cap);
+  d->comp = (int8_t *)malloc(d->cap);
+  d->val = (double *)malloc(sizeof(double) * d->cap);
+}
+static void dk_push(dk_t *d, int32_t f, int block, int32_t row, int32_t col, int comp, double v) {
+  if (v == 0.0) return;
+  if (d->n == d->cap) {
+    d->cap *= 2;
+    d->face = (int32_t *)realloc(d->face, sizeof(int32_t) * d->cap);
+    d->row = (int32_t *)realloc(d->row, sizeof(int32_t) * d->cap);
+    d->col = (int32_t *)realloc(d->col, sizeof(int32_t) * d->cap);
+    d->block = (int8_t *)realloc(d->block, d->cap);
+    d->comp = (int8_t *)realloc(d->comp, d->cap);
+    d->val = (double *)realloc(d->val, sizeof(double) * d->cap);
+  }
+  d->face[d->n] = f; d->block[d->n] = (int8_t)block; d->row[d->n] = row;
+  d->col[d->n] = col; d->comp[d->n] = (int8_t)comp; d->val[d->n] = v;
+  d->n++;
+}
+static const dk_t *g_dk_sort;
+static int cmp_dk(const void *a, const void *b) {
+  int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+  const dk_t *d = g_dk_sort;
+#define CMPF(x) if (d->x[i] != d->x[j]) return d->x[i] < d->x[j] ? -1 : 1;
+  CMPF(face) CMPF(block) CMPF(row) CMPF(col) CMPF(comp)
+#undef CMPF
+  return (i > j) - (i < j);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -657,6 +710,8 @@ int fg_generate(const fg_config *cfg, fg_problem *P) {
   qsort(er, (size_t)nrec, sizeof(edge_rec), cmp_edge);
 
   /* ---------------- H (3x3 per face pair), T (1x1), Q2 (1x3) */
+  dk_t dk;
+  dk_init(&dk);
   {
     coo_t hq, tq, q2;
     coo_init(&hq, 9); coo_init(&tq, 1); coo_init(&q2, 3);
@@ -690,6 +745,19 @@ int fg_generate(const fg_config *cfg, fg_problem *P) {
           }                                                                   \
         }                                                                     \
       } while (0)
+    /* derivative helper: d/d a_fc of coef * dg_M/du added to Q2 row `row` */
+    #define ADD_DG(fc, row, M, coef)                                          \
+      do {                                                                    \
+        if (P->state[M] == 2) {                                               \
+          int aM_ = P->face_geom[4 * (M)];                                    \
+          for (int kk_ = 0; kk_ < 4; kk_++) {                                 \
+            int32_t cm_ = P->face_copies[8 * (M) + kk_], cp_ = P->face_copies[8 * (M) + 4 + kk_]; \
+            if (cm_ == cp_) continue;                                         \
+            dk_push(&dk, fc, 1, row, cp_, aM_, 0.25 * (coef));                \
+            dk_push(&dk, fc, 1, row, cm_, aM_, -0.25 * (coef));               \
+          }                                                                   \
+        }                                                                     \
+      } while (0)
     int64_t s = 0;
     while (s < nrec) {
       int64_t t = s;
@@ -711,6 +779,28 @@ int fg_generate(const fg_config *cfg, fg_problem *P) {
           double dp = P->pl[K] - P->pl[L];
           ADD_DUPS(K, K, dp * dK); ADD_DUPS(K, L, dp * dL);
           ADD_DUPS(L, K, -dp * dK); ADD_DUPS(L, L, -dp * dL);
+          {
+            /* d/da of the transmissibility entries and of the flux
+             * derivative rows; Ups_M = 2 (C_f0 + a_M^3 / 12) / mu, so
+             * dUps_M/da_M = cM = (2 / mu)(a_M^2 / 4) and dcM/da_M = a_M / mu */
+            const double aK = P->aperture[K], aL = P->aperture[L];
+            const double cK = (2.0 / mu) * (aK * aK / 4.0), cL = (2.0 / mu) * (aL * aL / 4.0);
+            const double S = uK + uL, S3 = S * S * S;
+            const double tK = dK * cK, tL = dL * cL;
+            dk_push(&dk, K, 0, K, K, 0, tK); dk_push(&dk, K, 0, L, L, 0, tK);
+            dk_push(&dk, K, 0, K, L, 0, -tK); dk_push(&dk, K, 0, L, K, 0, -tK);
+            dk_push(&dk, L, 0, K, K, 0, tL); dk_push(&dk, L, 0, L, L, 0, tL);
+            dk_push(&dk, L, 0, K, L, 0, -tL); dk_push(&dk, L, 0, L, K, 0, -tL);
+            /* V = dK cK G_K + dL cL G_L; rows K (x dp) and L (x -dp) */
+            const double vKK = cK * cK * (-2.0 * uL * uL / S3) + dK * aK / mu;   /* dV/daK on G_K */
+            const double vKL = cK * cL * (2.0 * uK * uL / S3);                   /* dV/daK on G_L */
+            const double vLK = cK * cL * (2.0 * uK * uL / S3);                   /* dV/daL on G_K */
+            const double vLL = cL * cL * (-2.0 * uK * uK / S3) + dL * aL / mu;   /* dV/daL on G_L */
+            ADD_DG(K, K, K, dp * vKK); ADD_DG(K, K, L, dp * vKL);
+            ADD_DG(K, L, K, -dp * vKK); ADD_DG(K, L, L, -dp * vKL);
+            ADD_DG(L, K, K, dp * vLK); ADD_DG(L, K, L, dp * vLL);
+            ADD_DG(L, L, K, -dp * vLK); ADD_DG(L, L, L, -dp * vLL);
+          }
           int coplanar = P->face_geom[4 * K] == P->face_geom[4 * L] &&
                          P->face_geom[4 * K + 1] == P->face_geom[4 * L + 1];
           if (coplanar) {
@@ -766,6 +856,11 @@ int fg_generate(const fg_config *cfg, fg_problem *P) {
           if (cnt != 1) continue;
           double *v = coo_push(&tq, K, K); v[0] += P->ups_face[K];
           ADD_DUPS(K, K, P->pl[K]);
+          {
+            const double aK = P->aperture[K];
+            dk_push(&dk, K, 0, K, K, 0, (2.0 / mu) * (aK * aK / 4.0));
+            ADD_DG(K, K, K, P->pl[K] * aK / mu);
+          }
         }
       }
     }
@@ -781,6 +876,7 @@ int fg_generate(const fg_config *cfg, fg_problem *P) {
       }
     }
     #undef ADD_DUPS
+    #undef ADD_DG
     for (int64_t e = 0; e < q2.n; e++)
       for (int c = 0; c < 3; c++)
         if (dir[3 * q2.c[e] + c]) q2.v[3 * e + c] = 0.0;
@@ -788,6 +884,37 @@ int fg_generate(const fg_config *cfg, fg_problem *P) {
     coo_to_bsr(&tq, nf, nf, 1, 1, 0, &P->T);
     coo_to_bsr(&q2, nf, nn, 1, 3, 1, &P->Q2);
     coo_free(&hq); coo_free(&tq); coo_free(&q2);
+  }
+
+  /* ---------------- derivative entries: drop constrained Q2 columns, sort,
+   * merge duplicates */
+  {
+    int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (dk.n > 0 ? dk.n : 1));
+    for (int64_t e = 0; e < dk.n; e++) perm[e] = e;
+    g_dk_sort = &dk;
+    qsort(perm, (size_t)dk.n, sizeof(int64_t), cmp_dk);
+    int64_t m = 0;
+    P->dk_face = (int32_t *)malloc(sizeof(int32_t) * (dk.n > 0 ? dk.n : 1));
+    P->dk_row = (int32_t *)malloc(sizeof(int32_t) * (dk.n > 0 ? dk.n : 1));
+    P->dk_col = (int32_t *)malloc(sizeof(int32_t) * (dk.n > 0 ? dk.n : 1));
+    P->dk_block = (int8_t *)malloc(dk.n > 0 ? dk.n : 1);
+    P->dk_comp = (int8_t *)malloc(dk.n > 0 ? dk.n : 1);
+    P->dk_val = (double *)malloc(sizeof(double) * (dk.n > 0 ? dk.n : 1));
+    for (int64_t t = 0; t < dk.n; t++) {
+      int64_t e = perm[t];
+      if (dk.block[e] == 1 && dir[3 * dk.col[e] + dk.comp[e]]) continue;
+      if (m > 0 && P->dk_face[m - 1] == dk.face[e] && P->dk_block[m - 1] == dk.block[e] &&
+          P->dk_row[m - 1] == dk.row[e] && P->dk_col[m - 1] == dk.col[e] && P->dk_comp[m - 1] == dk.comp[e]) {
+        P->dk_val[m - 1] += dk.val[e];
+        continue;
+      }
+      P->dk_face[m] = dk.face[e]; P->dk_block[m] = dk.block[e]; P->dk_row[m] = dk.row[e];
+      P->dk_col[m] = dk.col[e]; P->dk_comp[m] = dk.comp[e]; P->dk_val[m] = dk.val[e];
+      m++;
+    }
+    P->n_dk = m;
+    free(perm);
+    free(dk.face); free(dk.row); free(dk.col); free(dk.block); free(dk.comp); free(dk.val);
   }
 
   /* ---------------- right-hand side */
@@ -810,6 +937,7 @@ void fg_free(fg_problem *P) {
   free(P->b); free(P->state); free(P->dirichlet); free(P->node_grid);
   free(P->face_geom); free(P->face_copies); free(P->aperture); free(P->pl);
   free(P->E_cell); free(P->Ebar_face); free(P->ups_face); free(P->rects); free(P->rects_q1);
+  free(P->dk_face); free(P->dk_row); free(P->dk_col); free(P->dk_block); free(P->dk_comp); free(P->dk_val);
   memset(P, 0, sizeof(*P));
 }
 

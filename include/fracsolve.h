@@ -190,6 +190,19 @@ int fc_apply_prec_adjoint(fc_ctx *ctx, int variant, const double *d_w, double *d
 int fc_solve_adjoint(fc_ctx *ctx, int variant, const double *d_g, double *d_lambda, double tol,
                      int maxit, int *iters, double *relres);
 
+/* Aperture gradient of an objective L(x) given the forward solution d_x and
+ * the adjoint d_lambda (J^T lambda = dL/dx):
+ *   d_grad[f] = -lambda^T (dJ/da_f) x,   f = 0 .. n_face-1,
+ * through the transmissibility T and the coupling Q2 (their entries carry
+ * the apertures: cubic-law conductivity, TPFA averages, flux derivatives).
+ * dJ/da arrives as entries sorted by face, DEVICE arrays: face_ptr (n_face+1,
+ * int64) delimits the entries of each face; entry e is d J[row, col]/d a_f =
+ * val with block[e] = 0 for T (row, col faces; comp unused) or 1 for Q2 (row a
+ * face, (col, comp) = (node copy, component)).  Deterministic. */
+int fc_aperture_gradient(fc_ctx *ctx, const int64_t *d_face_ptr, const int8_t *d_block,
+                         const int32_t *d_row, const int32_t *d_col, const int8_t *d_comp,
+                         const double *d_val, const double *d_x, const double *d_lambda, double *d_grad);
+
 /* ---------------- inspection (used by the parity tests) ---------------- */
 
 /* Hierarchies: FC_H_TPU_U = AMG of S~, FC_H_TPU_P = AMG of T,

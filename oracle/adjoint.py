@@ -88,3 +88,18 @@ def operator_matrix(apply, n):
     """Dense matrix of a linear operator, column by column (tiny cases)."""
     cols = [apply(e) for e in np.eye(n)]
     return np.array(cols).T
+
+
+def aperture_gradient(P, x: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """dL/da_f = -lambda^T (dJ/da_f) x from the derivative entries of the
+    transmissibility T and the coupling Q2 (rows are pressure equations)."""
+    d = P.dk
+    nu, nt = 3 * P.n_node, 3 * P.n_face
+    lam_p = lam[nu + nt:]
+    x_u, x_p = x[:nu], x[nu + nt:]
+    t = d["block"] == 0
+    xv = np.empty(len(d["val"]))
+    xv[t] = x_p[d["col"][t]]
+    xv[~t] = x_u[3 * d["col"][~t] + d["comp"][~t]]
+    contrib = lam_p[d["row"]] * d["val"] * xv
+    return -np.bincount(d["face"], weights=contrib, minlength=P.n_face)

@@ -26,7 +26,7 @@ VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP}
 # exported symbols declared by include/fracsolve.h
 SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_residual", "fc_residual_noalloc",
            "fc_apply_prec", "fc_solve", "fc_spmv_adjoint", "fc_apply_prec_adjoint", "fc_solve_adjoint",
-           "fc_vcycle_adjoint",
+           "fc_vcycle_adjoint", "fc_aperture_gradient",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
            "fc_get_fixed_stress", "fc_profile", "fc_kernel_stats", "fc_launch_count", "fc_destroy",
            "fc_strerror", "fc_last_error"]
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = False):
         "fc_apply_prec_adjoint": (C.c_int, [vp, C.c_int, vp, vp]),
         "fc_solve_adjoint": (C.c_int, [vp, C.c_int, vp, vp, d, C.c_int, pint, pd]),
         "fc_vcycle_adjoint": (C.c_int, [vp, C.c_int, vp, vp]),
+        "fc_aperture_gradient": (C.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "fc_num_levels": (C.c_int, [vp, C.c_int, pint]),
         "fc_get_bsr": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, pi32, pi32, pi32, pi32, pi64, vp, vp, vp]),
         "fc_get_aggregates": (C.c_int, [vp, C.c_int, C.c_int, vp, pd]),
@@ -226,6 +227,13 @@ class Context:
     def vcycle_adjoint(self, hier: int, f, x):
         self._check(self.lib.fc_vcycle_adjoint(self.h, hier, _ptr(f), _ptr(x)), self.h)
 
+    def aperture_gradient(self, dk: dict, x, lam, grad):
+        """dk: device tensors face_ptr (int64), block (int8), row, col (int32),
+        comp (int8), val (float64); see fc_aperture_gradient."""
+        self._check(self.lib.fc_aperture_gradient(
+            self.h, _ptr(dk["face_ptr"]), _ptr(dk["block"]), _ptr(dk["row"]), _ptr(dk["col"]), _ptr(dk["comp"]),
+            _ptr(dk["val"]), _ptr(x), _ptr(lam), _ptr(grad)), self.h)
+
     # ------------------------------------------------------------ inspection
     def num_levels(self, hier: int) -> int:
         n = C.c_int(0)
@@ -283,6 +291,19 @@ def device_blocks(problem, device="cuda"):
                      torch.from_numpy(np.ascontiguousarray(B.val).reshape(-1)).to(device),
                      B.n_brows, B.n_bcols, B.br, B.bc)
     return out
+
+
+def device_dk(problem, device="cuda"):
+    """Marshal a problem's aperture-derivative entries (sorted by face) and
+    the per-face offsets into CUDA tensors."""
+    import torch
+    d = problem.dk
+    fptr = np.zeros(problem.n_face + 1, dtype=np.int64)
+    np.add.at(fptr, d["face"] + 1, 1)
+    fptr = np.cumsum(fptr)
+    return {"face_ptr": torch.from_numpy(fptr).to(device),
+            **{k: torch.from_numpy(np.ascontiguousarray(d[k])).to(device)
+               for k in ("block", "row", "col", "comp", "val")}}
 
 
 def context_for(problem, options: fc_options | None = None, stream=None) -> Context:

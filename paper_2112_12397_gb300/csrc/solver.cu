@@ -938,6 +938,43 @@ int fc_vcycle_adjoint(fc_ctx *c, int hier, const double *f, double *x) {
   });
 }
 
+namespace {
+// grad[f] = - sum over the derivative entries e of face f of
+//   lambda_p[row_e] * val_e * x[col_e]   (x_p for T entries, x_u for Q2 entries)
+// one warp per face, lane-strided sums reduced in a fixed tree
+__global__ void k_aperture_gradient(int nf, const int64_t *fptr, const int8_t *block, const int *row,
+                                    const int *col, const int8_t *comp, const double *val, const double *x_u,
+                                    const double *x_p, const double *lam_p, double *grad) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t f = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; f < nf;
+       f += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (int64_t e = fptr[f] + lane; e < fptr[f + 1]; e += 32) {
+      const double xv = block[e] == 0 ? x_p[col[e]] : x_u[3 * (int64_t)col[e] + comp[e]];
+      s += lam_p[row[e]] * val[e] * xv;
+    }
+    s = warp_sum(s);
+    if (lane == 0) grad[f] = -s;
+  }
+}
+}  // namespace
+
+int fc_aperture_gradient(fc_ctx *c, const int64_t *face_ptr, const int8_t *block, const int32_t *row,
+                         const int32_t *col, const int8_t *comp, const double *val, const double *x,
+                         const double *lambda, double *grad) {
+  if (!c || !face_ptr || !x || !lambda || !grad) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_setup has not completed");
+    if (c->nf == 0) return FC_OK;
+    const double *x_u = x, *x_p = x + c->nu + c->nt, *lam_p = lambda + c->nu + c->nt;
+    k_aperture_gradient<<<blocks_for((int64_t)c->nf * 32, 256, kSMs * 16), 256, 0, c->s>>>(
+        c->nf, face_ptr, block, row, col, comp, val, x_u, x_p, lam_p, grad);
+    FS_LAUNCHED();
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
+}
+
 int fc_num_levels(fc_ctx *c, int hier, int *levels) {
   if (!c || !levels || hier < 0 || hier > 3) return FC_BAD_ARG;
   *levels = c->hier[hier].built ? c->hier[hier].levels() : 0;
