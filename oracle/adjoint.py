@@ -19,6 +19,12 @@ app_tup^T (from Eq. P2):
   v_u = s_u - AMG^T(S1, Q2^T v_p)
   v_t = H~^-T (C1^T v_u - w_t)
 
+app_tup_star^T = (D2^-1 L2^-1)^T = L2^-T D2^-T (from Eq. LDU2):
+  z_t = -H~^-T w_t,  z_u = AMG^T(S1, w_u),  z_p = S~2^-T w_p
+  v_p = z_p
+  v_u = z_u - AMG^T(S1, Q2^T z_p)
+  v_t = z_t + H~^-T (C1^T v_u)
+
 AMG^T is the transposed V-cycle (oracle.amg.AMG.vcycle_t); T and S~2 are
 symmetric and their scalar V-cycles are symmetric operators.  The solve is
 the same flexible GMRES on J^T.
@@ -64,6 +70,13 @@ class AdjointPreconditioner:
             v_u = self.u_t(t_u)
             v_p = t_p - self.p_t(self.Q1T @ v_u)
             v_t = self.HinvT @ (self.C1T @ v_u - w_t)
+        elif M.variant == "tup_star":
+            z_t = -(self.HinvT @ w_t)
+            z_u = self.u_t(w_u)
+            z_p = self.p_t(w_p)
+            v_p = z_p
+            v_u = z_u - self.u_t(self.Q2T @ z_p)
+            v_t = z_t + self.HinvT @ (self.C1T @ v_u)
         else:
             t_u = w_u + self.C2T @ (self.HinvT @ w_t)
             s_u = self.u_t(t_u)

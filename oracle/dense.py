@@ -6,6 +6,8 @@
 * ``m1_matrix`` / ``m2_matrix``: the preconditioners written as the products
   of block factors in Eq. P1 and Eq. P2 (in the permuted orders of
   Eq. Q1 / Eq. Q2, mapped back to [u; t; p]).
+* ``m2_factors`` / ``m2_star_matrix``: the three factors of Eq. P2 and the
+  incomplete form D2^-1 L2^-1 (the last two factors only).
 """
 from __future__ import annotations
 
@@ -70,8 +72,9 @@ def m1_matrix(P, S_tilde: np.ndarray | None = None, T: np.ndarray | None = None)
     return Q.T @ M_tpu @ Q
 
 
-def m2_matrix(P, S1_inv: np.ndarray | None = None, S2_tilde: np.ndarray | None = None):
-    """Eq. P2 in the order (t, u, p), returned in the [u; t; p] order."""
+def m2_factors(P, S1_inv: np.ndarray | None = None, S2_tilde: np.ndarray | None = None):
+    """The factors (U2^-1, D2^-1, L2^-1) of Eq. P2 in the (t, u, p) order of
+    Eq. Q2, and the permutation matrix Q with Q [u; t; p] = [t; u; p]."""
     d = blocks_dense(P)
     Hi = hinv_dense(P)
     S1 = d["A"] + d["C1"] @ Hi @ d["C2"]
@@ -91,7 +94,18 @@ def m2_matrix(P, S1_inv: np.ndarray | None = None, S2_tilde: np.ndarray | None =
     L = np.block([[I_t, Z((nt, nu)), Z((nt, npp))],
                   [d["C1"] @ Hi, I_u, Z((nu, npp))],
                   [-d["Q2"] @ S1i @ d["C1"] @ Hi, -d["Q2"] @ S1i, I_p]])
-    M = U @ D @ L
     perm = np.concatenate([np.arange(nu, nu + nt), np.arange(nu), np.arange(nu + nt, nu + nt + npp)])
     Q = np.eye(nu + nt + npp)[perm]
-    return Q.T @ M @ Q
+    return U, D, L, Q
+
+
+def m2_matrix(P, S1_inv: np.ndarray | None = None, S2_tilde: np.ndarray | None = None):
+    """Eq. P2 in the order (t, u, p), returned in the [u; t; p] order."""
+    U, D, L, Q = m2_factors(P, S1_inv, S2_tilde)
+    return Q.T @ (U @ D @ L) @ Q
+
+
+def m2_star_matrix(P, S1_inv: np.ndarray | None = None, S2_tilde: np.ndarray | None = None):
+    """The incomplete factorisation D2^-1 L2^-1 of Eq. P2, in [u; t; p]."""
+    U, D, L, Q = m2_factors(P, S1_inv, S2_tilde)
+    return Q.T @ (D @ L) @ Q

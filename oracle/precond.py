@@ -1,4 +1,6 @@
-"""The two block preconditioners, applied exactly as Alg. 2 and Alg. 4.
+"""The two block preconditioners, applied exactly as Alg. 2 and Alg. 4, and
+the incomplete t-u-p form M2* = D2^-1 L2^-1 (Sec. 3.2, the remark after
+Prop. 3.2: the factor U2^-1 of Eq. P2 is dropped).
 
 Inner solves are pluggable:
 * ``u_solver``: "amg" (one AMG V-cycle on S~ or S1, the paper's AMG(K, y)) or
@@ -35,7 +37,9 @@ def _solver(M, B, kind, opt):
 
 
 class BlockPreconditioner:
-    """M1^-1 (variant "tpu", Alg. 1-2) or M2^-1 (variant "tup", Alg. 3-4)."""
+    """M1^-1 (variant "tpu", Alg. 1-2), M2^-1 (variant "tup", Alg. 3-4) or
+    the incomplete M2*^-1 = D2^-1 L2^-1 (variant "tup_star", built by Alg. 3
+    like M2)."""
 
     def __init__(self, P, variant: str, u_solver: str = "amg", p_solver: str = "amg",
                  opt: AmgOptions | None = None, blk: dict | None = None,
@@ -56,7 +60,7 @@ class BlockPreconditioner:
             self.Su = schur.s_tilde(P, b, self.S1)                    # Alg. 1 line 3
             self.u_inv = _solver(self.Su if u_matrix is None else u_matrix, 3, u_solver, opt)
             self.p_inv = _solver(b["T"] if p_matrix is None else p_matrix, 1, p_solver, opt_p)
-        elif variant == "tup":
+        elif variant in ("tup", "tup_star"):
             self.S1 = schur.s1(P, b)                                  # Alg. 3 line 2
             self.Su = self.S1
             self.S2 = schur.s2_tilde(P, self.S1, b)                   # Alg. 3 line 3
@@ -98,6 +102,27 @@ class BlockPreconditioner:
         v_t = -t_t + self.Hinv @ s_t                   # 10
         return np.concatenate([v_u, v_t, v_p])
 
+    def apply_tup_star(self, w):
+        """M2*^-1 w = D2^-1 (L2^-1 w) with the factors of Eq. LDU2, in the
+        (t, u, p) order of Eq. Q2:
+          L2^-1: y_t = w_t, y_u = w_u + C1 H~^-1 w_t, y_p = w_p - Q2 S~1^-1 y_u
+          D2^-1: v_t = -H~^-1 y_t, v_u = S~1^-1 y_u, v_p = S~2^-1 y_p
+        S~1^-1 y_u appears in both factors; it is one AMG call."""
+        b = self.b
+        w_u, w_t, w_p = self.split(w)
+        t_t = self.Hinv @ w_t                          # H~^-1 w_t
+        y_u = w_u + b["C1"] @ t_t                      # L2^-1, u block
+        s_u = self.u_inv(y_u)                          # S~1^-1 y_u = AMG(S1, y_u)
+        y_p = w_p - b["Q2"] @ s_u                      # L2^-1, p block
+        v_p = self.p_inv(y_p)                          # D2^-1, p block
+        v_u = s_u                                      # D2^-1, u block
+        v_t = -t_t                                     # D2^-1, t block
+        return np.concatenate([v_u, v_t, v_p])
+
     def __call__(self, w):
         w = np.asarray(w, dtype=np.float64)
-        return self.apply_tpu(w) if self.variant == "tpu" else self.apply_tup(w)
+        if self.variant == "tpu":
+            return self.apply_tpu(w)
+        if self.variant == "tup":
+            return self.apply_tup(w)
+        return self.apply_tup_star(w)

@@ -12,6 +12,7 @@ import scipy.sparse as sp
 import fracgen
 from oracle import amg as oamg
 from oracle import dense, rng, schur
+from oracle.adjoint import operator_matrix as adjoint_operator
 from oracle import sparse as osp
 from oracle.amg import AMG, AmgOptions
 from oracle.fgmres import fgmres
@@ -46,14 +47,15 @@ def test_fgmres_matches_dense_solution(tiny, variant):
     assert np.linalg.norm(r.x - xs) <= 1e-11 * np.linalg.norm(xs)
 
 
-@pytest.mark.parametrize("variant", ["tpu", "tup"])
+@pytest.mark.parametrize("variant", ["tpu", "tup", "tup_star"])
 def test_algorithm_equals_block_factor_form(small_mixed, variant):
     """Alg. 2 (Alg. 4) with exact inner solves is the operator of Eq. P1
-    (Eq. P2)."""
+    (Eq. P2); the incomplete form is the product D2^-1 L2^-1 of Eq. P2's
+    last two factors."""
     P = small_mixed
     assert set(np.unique(P.state)) == {0, 1, 2}
     M = BlockPreconditioner(P, variant, "exact", "exact")
-    Md = dense.m1_matrix(P) if variant == "tpu" else dense.m2_matrix(P)
+    Md = {"tpu": dense.m1_matrix, "tup": dense.m2_matrix, "tup_star": dense.m2_star_matrix}[variant](P)
     rs = np.random.default_rng(5)
     for _ in range(3):
         w = rs.standard_normal(P.n)
@@ -77,6 +79,52 @@ def test_exact_factors_give_one_iteration(variant):
                                 p_matrix=sp.csr_matrix(dense.schur2_exact(P)))
     r = fgmres(lambda v: J @ v, M, P.b, tol=1e-10, maxit=20)
     assert r.iters == 1 and r.relres <= 1e-9
+
+
+def test_incomplete_tup_with_exact_factors_is_unipotent():
+    """Exact pieces (all faces open, exact S2): Q2 J Q2^T = L2 D2 U2, so
+    M2*^-1 J = Q2^T U2 Q2 exactly.  With every face open C2 = 0, and U2 - I
+    keeps only its (u, p) block S1^-1 Q1: E = M2*^-1 J - I is non-zero with
+    E^2 = 0, so the minimal polynomial is (z - 1)^2 and GMRES stops after
+    exactly two steps (the complete M2 takes one)."""
+    P = fracgen.generate("planes64", N=4, p_stick=0.0, p_slip=0.0, seed=1)
+    J = osp.jacobian(P)
+    M = BlockPreconditioner(P, "tup_star", "exact", "exact",
+                            p_matrix=sp.csr_matrix(dense.schur2_exact(P)))
+    E = adjoint_operator(M, P.n) @ J.toarray() - np.eye(P.n)
+    nu, nt = 3 * P.n_node, 3 * P.n_face
+    # u and p carry different units: rescale u by the size of the (u, p)
+    # block so that every block of E is dimensionless
+    su = np.abs(E[:nu, nu + nt:]).max()
+    assert su > 0
+    d = np.ones(P.n)
+    d[:nu] = su
+    E = E / d[:, None] * d[None, :]
+    off = E.copy()
+    off[:nu, nu + nt:] = 0.0
+    assert np.abs(off).max() <= 1e-10
+    assert np.abs(E @ E).max() <= 1e-10
+    r = fgmres(lambda v: J @ v, M, P.b, tol=1e-10, maxit=20)
+    assert r.iters == 2 and r.relres <= 1e-9
+
+
+def test_complete_tup_is_U2_inverse_times_incomplete(small_mixed):
+    """M2^-1 = U2^-1 M2*^-1 (Eq. P2) with the AMG V-cycles as the inner
+    S~1^-1 and S~2^-1: the two algorithms differ by exactly Eq. P2's first
+    factor, built from the V-cycle operators column by column."""
+    P = small_mixed
+    opt = AmgOptions(coarse_max=20)
+    Mc = BlockPreconditioner(P, "tup", opt=opt, opt_p=AmgOptions(coarse_max=8))
+    Ms = BlockPreconditioner(P, "tup_star", opt=opt, opt_p=AmgOptions(coarse_max=8))
+    nu = 3 * P.n_node
+    S1i = adjoint_operator(Ms.u_inv, nu)
+    S2 = np.linalg.inv(adjoint_operator(Ms.p_inv, P.n_face))
+    U, _, _, Q = dense.m2_factors(P, S1_inv=S1i, S2_tilde=S2)
+    rs = np.random.default_rng(9)
+    for _ in range(3):
+        w = rs.standard_normal(P.n)
+        a, b = Mc(w), Q.T @ (U @ (Q @ Ms(w)))
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a)
 
 
 def test_prop31_unit_eigenvalues_tpu(small_mixed):

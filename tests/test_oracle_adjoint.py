@@ -29,7 +29,7 @@ def test_transposed_vcycle_is_the_transpose(small):
     assert np.abs(Bt - B.T).max() <= 1e-10 * np.abs(B).max()
 
 
-@pytest.mark.parametrize("variant", ["tpu", "tup"])
+@pytest.mark.parametrize("variant", ["tpu", "tup", "tup_star"])
 @pytest.mark.parametrize("inner", ["amg", "exact"])
 def test_transposed_preconditioner_is_the_transpose(small, variant, inner):
     M = BlockPreconditioner(small, variant, inner, inner, opt=AmgOptions(coarse_max=20),
@@ -41,7 +41,7 @@ def test_transposed_preconditioner_is_the_transpose(small, variant, inner):
     assert np.abs(Mtd - Md.T).max() <= 1e-9 * np.abs(Md).max()
 
 
-@pytest.mark.parametrize("variant", ["tpu", "tup"])
+@pytest.mark.parametrize("variant", ["tpu", "tup", "tup_star"])
 def test_adjoint_solve_matches_dense(variant):
     P = fracgen.generate("tiny8")
     g = np.zeros(P.n)
