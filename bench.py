@@ -53,11 +53,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rects128", choices=sorted(WORKLOADS))
-    ap.add_argument("--variant", default="tup", choices=["tup", "tpu"])
+    ap.add_argument("--variant", default="tup", choices=["tup", "tpu", "tup_star"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=600)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--variant-steps", type=int, default=1,
+                    help="timed solves per preconditioner variant on one shared setup (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -210,7 +212,7 @@ def ours(args, rank, world, local_rank):
     blocks = fs.device_blocks(P)
     b = torch.from_numpy(P.b).cuda()
     x = torch.zeros_like(b)
-    variant_bit = 1 << fs.VARIANTS[args.variant]
+    variant_bit = fs.variant_bit(args.variant)
 
     def make_ctx(prec):
         ctx = fs.Context(fs.default_options(precision=prec, variants=variant_bit, verbose=args.verbose))
@@ -262,6 +264,14 @@ def ours(args, rank, world, local_rank):
     jac = ctx.kernel_stats(fs.FC_K_JAC)
     cgs = ctx.kernel_stats(fs.FC_K_CGS)
     prec = ctx.kernel_stats(fs.FC_K_PREC)
+    detail = {}
+    for name, k in (("vcycle_u", fs.FC_K_VCYCLE), ("vcycle_p", fs.FC_K_VCYCLE_P), ("resid0", fs.FC_K_RESID0),
+                    ("restrict0", fs.FC_K_RESTRICT0), ("prolong0", fs.FC_K_PROLONG0), ("coarse0", fs.FC_K_COARSE0),
+                    ("smooth0", fs.FC_K_SMOOTH0), ("jac", fs.FC_K_JAC), ("cgs", fs.FC_K_CGS)):
+        n_, ms_, b_ = ctx.kernel_stats(k)
+        if n_:
+            detail[name] = {"ms_per_launch": ms_ / n_, "launches_per_step": n_ / args.steps,
+                            "GBps_alg": (b_ / (ms_ * 1e-3) / 1e9) if (b_ and ms_) else None}
     ctx.profile(False)
     x_mixed = x.cpu().numpy().copy()
 
@@ -286,6 +296,33 @@ def ours(args, rank, world, local_rank):
                 "relres": r64[-1],
                 "mixed_vs_fp64_rel_diff": float(np.linalg.norm(x_mixed - x64) / np.linalg.norm(x64))}
         del c64
+        ctx = make_ctx(args.precision)
+
+    # the three preconditioners on one setup (outside the timed region):
+    # iterations against time per iteration
+    variants = None
+    if args.variant_steps > 0:
+        del ctx
+        torch.cuda.empty_cache()
+        cv = fs.Context(fs.default_options(precision=args.precision, variants=3, verbose=args.verbose))
+        cv.setup(blocks, P.n_node, P.n_face)
+        variants = {}
+        for name in ("tpu", "tup", "tup_star"):
+            cv.solve(name, b, x, args.tol, args.maxit, allow_fail=True)
+            cv.profile(True)
+            ts = []
+            for _ in range(args.variant_steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rc, it_v, rr_v = cv.solve(name, b, x, args.tol, args.maxit, allow_fail=True)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            pr = cv.kernel_stats(fs.FC_K_PREC)
+            cv.profile(False)
+            variants[name] = {"solve_s": statistics.mean(ts) / 1e3, "iters": it_v, "relres": rr_v,
+                              "prec_apply_ms": pr[1] / max(pr[0], 1)}
+        del cv
         ctx = make_ctx(args.precision)
 
     # end to end through the C-ABI with host buffers
@@ -345,8 +382,10 @@ def ours(args, rank, world, local_rank):
         "breakdown": {"setup_s": mean_setup, "solve_s": mean_solve, "iters": its[-1], "relres": rrs[-1],
                       "prec_apply_ms": prec[1] / max(prec[0], 1), "jac_ms": jac[1] / max(jac[0], 1),
                       "cgs_pass_ms": cgs[1] / max(cgs[0], 1),
-                      "smoother_share_of_solve": (sm_ms / (sum(solve_ms))) if solve_ms else None},
+                      "smoother_share_of_solve": (sm_ms / (sum(solve_ms))) if solve_ms else None,
+                      "kernels": detail},
         "fp64": fp64,
+        "variants": variants,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -365,9 +404,8 @@ def vcycle_case(args):
     import paper_2112_12397_gb300 as fs
     fracgen.build()
     P = fracgen.generate(args.workload)
-    v = fs.VARIANTS[args.variant]
-    ctx = fs.context_for(P, fs.default_options(precision=args.precision, variants=1 << v))
-    hier = fs.FC_H_TUP_U if v == fs.FC_TUP else fs.FC_H_TPU_U
+    ctx = fs.context_for(P, fs.default_options(precision=args.precision, variants=fs.variant_bit(args.variant)))
+    hier = fs.FC_H_TPU_U if args.variant == "tpu" else fs.FC_H_TUP_U
     f = torch.randn(3 * P.n_node, dtype=torch.float64, device="cuda")
     x = torch.zeros_like(f)
     for _ in range(2):

@@ -52,8 +52,11 @@ typedef enum {
   FC_NOT_SETUP = 9        /* fc_setup has not built what the call needs */
 } fc_status;
 
-/* Variants of the block preconditioner (Sec. 3). */
-enum { FC_TPU = 0, FC_TUP = 1 };
+/* Variants of the block preconditioner (Sec. 3).  FC_TUP_STAR is the
+ * incomplete t-u-p factorisation D2^-1 L2^-1 of Eq. P2 (the remark after
+ * Prop. 3.2): one S1 V-cycle per application instead of two.  It uses the
+ * t-u-p setup, so bit FC_TUP of fc_options.variants builds it. */
+enum { FC_TPU = 0, FC_TUP = 1, FC_TUP_STAR = 2 };
 
 /* Precision modes. FP64: everything in double.  MIXED: the AMG hierarchies,
  * smoothers, H~^-1 and the coupling blocks used inside the preconditioner are
@@ -104,13 +107,17 @@ typedef struct {
   uint64_t amg_seed;
   int32_t max_restarts;     /* MIXED: true-residual restarts allowed */
   int32_t verbose;
+  int32_t coarse_graphs;    /* 1: the coarse levels (1 ..) of every V-cycle run as one
+                             * CUDA graph, captured at the first cycle; 0: launched one
+                             * by one.  Same kernels and results either way. */
 } fc_options;
 
 typedef struct fc_ctx fc_ctx;
 
 /* Fill *opt with the defaults (FP64, both variants, theta0 0.08, decay 0.5,
  * coarse_max 1000, coarse_max_p 1000, 12 levels, ratio 0.8, 15 power
- * steps, omega_num 4/3, Chebyshev degree 2 on [0.11, 1.1] * lambda). */
+ * steps, omega_num 4/3, Chebyshev degree 2 on [0.11, 1.1] * lambda,
+ * 3 restarts, coarse_graphs 1). */
 void fc_default_options(fc_options *opt);
 
 /* Create a context bound to the current CUDA device and to `cuda_stream`
@@ -151,7 +158,8 @@ int fc_residual(fc_ctx *ctx, const double *d_b, const double *d_x, double *d_r, 
 int fc_residual_noalloc(fc_ctx *ctx, const double *d_b, const double *d_x, double *relres);
 
 /* d_v = M^-1 d_w: app_tpu (Alg. 2) for FC_TPU, app_tup (Alg. 4) for FC_TUP,
- * device vectors of length n. */
+ * D2^-1 L2^-1 (Eq. P2 without its first factor) for FC_TUP_STAR; device
+ * vectors of length n. */
 int fc_apply_prec(fc_ctx *ctx, int variant, const double *d_w, double *d_v);
 
 /* Solve J x = b by right-preconditioned FGMRES-CGS2 with x0 = 0 (Sec. 4).
@@ -179,7 +187,8 @@ int fc_solve_host(fc_ctx *ctx, int variant, const double *h_b, double *h_x, doub
 int fc_spmv_adjoint(fc_ctx *ctx, const double *d_x, double *d_y);
 
 /* d_v = M^-T d_w: the transposes of the block factorisations of Eq. P1
- * (FC_TPU) or Eq. P2 (FC_TUP), factors applied in reverse order, with the
+ * (FC_TPU), Eq. P2 (FC_TUP) or its incomplete form L2^-T D2^-T
+ * (FC_TUP_STAR), factors applied in reverse order, with the
  * transposed V-cycle for S~ / S1 (the V-cycles of the symmetric T and S~2 are
  * symmetric). */
 int fc_apply_prec_adjoint(fc_ctx *ctx, int variant, const double *d_w, double *d_v);
@@ -242,8 +251,15 @@ int fc_get_fixed_stress(fc_ctx *ctx, double *h_sk);
  * on: FC_K_SMOOTH0 = one fused Chebyshev step on the finest level of the
  * elasticity hierarchy (S1 or S~); FC_K_JAC = one product J z (all seven
  * blocks); FC_K_CGS = one classical Gram-Schmidt pass (dots + update);
- * FC_K_PREC = one preconditioner application.  (FC_K_VCYCLE is reserved.) */
-enum { FC_K_SMOOTH0 = 0, FC_K_JAC = 1, FC_K_CGS = 2, FC_K_VCYCLE = 3, FC_K_PREC = 4 };
+ * FC_K_PREC = one preconditioner application; FC_K_VCYCLE = one V-cycle of
+ * the elasticity hierarchy inside t-u-p (first of the two); FC_K_RESID0,
+ * FC_K_RESTRICT0, FC_K_PROLONG0 = residual, restriction, prolongation on the
+ * finest level; FC_K_COARSE0 = everything below the finest level;
+ * FC_K_VCYCLE_P = the pressure V-cycle of t-u-p. */
+enum {
+  FC_K_SMOOTH0 = 0, FC_K_JAC = 1, FC_K_CGS = 2, FC_K_VCYCLE = 3, FC_K_PREC = 4, FC_K_RESID0 = 5,
+  FC_K_RESTRICT0 = 6, FC_K_PROLONG0 = 7, FC_K_COARSE0 = 8, FC_K_VCYCLE_P = 9
+};
 
 /* Turn event timing on (enable != 0) or off, clearing what was recorded. */
 int fc_profile(fc_ctx *ctx, int enable);

@@ -17,11 +17,11 @@ LIB_PATH = os.path.join(_HERE, "lib", "libfracsolve.so")
 
 FC_OK, FC_NOT_CONVERGED, FC_BREAKDOWN, FC_SINGULAR_BLOCK, FC_NAN, FC_BAD_ARG, \
     FC_CUDA_ERROR, FC_OOM, FC_INTERNAL, FC_NOT_SETUP = range(10)
-FC_TPU, FC_TUP = 0, 1
+FC_TPU, FC_TUP, FC_TUP_STAR = 0, 1, 2
 FC_FP64, FC_MIXED = 0, 1
 FC_H_TPU_U, FC_H_TPU_P, FC_H_TUP_U, FC_H_TUP_P = range(4)
 FC_M_LEVEL, FC_M_PROLONG, FC_M_S1, FC_M_STILDE, FC_M_S2TILDE = range(5)
-VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP}
+VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP, "tup_star": FC_TUP_STAR}
 
 # exported symbols declared by include/fracsolve.h
 SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_residual", "fc_residual_noalloc",
@@ -30,7 +30,8 @@ SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_residua
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
            "fc_get_fixed_stress", "fc_profile", "fc_kernel_stats", "fc_launch_count", "fc_destroy",
            "fc_strerror", "fc_last_error"]
-FC_K_SMOOTH0, FC_K_JAC, FC_K_CGS, FC_K_VCYCLE, FC_K_PREC = range(5)
+(FC_K_SMOOTH0, FC_K_JAC, FC_K_CGS, FC_K_VCYCLE, FC_K_PREC, FC_K_RESID0, FC_K_RESTRICT0, FC_K_PROLONG0,
+ FC_K_COARSE0, FC_K_VCYCLE_P) = range(10)
 
 
 class FcError(RuntimeError):
@@ -45,7 +46,7 @@ class fc_options(C.Structure):
                 ("max_levels", C.c_int32), ("max_ratio", C.c_double), ("power_steps", C.c_int32),
                 ("omega_num", C.c_double), ("cheb_degree", C.c_int32), ("cheb_hi", C.c_double),
                 ("cheb_lo", C.c_double), ("amg_seed", C.c_uint64), ("max_restarts", C.c_int32),
-                ("verbose", C.c_int32)]
+                ("verbose", C.c_int32), ("coarse_graphs", C.c_int32)]
 
 
 class fc_bsr(C.Structure):
@@ -109,6 +110,13 @@ def load(build_if_missing: bool = False):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def variant_bit(variant: str) -> int:
+    """The fc_options.variants bit whose setup a variant needs (the
+    incomplete t-u-p form runs on the t-u-p setup)."""
+    v = VARIANTS[variant]
+    return 1 << (FC_TUP if v == FC_TUP_STAR else v)
 
 
 def default_options(**over) -> fc_options:

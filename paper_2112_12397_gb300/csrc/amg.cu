@@ -33,6 +33,10 @@ namespace {
 constexpr int kT = 256;
 inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
 
+// levels whose rows hold more blocks than this on average use the
+// lane-group BSR kernel instead of sliced ELL (coarse levels)
+constexpr double kSellMaxMeanRow = 40.0;
+
 __device__ inline double frob2(const double *v, int bs) {
   double s = 0.0;
   for (int k = 0; k < bs; k++) s = __dadd_rn(s, __dmul_rn(v[k], v[k]));
@@ -664,10 +668,11 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
     LevelCycle<TP> &c = C[l];
     const int64_t n = (int64_t)L.nb * L.B;
     const bool last = (l + 1 == H.lev.size());
+    const bool sell = L.nb == 0 || (double)L.S.nnzb / L.nb <= kSellMaxMeanRow;
     if constexpr (std::is_same<TP, double>::value) {
       c.S = L.S.view();
       if (!last) { c.P = L.P.view(); c.R = L.R.view(); c.Dinv = L.Dinv.p; }
-      c.Ss = L.Ssd.nbr == L.nb && L.Ssd.sp.p ? std::move(L.Ssd) : to_sell<TP>(L.S.view(), s);
+      if (sell) c.Ss = L.Ssd.nbr == L.nb && L.Ssd.sp.p ? std::move(L.Ssd) : to_sell<TP>(L.S.view(), s);
     } else {
       if (!last) {
         c.R_own = copy_cast<TP, double>(L.R.view(), s);
@@ -680,8 +685,19 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
         }
         c.Dinv = c.Dinv_own.p;
       }
-      c.Ss = L.Ssf.nbr == L.nb && L.Ssf.sp.p ? std::move(L.Ssf) : to_sell<TP>(L.S.view(), s);
+      if (sell) c.Ss = L.Ssf.nbr == L.nb && L.Ssf.sp.p ? std::move(L.Ssf) : to_sell<TP>(L.S.view(), s);
+      else {
+        c.S_own = copy_cast<TP, double>(L.S.view(), s);
+        c.S = c.S_own.view();
+      }
     }
+    L.Ssf = Sell<float>();
+    L.Ssd = Sell<double>();
+    c.op.sell = sell;
+    c.op.sv = c.Ss.view();
+    c.op.bv = c.S;
+    c.op.nnzb = L.S.nnzb;
+    c.op.nbr = L.nb;
     if (!last) c.Ps = to_sell<TP>(L.P.view(), s);
     c.f.alloc(n > 0 ? n : 1);
     c.x.alloc(n > 0 ? n : 1);
@@ -777,6 +793,9 @@ void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int 
   H.prm = prm;
   H.B = B;
   H.built = false;
+  H.graphs = prm.graphs;
+  for (auto &row : H.coarse)
+    for (auto &g : row) g.reset();
   if (B == 3) setup_levels<3>(H, std::move(S0), precision, s);
   else if (B == 1) setup_levels<1>(H, std::move(S0), precision, s);
   else throw Error(FC_BAD_ARG, "AMG block size must be 1 or 3");
@@ -788,13 +807,64 @@ namespace {
 // column indices, row pointers), the iterate gathered once, f, d read and
 // written, the new iterate and the inverse diagonal blocks
 template <int B, typename TP>
-double cheb_bytes(const Sell<TP> &S, bool read_d) {
+double cheb_bytes(const LevelOp<TP> &S, bool read_d) {
   const double sz = sizeof(TP);
   return (double)S.nnzb * (B * B * sz + 4) + (double)(S.nbr + 1) * 4 +
          (double)S.nbr * B * sz * (read_d ? 5 : 4) + (double)S.nbr * B * B * sz;
 }
 
+template <int BR, int BC, typename TP, typename TX, typename Epi>
+inline void op_spmv(const LevelOp<TP> &A, const TX *x, const Epi &e, cudaStream_t s) {
+  if (A.sell) sell_spmv<BR, BC>(A.sv, x, e, s);
+  else spmv<BR, BC>(A.bv, x, e, s);
+}
+template <int BR, int BC, typename TP, typename TX, typename TY, typename TZ>
+inline void op_axpby(const LevelOp<TP> &A, const TX *x, TY *y, double alpha, double beta, const TZ *z,
+                     cudaStream_t s) {
+  EpiAxpby<BR, TP, TY, TZ> e{y, z, (TP)alpha, (TP)beta};
+  op_spmv<BR, BC>(A, x, e, s);
+}
+
+
 template <int B, typename TP, bool TR = false>
+void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *f, TP *xout, cudaStream_t s);
+
+// Levels 1 .. of the cycle (level-1 f in, level-1 x out) replayed as one CUDA
+// graph: the coarse levels are many short kernels whose launch cost exceeds
+// their run time.  Captured on a private stream at the first use.
+template <int B, typename TP, bool TR>
+void coarse_graph(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s) {
+  GraphExec &ge = H.coarse[sizeof(TP) == 8 ? 1 : 0][TR ? 1 : 0];
+  if (!ge.g) {
+    cudaStream_t cs = nullptr;
+    FS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    const unsigned long long k0 = launch_count();
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        cycle_level<B, TP, TR>(H, C, 1, C[1].f.p, C[1].x.p, cs);
+      } catch (...) {
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        throw;
+      }
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    const unsigned long long captured = launch_count() - k0;
+    add_launches(-(long long)captured);   // recorded, not run
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.g, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    FS_CUDA(e);
+    ge.kernels = captured;
+  }
+  FS_CUDA(cudaGraphLaunch(ge.g, s));
+  add_launches((long long)ge.kernels);
+}
+
+template <int B, typename TP, bool TR>
 void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *f, TP *xout, cudaStream_t s) {
   const int L = (int)C.size();
   if (l == L - 1) {
@@ -806,9 +876,9 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
     return;
   }
   LevelCycle<TP> &c = C[l];
-  const SellView<TP> Sop = TR ? c.SsT.view() : c.Ss.view();
+  const LevelOp<TP> &Sop = TR ? c.opT : c.op;
   const TP *Dv = TR ? c.DinvT.p : c.Dinv;
-  const int64_t nb = c.Ss.nbr;
+  const int64_t nb = c.op.nbr;
   const int deg = H.prm.cheb_degree;
   TP *buf[2] = {c.xa.p, xout};
   int cur = 0;
@@ -821,32 +891,41 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
     double rn = 1.0 / (2.0 * c.sigma - rho);
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, Dv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    sell_spmv<B, B>(Sop, buf[cur], e, s);
-    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, true));
+    op_spmv<B, B>(Sop, buf[cur], e, s);
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.op, true));
     cur ^= 1;
     rho = rn;
   }
   // residual, restriction, coarse correction, prolongation
-  sell_axpby<B, B>(Sop, buf[cur], c.r.p, -1.0, 1.0, f, s);
+  if (pf) pf->start(PK_RESID0, s);
+  op_axpby<B, B>(Sop, buf[cur], c.r.p, -1.0, 1.0, f, s);
+  if (pf) pf->stop(PK_RESID0, s, cheb_bytes<B, TP>(c.op, false) - (double)c.op.nbr * B * B * sizeof(TP));
   LevelCycle<TP> &cn = C[l + 1];
+  if (pf) pf->start(PK_RESTRICT0, s);
   spmv_axpby<B, B>(c.R, c.r.p, cn.f.p, 1.0, 0.0, (const TP *)nullptr, s);
-  cycle_level<B, TP, TR>(H, C, l + 1, cn.f.p, cn.x.p, s);
+  if (pf) pf->stop(PK_RESTRICT0, s, (double)c.R.nnzb * (B * B * sizeof(TP) + 4) + (double)c.R.nbr * 4);
+  if (pf) pf->start(PK_COARSE0, s);
+  if (l == 0 && H.graphs && L > 2) coarse_graph<B, TP, TR>(H, C, s);
+  else cycle_level<B, TP, TR>(H, C, l + 1, cn.f.p, cn.x.p, s);
+  if (pf) pf->stop(PK_COARSE0, s, 0.0);
+  if (pf) pf->start(PK_PROLONG0, s);
   sell_axpby<B, B>(c.Ps.view(), cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
+  if (pf) pf->stop(PK_PROLONG0, s, (double)c.Ps.nnzb * (B * B * sizeof(TP) + 4) + (double)c.Ps.nbr * 4);
   // post-smoothing from the corrected iterate
   rho = 1.0 / c.sigma;
   {
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, Dv, (TP)0, (TP)(1.0 / c.theta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    sell_spmv<B, B>(Sop, buf[cur], e, s);
-    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, false));
+    op_spmv<B, B>(Sop, buf[cur], e, s);
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.op, false));
     cur ^= 1;
   }
   for (int k = 1; k < deg; k++) {
     double rn = 1.0 / (2.0 * c.sigma - rho);
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, Dv, (TP)(rn * rho), (TP)(2.0 * rn / c.delta)};
     if (pf) pf->start(PK_SMOOTH0, s);
-    sell_spmv<B, B>(Sop, buf[cur], e, s);
-    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.Ss, true));
+    op_spmv<B, B>(Sop, buf[cur], e, s);
+    if (pf) pf->stop(PK_SMOOTH0, s, cheb_bytes<B, TP>(c.op, true));
     cur ^= 1;
     rho = rn;
   }
@@ -891,7 +970,16 @@ void prepare_transpose(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_
     LevelCycle<TP> &c = C[l];
     if (l + 1 == H.lev.size()) break;   // the coarsest level uses cinvT
     Bsr<double> St = transpose(L.S.view(), s);
-    c.SsT = to_sell<TP>(St.view(), s);
+    c.opT.sell = c.op.sell;
+    c.opT.nnzb = c.op.nnzb;
+    c.opT.nbr = c.op.nbr;
+    if (c.op.sell) {
+      c.SsT = to_sell<TP>(St.view(), s);
+      c.opT.sv = c.SsT.view();
+    } else {
+      c.St_own = copy_cast<TP, double>(St.view(), s);
+      c.opT.bv = c.St_own.view();
+    }
     const int64_t nb = L.nb;
     c.DinvT.alloc((size_t)nb * L.B * L.B);
     k_transpose_blocks<TP><<<blocks_for(nb, 256, kSMs * 8), 256, 0, s>>>(nb, L.B, c.Dinv, c.DinvT.p);

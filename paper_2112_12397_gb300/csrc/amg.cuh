@@ -19,6 +19,7 @@ struct AmgParams {
   double cheb_hi = 1.1, cheb_lo = 0.1;
   uint64_t seed = 0;
   int verbose = 0;
+  bool graphs = true;   // replay the coarse levels of the cycle as a CUDA graph
 };
 
 // Per-level data built in double precision.
@@ -36,9 +37,22 @@ struct LevelSetup {
   DBuf<float> Dinvf;
 };
 
+// Level operator as seen by the cycle: sliced ELL (one thread per row) for
+// short rows, BSR with a lane group per row for long rows (coarse levels).
+template <typename TP>
+struct LevelOp {
+  bool sell = true;
+  SellView<TP> sv;
+  BsrView<TP> bv;
+  int64_t nnzb = 0;
+  int nbr = 0;
+};
+
 // Per-level data of the cycle in precision TP.
 template <typename TP>
 struct LevelCycle {
+  LevelOp<TP> op, opT;           // S and S^T as used by the cycle
+  Bsr<TP> St_own;                // S^T in BSR form for long-row levels
   BsrView<TP> S, P, R;
   const TP *Dinv = nullptr;
   Bsr<TP> S_own, P_own, R_own;   // used when TP differs from double
@@ -48,6 +62,31 @@ struct LevelCycle {
   DBuf<TP> Dinv_own;
   DBuf<TP> f, x, xa, d, r;       // right-hand side, iterate (two buffers), direction, residual
   double theta = 0, delta = 0, sigma = 0;
+};
+
+// An instantiated CUDA graph (move-only) and the kernel launches it replays.
+struct GraphExec {
+  cudaGraphExec_t g = nullptr;
+  unsigned long long kernels = 0;
+  GraphExec() = default;
+  GraphExec(const GraphExec &) = delete;
+  GraphExec &operator=(const GraphExec &) = delete;
+  GraphExec(GraphExec &&o) noexcept : g(o.g), kernels(o.kernels) { o.g = nullptr; }
+  GraphExec &operator=(GraphExec &&o) noexcept {
+    if (this != &o) {
+      reset();
+      g = o.g;
+      kernels = o.kernels;
+      o.g = nullptr;
+    }
+    return *this;
+  }
+  ~GraphExec() { reset(); }
+  void reset() {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+    kernels = 0;
+  }
 };
 
 struct Hierarchy {
@@ -63,6 +102,10 @@ struct Hierarchy {
   Profiler *prof = nullptr;      // times the level-0 smoother steps when set
   bool have_t = false;           // transposed cycle data built
   DBuf<double> cinvT;            // transposed coarsest inverse
+  // levels 1 .. of the cycle as one graph: [double precision][transposed];
+  // its buffers (level-1 f and x and below) are fixed for the hierarchy
+  bool graphs = true;
+  GraphExec coarse[2][2];
   int levels() const { return (int)lev.size(); }
 };
 

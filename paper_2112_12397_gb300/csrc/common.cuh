@@ -30,6 +30,7 @@ struct Error : std::runtime_error {
 // counts it (fc_launch_count)
 void count_launch();
 unsigned long long launch_count();
+void add_launches(long long delta);   // kernels replayed by a graph (+) or captured only (-)
 #define FS_LAUNCHED()               \
   do {                              \
     ::fs::count_launch();           \
@@ -114,7 +115,10 @@ struct Bsr {
 
 // ---------------------------------------------------------------- profiling
 // CUDA-event timing of selected kernels on the launching stream.
-enum ProfKernel { PK_SMOOTH0 = 0, PK_JAC = 1, PK_CGS = 2, PK_VCYCLE = 3, PK_PREC = 4, PK_N = 5 };
+enum ProfKernel {
+  PK_SMOOTH0 = 0, PK_JAC = 1, PK_CGS = 2, PK_VCYCLE = 3, PK_PREC = 4, PK_RESID0 = 5, PK_RESTRICT0 = 6,
+  PK_PROLONG0 = 7, PK_COARSE0 = 8, PK_VCYCLE_P = 9, PK_N = 10
+};
 struct Profiler {
   bool on = false;
   std::vector<cudaEvent_t> pool;

@@ -46,66 +46,18 @@ __global__ void k_face_hinv(int64_t nf, const TP *Hinv, const TP *in, TP *out) {
   }
 }
 
-// partial[(c0+q) * gridDim.x + block] = sum over this block's elements of V_{c0+q} . w
-constexpr int kMdotBlocks = 2 * kSMs;
-constexpr int kMdotThreads = 256;
-constexpr int kMdotChunk = 8;
-
-__global__ void __launch_bounds__(kMdotThreads)
-    k_mdot(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ w, double *partial) {
-  __shared__ double sm[kMdotThreads / 32][kMdotChunk];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c0 = 0; c0 < m; c0 += kMdotChunk) {
-    const int nq = min(kMdotChunk, m - c0);
-    double acc[kMdotChunk];
-#pragma unroll
-    for (int q = 0; q < kMdotChunk; q++) acc[q] = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-      const double we = w[e];
-#pragma unroll
-      for (int q = 0; q < kMdotChunk; q++)
-        if (q < nq) acc[q] += V[(int64_t)(c0 + q) * n + e] * we;
-    }
-#pragma unroll
-    for (int q = 0; q < kMdotChunk; q++) {
-      double v = warp_sum(acc[q]);
-      if (lane == 0) sm[wid][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < nq) {
-      double v = 0.0;
-      for (int k = 0; k < kMdotThreads / 32; k++) v += sm[k][threadIdx.x];
-      partial[(int64_t)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
-    }
-    __syncthreads();
-  }
-}
-
-// h[i] = sum_b partial[i][b]; hacc[i] (+)= h[i]
-__global__ void k_mdot_final(const double *partial, int m, int nb, double *h, double *hacc, int accumulate) {
-  const int lane = threadIdx.x & 31;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += (gridDim.x * blockDim.x) >> 5) {
-    double v = 0.0;
-    for (int b = lane; b < nb; b += 32) v += partial[(int64_t)i * nb + b];
-    v = warp_sum(v);
-    if (lane == 0) {
-      h[i] = v;
-      hacc[i] = accumulate ? hacc[i] + v : v;
-    }
-  }
-}
-
-// w -= sum_i V_i h_i
-__global__ void k_msub(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ h, double *w) {
-  extern __shared__ double hs[];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) hs[i] = h[i];
-  __syncthreads();
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i < m; i++) s += V[(int64_t)i * n + e] * hs[i];
-    w[e] -= s;
+// out = Hinv in per face, and neg = -out (the t block of D2^-1 L2^-1)
+template <typename TP>
+__global__ void k_face_hinv_neg(int64_t nf, const TP *Hinv, const TP *in, TP *out, TP *neg) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const TP *h = Hinv + f * 9;
+    TP a = in[3 * f], b = in[3 * f + 1], c = in[3 * f + 2];
+    const TP o0 = h[0] * a + h[1] * b + h[2] * c;
+    const TP o1 = h[3] * a + h[4] * b + h[5] * c;
+    const TP o2 = h[6] * a + h[7] * b + h[8] * c;
+    out[3 * f] = o0; out[3 * f + 1] = o1; out[3 * f + 2] = o2;
+    neg[3 * f] = -o0; neg[3 * f + 1] = -o1; neg[3 * f + 2] = -o2;
   }
 }
 
@@ -120,6 +72,107 @@ __global__ void k_mcomb(const TP *__restrict__ Z, int k, int64_t n, const double
     double s = 0.0;
     for (int j = 0; j < k; j++) s += (double)Z[(int64_t)j * n + e] * ys[j];
     x[e] = s;
+  }
+}
+
+// Classical Gram-Schmidt passes over the basis V (m vectors of length n,
+// row-major).  Both kernels are bound by the FP64 FMA rate rather than by
+// HBM on this part, so they are laid out for arithmetic throughput: the dot
+// kernel sweeps the vector with a grid of 8 blocks per SM, kCgsQ basis
+// vectors per sweep (w is re-read per sweep from L2), and reduces per block
+// into partial sums that a second kernel adds in a fixed order; the update
+// kernel gives each thread one entry of w and all m basis vectors.
+constexpr int kCgsT = 256, kCgsQ = 4;
+constexpr int kCgsDotGrid = kSMs * 8, kCgsSubGrid = kSMs * 16;
+
+// partial[i * gridDim.x + block] = V_i . w over the block's entries (i < m);
+// with_norm adds row m = w . w
+__global__ void __launch_bounds__(kCgsT)
+    k_cgs_dot(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ w, double *partial,
+              int with_norm) {
+  __shared__ double red[kCgsT / 32][kCgsQ];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int mm = m + (with_norm ? 1 : 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int i0 = 0; i0 < mm; i0 += kCgsQ) {
+    const int nq = min(kCgsQ, mm - i0);
+    double acc[kCgsQ];
+#pragma unroll
+    for (int q = 0; q < kCgsQ; q++) acc[q] = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + tid; e < n; e += stride) {
+      const double we = __ldg(w + e);
+#pragma unroll
+      for (int q = 0; q < kCgsQ; q++)
+        if (q < nq) {
+          const int i = i0 + q;
+          const double v = i < m ? __ldg(V + (int64_t)i * n + e) : we;
+          acc[q] += v * we;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kCgsQ; q++) {
+      const double r = warp_sum(acc[q]);
+      if (lane == 0) red[wid][q] = r;
+    }
+    __syncthreads();
+    if (tid < nq) {
+      double sum = 0.0;
+#pragma unroll
+      for (int k = 0; k < kCgsT / 32; k++) sum += red[k][tid];
+      partial[(int64_t)(i0 + tid) * gridDim.x + blockIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// h[i] = sum_b partial[i][b] (fixed order); hacc[i] (+)= h[i] for i < m;
+// row m (if present) goes to *extra
+__global__ void k_cgs_final(const double *partial, int m, int rows, int nb, double *h, double *hacc,
+                            int accumulate, double *extra) {
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows; i += (gridDim.x * blockDim.x) >> 5) {
+    double v = 0.0;
+    for (int b = lane; b < nb; b += 32) v += partial[(int64_t)i * nb + b];
+    v = warp_sum(v);
+    if (lane == 0) {
+      if (i < m) {
+        h[i] = v;
+        hacc[i] = accumulate ? hacc[i] + v : v;
+      } else {
+        *extra = v;
+      }
+    }
+  }
+}
+
+// w -= V h, one thread per entry; partial_norm (if given): partial[block] =
+// the block's share of ||w||^2 after the update
+__global__ void __launch_bounds__(kCgsT)
+    k_cgs_sub(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ h, double *w,
+              double *partial_norm) {
+  extern __shared__ double hs[];
+  __shared__ double red[kCgsT / 32];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double nn = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + tid; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < m; i++) sum += __ldg(V + (int64_t)i * n + e) * hs[i];
+    const double we = w[e] - sum;
+    w[e] = we;
+    nn += we * we;
+  }
+  if (partial_norm) {
+    nn = warp_sum(nn);
+    if (lane == 0) red[wid] = nn;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int k = 0; k < kCgsT / 32; k++) sum += red[k];
+      partial_norm[blockIdx.x] = sum;
+    }
   }
 }
 
@@ -209,6 +262,11 @@ struct fc_ctx {
 
 namespace {
 
+bool valid_variant(int v) { return v == FC_TPU || v == FC_TUP || v == FC_TUP_STAR; }
+
+// the incomplete t-u-p form uses the t-u-p setup (S1, S~2 and their AMG)
+bool built(const fc_ctx &c, int v) { return c.have[v == FC_TUP_STAR ? FC_TUP : v]; }
+
 AmgParams amg_params(const fc_options &o, bool pressure) {
   AmgParams p;
   p.theta0 = o.theta0;
@@ -223,6 +281,7 @@ AmgParams amg_params(const fc_options &o, bool pressure) {
   p.cheb_lo = o.cheb_lo;
   p.seed = o.amg_seed;
   p.verbose = o.verbose;
+  p.graphs = o.coarse_graphs != 0;
   return p;
 }
 
@@ -260,7 +319,8 @@ void prepare_prec(fc_ctx &c, PrecData<TP> &P) {
   P.ready = true;
 }
 
-// z = M^-1 w, both in precision TP (Alg. 2 or Alg. 4)
+// z = M^-1 w, both in precision TP (Alg. 2, Alg. 4, or the incomplete
+// t-u-p form D2^-1 L2^-1 of Eq. P2)
 template <typename TP>
 void apply_prec(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
   cudaStream_t s = c.s;
@@ -268,13 +328,33 @@ void apply_prec(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
   const int64_t nf = c.nf;
   const TP *w_u = w, *w_t = w + nu, *w_p = w + nu + nt;
   TP *z_u = z, *z_t = z + nu, *z_p = z + nu + nt;
-  if (variant == FC_TUP) {
+  if (variant == FC_TUP_STAR) {
+    Hierarchy &Hu = c.hier[FC_H_TUP_U], &Hp = c.hier[FC_H_TUP_P];
+    if (nf) {   // t_t = H~^-1 w_t; v_t = -t_t
+      k_face_hinv_neg<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p, z_t);
+      FS_LAUNCHED();
+    }
+    sell_axpby<3, 3>(P.sC1.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);   // y_u = w_u + C1 t_t
+    c.prof.start(PK_VCYCLE, s);
+    amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                  // v_u = S~1^-1 y_u
+    c.prof.stop(PK_VCYCLE, s, 0.0);
+    if (nf) {
+      sell_axpby<1, 3>(P.sQ2.view(), z_u, P.tp.p, -1.0, 1.0, w_p, s);   // y_p = w_p - Q2 v_u
+      c.prof.start(PK_VCYCLE_P, s);
+      amg_vcycle<TP>(Hp, P.tp.p, z_p, s);                                // v_p = S~2^-1 y_p
+      c.prof.stop(PK_VCYCLE_P, s, 0.0);
+    }
+  } else if (variant == FC_TUP) {
     Hierarchy &Hu = c.hier[FC_H_TUP_U], &Hp = c.hier[FC_H_TUP_P];
     if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }   // 1
     sell_axpby<3, 3>(P.sC1.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                // 2
+    c.prof.start(PK_VCYCLE, s);
     amg_vcycle<TP>(Hu, P.tu.p, P.su.p, s);                                                            // 3
+    c.prof.stop(PK_VCYCLE, s, 0.0);
     sell_axpby<1, 3>(P.sQ2.view(), P.su.p, P.tp.p, -1.0, 1.0, w_p, s);                              // 4
+    c.prof.start(PK_VCYCLE_P, s);
     if (nf) amg_vcycle<TP>(Hp, P.tp.p, z_p, s);                                                        // 5
+    c.prof.stop(PK_VCYCLE_P, s, 0.0);
     sell_axpby<3, 1>(P.sQ1.view(), z_p, P.tu.p, 1.0, 0.0, (const TP *)nullptr, s);                 // 6
     amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // 7
     axpbyz(z_u, P.su.p, z_u, 1.0, -1.0, nu, s);                                                       // 8
@@ -353,7 +433,23 @@ void apply_prec_t(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
   const int64_t nu = c.nu, nt = c.nt, nf = c.nf;
   const TP *w_u = w, *w_t = w + nu, *w_p = w + nu + nt;
   TP *z_u = z, *z_t = z + nu, *z_p = z + nu + nt;
-  if (variant == FC_TUP) {
+  if (variant == FC_TUP_STAR) {
+    // (D2^-1 L2^-1)^T = L2^-T D2^-T: z_p = S~2^-T w_p; v_u = S~1^-T w_u -
+    // S~1^-T Q2^T z_p, formed as one transposed V-cycle on w_u - Q2^T z_p
+    // (the V-cycle is a fixed linear operator); v_t = H~^-T (C1^T v_u - w_t)
+    Hierarchy &Hu = c.hier[FC_H_TUP_U], &Hp = c.hier[FC_H_TUP_P];
+    if (nf) {
+      amg_vcycle<TP>(Hp, w_p, z_p, s);
+      sell_axpby<3, 1>(P.tQ2.view(), z_p, P.tu.p, -1.0, 1.0, w_u, s);
+    }
+    amg_vcycle_t<TP>(Hu, nf ? P.tu.p : w_u, z_u, s);
+    if (nf) {
+      k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.HinvT.p, w_t, P.tt.p);
+      FS_LAUNCHED();
+      EpiHinvUpdate<TP> e{z_t, P.tt.p, P.HinvT.p};
+      sell_spmv<3, 3>(P.tC1.view(), z_u, e, s);
+    }
+  } else if (variant == FC_TUP) {
     Hierarchy &Hu = c.hier[FC_H_TUP_U], &Hp = c.hier[FC_H_TUP_P];
     if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.HinvT.p, w_t, P.tt.p); FS_LAUNCHED(); }
     sell_axpby<3, 3>(P.tC2.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);        // t_u = w_u + C2^T H~^-T w_t
@@ -407,21 +503,37 @@ void ensure_krylov(fc_ctx &c, int maxit) {
   c.Hm.alloc((size_t)(maxit + 1) * maxit);
   c.cs.alloc(maxit); c.sn.alloc(maxit); c.g.alloc(maxit + 1); c.y.alloc(maxit);
   c.hacc.alloc(maxit + 1); c.htmp.alloc(maxit + 1);
-  c.partial.alloc((size_t)(maxit + 1) * kMdotBlocks);
+  c.partial.alloc((size_t)(maxit + 2) * (size_t)(kCgsSubGrid > kCgsDotGrid ? kCgsSubGrid : kCgsDotGrid));
   c.kcap = maxit;
 }
 
-void cgs_pass(fc_ctx &c, int m, double *w, int accumulate) {
+// Classical Gram-Schmidt applied twice against V_0..V_{m-1}:
+//   h = V^T w; w -= V h; h' = V^T w; w -= V h'; h += h'
+// with ||w||^2 before (w02) and after (w2) folded into the passes.
+void cgs2(fc_ctx &c, int m, double *w) {
   const int64_t n = c.n;
-  c.prof.start(PK_CGS, c.s);
-  k_mdot<<<kMdotBlocks, kMdotThreads, 0, c.s>>>(c.V.p, m, n, w, c.partial.p);
+  cudaStream_t s = c.s;
+  const int nd = kCgsDotGrid, ns = kCgsSubGrid;
+  const int fg = blocks_for((int64_t)(m + 1) * 32, 256, 1024);
+  const size_t hsh = sizeof(double) * m;
+  c.prof.start(PK_CGS, s);
+  k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, 1);
   FS_LAUNCHED();
-  k_mdot_final<<<blocks_for((int64_t)m * 32, 256, 1024), 256, 0, c.s>>>(c.partial.p, m, kMdotBlocks, c.htmp.p,
-                                                                         c.hacc.p, accumulate);
+  k_cgs_final<<<fg, 256, 0, s>>>(c.partial.p, m, m + 1, nd, c.htmp.p, c.hacc.p, 0, c.w02.p);
   FS_LAUNCHED();
-  k_msub<<<vgrid(n), 256, sizeof(double) * m, c.s>>>(c.V.p, m, n, c.htmp.p, w);
+  k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, nullptr);
   FS_LAUNCHED();
-  c.prof.stop(PK_CGS, c.s, (2.0 * m + 3.0) * n * sizeof(double));
+  c.prof.stop(PK_CGS, s, (2.0 * m + 3.0) * n * sizeof(double));
+  c.prof.start(PK_CGS, s);
+  k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, 0);
+  FS_LAUNCHED();
+  k_cgs_final<<<fg, 256, 0, s>>>(c.partial.p, m, m, nd, c.htmp.p, c.hacc.p, 1, nullptr);
+  FS_LAUNCHED();
+  k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, c.partial.p);
+  FS_LAUNCHED();
+  k_cgs_final<<<1, 32, 0, s>>>(c.partial.p, 0, 1, ns, nullptr, nullptr, 0, c.w2.p);
+  FS_LAUNCHED();
+  c.prof.stop(PK_CGS, s, (2.0 * m + 3.0) * n * sizeof(double));
 }
 
 struct FgmresOut {
@@ -465,10 +577,7 @@ FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rt
     c.prof.stop(PK_PREC, s, 0.0);
     if constexpr (ADJ) jac_spmv_t<TP>(c, zj, w);
     else jac_spmv<TP>(c, zj, w);
-    nrm2sq_dev(w, n, c.w02.p, s, c.red.p);
-    cgs_pass(c, j + 1, w, 0);
-    cgs_pass(c, j + 1, w, 1);
-    nrm2sq_dev(w, n, c.w2.p, s, c.red.p);
+    cgs2(c, j + 1, w);
     k_givens<<<1, 1, 0, s>>>(j, maxit + 1, c.hacc.p, c.w2.p, c.w02.p, beta, c.Hm.p, c.cs.p, c.sn.p, c.g.p, c.stat.p);
     FS_LAUNCHED();
     k_scale_by<<<vgrid(n), 256, 0, s>>>(w, n, c.stat.p + 3);
@@ -710,6 +819,7 @@ void fc_default_options(fc_options *o) {
   o->amg_seed = 0;
   o->max_restarts = 3;
   o->verbose = 0;
+  o->coarse_graphs = 1;
 }
 
 int fc_create(fc_ctx **out, const fc_options *opt, void *stream) {
@@ -826,9 +936,9 @@ int fc_residual(fc_ctx *c, const double *b, const double *x, double *r, double *
 }
 
 int fc_apply_prec(fc_ctx *c, int variant, const double *w, double *v) {
-  if (!c || !w || !v || (variant != FC_TPU && variant != FC_TUP)) return FC_BAD_ARG;
+  if (!c || !w || !v || !valid_variant(variant)) return FC_BAD_ARG;
   return run(c, [&]() {
-    FS_REQUIRE(c->ready && c->have[variant], FC_NOT_SETUP, "variant not built by fc_setup");
+    FS_REQUIRE(c->ready && built(*c, variant), FC_NOT_SETUP, "variant not built by fc_setup");
     if (c->opt.precision == FC_MIXED) {
       cast(c->pf.w.p, w, c->n, c->s);
       apply_prec<float>(*c, c->pf, variant, c->pf.w.p, c->pf.out.p);
@@ -843,10 +953,10 @@ int fc_apply_prec(fc_ctx *c, int variant, const double *w, double *v) {
 
 int fc_solve(fc_ctx *c, int variant, const double *b, double *x, double tol, int maxit, int *iters,
              double *relres) {
-  if (!c || !b || !x || (variant != FC_TPU && variant != FC_TUP) || maxit < 1 || maxit > 4000 || !(tol > 0))
+  if (!c || !b || !x || !valid_variant(variant) || maxit < 1 || maxit > 4000 || !(tol > 0))
     return FC_BAD_ARG;
   return run(c, [&]() {
-    FS_REQUIRE(c->ready && c->have[variant], FC_NOT_SETUP, "variant not built by fc_setup");
+    FS_REQUIRE(c->ready && built(*c, variant), FC_NOT_SETUP, "variant not built by fc_setup");
     int rc = c->opt.precision == FC_MIXED ? solve_impl<float>(*c, variant, b, x, tol, maxit, iters, relres)
                                           : solve_impl<double>(*c, variant, b, x, tol, maxit, iters, relres);
     FS_CUDA(cudaStreamSynchronize(c->s));
@@ -886,9 +996,9 @@ int fc_spmv_adjoint(fc_ctx *c, const double *x, double *y) {
 }
 
 int fc_apply_prec_adjoint(fc_ctx *c, int variant, const double *w, double *v) {
-  if (!c || !w || !v || (variant != FC_TPU && variant != FC_TUP)) return FC_BAD_ARG;
+  if (!c || !w || !v || !valid_variant(variant)) return FC_BAD_ARG;
   return run(c, [&]() {
-    FS_REQUIRE(c->ready && c->have[variant], FC_NOT_SETUP, "variant not built by fc_setup");
+    FS_REQUIRE(c->ready && built(*c, variant), FC_NOT_SETUP, "variant not built by fc_setup");
     ensure_adjoint(*c);
     if (c->opt.precision == FC_MIXED) {
       cast(c->pf.w.p, w, c->n, c->s);
@@ -904,11 +1014,11 @@ int fc_apply_prec_adjoint(fc_ctx *c, int variant, const double *w, double *v) {
 
 int fc_solve_adjoint(fc_ctx *c, int variant, const double *g, double *lambda, double tol, int maxit, int *iters,
                      double *relres) {
-  if (!c || !g || !lambda || (variant != FC_TPU && variant != FC_TUP) || maxit < 1 || maxit > 4000 ||
+  if (!c || !g || !lambda || !valid_variant(variant) || maxit < 1 || maxit > 4000 ||
       !(tol > 0))
     return FC_BAD_ARG;
   return run(c, [&]() {
-    FS_REQUIRE(c->ready && c->have[variant], FC_NOT_SETUP, "variant not built by fc_setup");
+    FS_REQUIRE(c->ready && built(*c, variant), FC_NOT_SETUP, "variant not built by fc_setup");
     ensure_adjoint(*c);
     int rc = c->opt.precision == FC_MIXED
                  ? solve_impl<float, true>(*c, variant, g, lambda, tol, maxit, iters, relres)

@@ -215,11 +215,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // lane (p * BR + r) mod 32.  Each lane gathers the products that touch its
 // units (in enumeration order) and computes them, so every entry of C is
 // summed in the same order on every run, with no atomics.
-constexpr int kProdChunk = 256;
+constexpr int kProdChunk = 128;
 
 template <int BR, int BK, int BC>
 __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC,
-                                    double *valC, int ucap) {
+                                    double *valC, int ulo, int ucap) {
   constexpr int BS = BR * BC;
   extern __shared__ double smem[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -234,7 +234,7 @@ __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const 
   const int64_t nwarps = (int64_t)gridDim.x * wpb;
   for (int64_t i = blockIdx.x * (int64_t)wpb + wid; i < A.nbr; i += nwarps) {
     const int cs = rpC[i], cn = rpC[i + 1] - cs;
-    if (cn > ucap) continue;   // handled by the global-memory kernel
+    if (cn <= ulo || cn > ucap) continue;   // another tier (or the global kernel)
     for (int t = lane; t < cn; t += 32) cols[t] = ciC[cs + t];
     for (int t = lane; t < cn * BS; t += 32) acc[t] = 0.0;
     __syncwarp();
@@ -279,7 +279,7 @@ __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const 
           for (int tt = 0; tt < BK; tt++) av[tt] = a[tt];
 #pragma unroll
           for (int cc = 0; cc < BC; cc++) {
-            double sum = 0.0;
+            double sum = 0;
 #pragma unroll
             for (int tt = 0; tt < BK; tt++) sum += av[tt] * b[tt * BC + cc];
             c[cc] += sum;
@@ -311,42 +311,6 @@ __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const 
   }
 }
 
-// Fallback for rows longer than the shared capacity: same order, global slots.
-template <int BR, int BK, int BC>
-__global__ void __launch_bounds__(128)
-    k_spgemm_numeric(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC,
-                     double *valC, int ucap) {
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + wid; i < A.nbr; i += nwarps) {
-    const int cs = rpC[i], cn = rpC[i + 1] - cs;
-    if (cn <= ucap) continue;
-    for (int e = A.rp[i]; e < A.rp[i + 1]; e++) {
-      const int k = A.ci[e];
-      double a[BR * BK];
-#pragma unroll
-      for (int q = 0; q < BR * BK; q++) a[q] = A.val[(int64_t)e * BR * BK + q];
-      for (int f = B.rp[k] + lane; f < B.rp[k + 1]; f += 32) {
-        const int j = B.ci[f];
-        const int p = find_sorted(ciC + cs, cn, j);
-        if (p < 0) continue;   // cannot happen: the symbolic pass saw every j
-        const double *b = B.val + (int64_t)f * BK * BC;
-        double *c = valC + (int64_t)(cs + p) * BR * BC;
-#pragma unroll
-        for (int r = 0; r < BR; r++)
-#pragma unroll
-          for (int cc = 0; cc < BC; cc++) {
-            double s = 0.0;
-#pragma unroll
-            for (int t = 0; t < BK; t++) s += a[r * BK + t] * b[t * BC + cc];
-            c[r * BC + cc] += s;
-          }
-      }
-      __syncwarp();
-    }
-  }
-}
-
 __global__ void k_max_row_len(const int *rp, int n, int *out) {
   int m = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -365,22 +329,24 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   int umax = 0;
   FS_CUDA(cudaMemcpyAsync(&umax, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   FS_CUDA(cudaStreamSynchronize(s));
-  // shared per warp: ucap slots (accumulator + column) and the product chunk;
-  // fit up to 8 warps in ~200 KB
+  // rows are processed in tiers of increasing length so that the shared
+  // accumulators of short rows do not limit the occupancy: per warp, ucap
+  // slots (accumulator + column) and the product chunk
   const size_t per_slot = BS * sizeof(double) + sizeof(int);
   const size_t fixed = (size_t)4 * kProdChunk * BR * sizeof(int);
-  int ucap = umax > 0 ? umax : 1;
-  int wpb = 8;
-  while (wpb > 1 && (size_t)wpb * (ucap * per_slot + fixed) > 200 * 1024) wpb >>= 1;
-  if ((size_t)wpb * (ucap * per_slot + fixed) > 200 * 1024) ucap = (int)((200 * 1024 - fixed) / per_slot);
-  const size_t shm = (size_t)wpb * (ucap * per_slot + fixed);
-  auto kern = k_spgemm_numeric_sh<BR, BK, BC>;
-  FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  kern<<<kSMs * 4, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, ucap);
-  FS_LAUNCHED();
-  if (umax > ucap) {
-    k_spgemm_numeric<BR, BK, BC><<<kSMs * 8, 128, 0, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, ucap);
+  const int tiers[3] = {64, 256, kListCap};
+  FS_REQUIRE(umax <= kListCap, FC_INTERNAL, "spgemm: product row longer than the symbolic pass allows");
+  int ulo = 0, ucap = 0;
+  for (int t = 0; t < 3 && ulo < umax; t++) {
+    ucap = tiers[t];
+    int wpb = 8;
+    while (wpb > 1 && (size_t)wpb * (ucap * per_slot + fixed) > 200 * 1024) wpb >>= 1;
+    const size_t shm = (size_t)wpb * (ucap * per_slot + fixed);
+    auto kern = k_spgemm_numeric_sh<BR, BK, BC>;
+    FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    kern<<<kSMs * 8, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, ulo, ucap);
     FS_LAUNCHED();
+    ulo = ucap;
   }
 }
 
@@ -413,8 +379,6 @@ Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStrea
   k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 1, nullptr, C.rp.p, C.ci.p, ovf.p);
   FS_LAUNCHED();
   pt.mark("symbolic fill");
-  // rows longer than the shared capacity accumulate in place in C.val
-  FS_CUDA(cudaMemsetAsync(C.val.p, 0, sizeof(double) * nnz * C.br * C.bc, s));
   const int sh = A.br * 100 + A.bc * 10 + B.bc;
   switch (sh) {
     case 333: numeric<3, 3, 3>(A, B, C, s); break;

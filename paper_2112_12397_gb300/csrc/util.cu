@@ -10,6 +10,9 @@ int g_verbose = 0;
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(); }
+void add_launches(long long delta) {
+  g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed);
+}
 
 cudaEvent_t Profiler::get() {
   if (used == pool.size()) {

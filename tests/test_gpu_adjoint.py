@@ -66,7 +66,7 @@ def test_transposed_products(fs, name):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
-@pytest.mark.parametrize("variant", ["tpu", "tup"])
+@pytest.mark.parametrize("variant", ["tpu", "tup", "tup_star"])
 def test_adjoint_preconditioner_and_solve(fs, name, variant):
     P, ctx, opt, optp = case(name, fs)
     M = BlockPreconditioner(P, variant, opt=opt, opt_p=optp)
@@ -78,12 +78,15 @@ def test_adjoint_preconditioner_and_solve(fs, name, variant):
     g = np.zeros(P.n)
     g[-P.n_face:] = np.random.default_rng(4).standard_normal(P.n_face)
     lam = torch.zeros(P.n, dtype=torch.float64, device="cuda")
-    rc, it, rr = ctx.solve_adjoint(variant, cuda(g), lam, 1e-8, 400)
+    # M2*^-T leaves the same attainable-accuracy floor near 1e-8 (its p/u
+    # blocks are uncorrected); the other two forms must reach tol
+    star = variant == "tup_star"
+    rc, it, rr = ctx.solve_adjoint(variant, cuda(g), lam, 1e-8, 400, allow_fail=star)
     ref = adjoint.solve_adjoint(P, M, g, 1e-8, 400)
     assert abs(it - ref.iters) <= 1
     assert rel(lam.cpu().numpy(), ref.x) <= 1e-8
     JT = osp.jacobian(P).T.tocsr()
-    assert np.linalg.norm(g - JT @ lam.cpu().numpy()) / np.linalg.norm(g) <= 1e-8
+    assert np.linalg.norm(g - JT @ lam.cpu().numpy()) / np.linalg.norm(g) <= (3e-8 if star else 1e-8)
 
 
 def test_adjoint_matches_dense_on_8cubed(fs):
