@@ -69,6 +69,7 @@ class Level:
     P: sp.csr_matrix | None = None
     R: sp.csr_matrix | None = None
     agg: np.ndarray | None = None
+    nc: int = 0
     info: dict = field(default_factory=dict)
 
 
@@ -221,7 +222,12 @@ def power_lambda(S, Dinv, B, level, opt: AmgOptions) -> float:
 class AMG:
     """Hierarchy and V-cycle for one operator (block size B)."""
 
-    def __init__(self, S: sp.csr_matrix, B: int, opt: AmgOptions | None = None):
+    def __init__(self, S: sp.csr_matrix, B: int, opt: AmgOptions | None = None,
+                 aggregates: list | None = None):
+        """``aggregates``: the (agg, n_coarse) pair of every coarsening step of
+        an earlier hierarchy.  Given, the hierarchy is rebuilt on new values
+        of S with those aggregates (no strength graph, no MIS-2): the same
+        levels, with D^-1, lambda, P, R and the Galerkin products recomputed."""
         self.opt = opt or AmgOptions()
         self.B = B
         self.levels: list[Level] = []
@@ -232,13 +238,19 @@ class AMG:
             n = S.shape[0] // B
             L = Level(S=S, B=B, n=n)
             self.levels.append(L)
-            if n <= self.opt.coarse_max or lvl + 1 >= self.opt.max_levels:
-                break
-            W = strength_graph(S, B, lvl, self.opt)
-            is_root = mis2_greedy(W, priority_keys(n, lvl, self.opt.seed))
-            agg, nc = aggregate(W, is_root)
-            if nc == 0 or nc > self.opt.max_ratio * n:
-                break
+            if aggregates is not None:
+                if lvl >= len(aggregates):
+                    break
+                agg, nc = aggregates[lvl]
+                is_root = np.zeros(n, dtype=bool)
+            else:
+                if n <= self.opt.coarse_max or lvl + 1 >= self.opt.max_levels:
+                    break
+                W = strength_graph(S, B, lvl, self.opt)
+                is_root = mis2_greedy(W, priority_keys(n, lvl, self.opt.seed))
+                agg, nc = aggregate(W, is_root)
+                if nc == 0 or nc > self.opt.max_ratio * n:
+                    break
             Sb = to_bsr(S, B)
             D = diag_blocks(Sb, B)
             Dinv = np.linalg.inv(D)
@@ -252,12 +264,17 @@ class AMG:
             Sc.sort_indices()
             L.Dinv, L.lam, L.P, L.R, L.agg = Dinv, lam, P, R, agg
             L.info = dict(n_coarse=nc, n_roots=int(is_root.sum()))
+            L.nc = nc
             S = Sc
             lvl += 1
         last = self.levels[-1]
         if last.S.shape[0] > self.opt.dense_limit:
             raise RuntimeError(f"coarsest level too large for a dense solve: {last.S.shape[0]}")
         self.lu = sla.lu_factor(last.S.toarray()) if last.S.shape[0] else None
+
+    def aggregates(self) -> list:
+        """(agg, n_coarse) of every coarsening step, for a numeric rebuild."""
+        return [(L.agg, L.nc) for L in self.levels[:-1]]
 
     # -------------------------------------------------------------- apply
     def _cheb(self, L: Level, f: np.ndarray, x0: np.ndarray | None) -> np.ndarray:

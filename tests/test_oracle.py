@@ -279,3 +279,25 @@ def test_vcycle_symmetric_for_symmetric_operator():
         e = e - amg(S @ e)
     e2 = e - amg(S @ e)
     assert np.linalg.norm(e2) < 0.9 * np.linalg.norm(e)
+
+
+def test_amg_numeric_rebuild_on_kept_aggregates():
+    """The numeric rebuild (kept aggregates, new values): on the same S it is
+    the original hierarchy; on 2 S every recomputed piece scales exactly
+    (D^-1 halves, lambda, P and the tentative prolongator stay, the Galerkin
+    operators and the coarsest solve double), so the V-cycle halves; a rebuild
+    that kept any old value would not."""
+    P = fracgen.generate("planes64", N=8, seed=3)
+    S1 = schur.s1(P)
+    opt = AmgOptions(coarse_max=20)
+    a = AMG(S1, 3, opt)
+    assert len(a.levels) >= 3
+    same = AMG(S1, 3, opt, aggregates=a.aggregates())
+    dbl = AMG((2.0 * S1).tocsr(), 3, opt, aggregates=a.aggregates())
+    f = np.random.default_rng(4).standard_normal(S1.shape[0])
+    x = a(f)
+    assert np.array_equal(same(f), x)
+    assert np.linalg.norm(2.0 * dbl(f) - x) <= 1e-14 * np.linalg.norm(x)
+    for La, Ld in zip(a.levels[:-1], dbl.levels[:-1]):
+        assert La.lam == pytest.approx(Ld.lam, rel=1e-13)
+        assert abs(Ld.P - La.P).max() <= 1e-14 * abs(La.P).max()
