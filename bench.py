@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--variant-steps", type=int, default=1,
                     help="timed solves per preconditioner variant on one shared setup (0: skip)")
+    ap.add_argument("--update-steps", type=int, default=1,
+                    help="timed fc_update calls per update case (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -67,6 +69,18 @@ def parse():
     ap.add_argument("--mode", default="bench", choices=["bench", "vcycle"],
                     help="vcycle: fc_setup then two V-cycles of the elasticity hierarchy (profiling case)")
     return ap.parse_args()
+
+
+# nominal dense FP64 rate of a GB300 (the FMA pipes, not the tensor cores)
+FP64_NOMINAL_TFLOPS = 1.25
+
+# DRAM traffic of the fused Chebyshev step from one ncu capture of the same
+# kernel (finest S1 level of the 64^3 three-plane workload, a launch that
+# reads the previous direction): dram__bytes_read.sum + dram__bytes_write.sum
+# against that launch's algorithmic bytes.  The 128^3 launch is too large to
+# capture with the full metric set; its traffic is scaled by the algorithmic
+# bytes (blocks and rows grow together).
+SMOOTHER_CAPTURE = {"dram_bytes": 329128960 + 3432704, "alg_bytes": 329392804}
 
 
 def measured_peaks():
@@ -273,6 +287,18 @@ def ours(args, rank, world, local_rank):
             detail[name] = {"ms_per_launch": ms_ / n_, "launches_per_step": n_ / args.steps,
                             "GBps_alg": (b_ / (ms_ * 1e-3) / 1e9) if (b_ and ms_) else None}
     ctx.profile(False)
+    # the FP64-ALU-bound kernels: J z does one FMA per stored scalar of J;
+    # a Gram-Schmidt pass against j basis vectors does about (2 j + 1) n,
+    # n (k + 2) per pass on average over k iterations
+    fp64_peak = FP64_NOMINAL_TFLOPS * 1e3 / 2.0   # GFMA/s
+    if "jac" in detail:
+        gf = sum(int(t[2].numel()) for t in blocks.values()) / (detail["jac"]["ms_per_launch"] * 1e-3) / 1e9
+        detail["jac"].update({"bound": "alu", "GFMA_per_s": gf, "fp64_peak_GFMA_per_s": fp64_peak,
+                              "frac_fp64": gf / fp64_peak})
+    if "cgs" in detail:
+        gf = P.n * (its[-1] + 2) / (detail["cgs"]["ms_per_launch"] * 1e-3) / 1e9
+        detail["cgs"].update({"bound": "alu", "GFMA_per_s": gf, "fp64_peak_GFMA_per_s": fp64_peak,
+                              "frac_fp64": gf / fp64_peak})
     x_mixed = x.cpu().numpy().copy()
 
     # max over ranks
@@ -325,6 +351,37 @@ def ours(args, rank, world, local_rank):
         del cv
         ctx = make_ctx(args.precision)
 
+    # numeric refresh (fc_update) against a full setup, same patterns: a
+    # hydraulic update (T and Q2 change, S1 and its hierarchy do not) and an
+    # update of every block (A scaled too, so every hierarchy is rebuilt)
+    update = None
+    if args.update_steps > 0:
+        def scaled(src, factors):
+            out = dict(src)
+            for name, f in factors.items():
+                rp, ci, val = src[name][:3]
+                out[name] = (rp, ci, val * f) + tuple(src[name][3:])
+            return out
+        cases = {"hydraulic_T_Q2": scaled(blocks, {"T": 1.3, "Q2": 0.7}),
+                 "all_blocks": scaled(blocks, {"A": 1.1, "T": 1.3, "Q2": 0.7})}
+        update = {}
+        for name, blk in cases.items():
+            ts, its_u = [], None
+            for _ in range(args.update_steps):
+                ctx.setup(blocks, P.n_node, P.n_face)
+                torch.cuda.synchronize()
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                ctx.update(blk, P.n_node, P.n_face)
+                e1.record(stream)
+                rc, its_u, rr_u = ctx.solve(args.variant, b, x, args.tol, args.maxit, allow_fail=True)
+                e2.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            update[name] = {"update_s": statistics.mean(ts) / 1e3, "solve_iters_after": its_u,
+                            "relres_after": rr_u}
+        update["full_setup_s"] = statistics.mean(setup_ms) / 1e3
+
     # end to end through the C-ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -364,9 +421,13 @@ def ours(args, rank, world, local_rank):
     if rank != 0:
         return
     achieved = sm_bytes / (sm_ms * 1e-3) / 1e9 if sm_ms > 0 else None
+    alg_launch = sm_bytes / max(sm_launch, 1)
+    traffic = (alg_launch * SMOOTHER_CAPTURE["dram_bytes"] / SMOOTHER_CAPTURE["alg_bytes"]
+               if args.precision == "mixed" and sm_launch else None)
     roofline = {"bound": "hbm", "kernel": "fused Chebyshev step, finest level of the S1 hierarchy",
                 "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_source": "ncu capture on the 64^3 three-plane workload, scaled by algorithmic bytes",
                 "launches": sm_launch, "avg_launch_ms": sm_ms / max(sm_launch, 1),
                 "alg_bytes_per_launch": sm_bytes / max(sm_launch, 1)}
     mean_setup = statistics.mean(setup_ms) / 1e3
@@ -386,6 +447,7 @@ def ours(args, rank, world, local_rank):
                       "kernels": detail},
         "fp64": fp64,
         "variants": variants,
+        "update": update,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

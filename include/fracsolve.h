@@ -135,6 +135,23 @@ int fc_create(fc_ctx **ctx, const fc_options *opt, void *cuda_stream);
  * FC_INTERNAL, FC_CUDA_ERROR. */
 int fc_setup(fc_ctx *ctx, const fc_blocks *J);
 
+/* Numeric refresh of the last fc_setup for new block values with exactly the
+ * same sparsity patterns and sizes (the same mesh and contact states: the
+ * next Newton iteration of an active set, or new apertures and pressures
+ * that change T and Q2; the paper's outer loop, Sec. 2, recomputes J while
+ * A, C1, Q1 stay fixed).  H~^-1, S1, S~ / S~2 and the fixed stress are
+ * recomputed as in fc_setup.  Each AMG hierarchy whose level-0 operator
+ * changed is rebuilt numerically on its kept aggregates and patterns: no
+ * strength graph, no aggregation, no symbolic products; D^-1, lambda, the
+ * smoothed prolongator values, R, the Galerkin products, the coarsest
+ * inverse and the cycle data are recomputed.  A hierarchy whose operator is
+ * bitwise unchanged is kept.  The blocks are read, not kept.
+ * Errors: FC_NOT_SETUP before a completed fc_setup; FC_BAD_ARG when a size
+ * or a block's pattern differs (call fc_setup instead); FC_SINGULAR_BLOCK,
+ * FC_OOM, FC_INTERNAL, FC_CUDA_ERROR as fc_setup (the context then needs a
+ * new fc_setup). */
+int fc_update(fc_ctx *ctx, const fc_blocks *J);
+
 /* d_y = J d_x (Eq. JacSys), double, device vectors of length n. */
 int fc_spmv(fc_ctx *ctx, const double *d_x, double *d_y);
 

@@ -24,7 +24,7 @@ FC_M_LEVEL, FC_M_PROLONG, FC_M_S1, FC_M_STILDE, FC_M_S2TILDE = range(5)
 VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP, "tup_star": FC_TUP_STAR}
 
 # exported symbols declared by include/fracsolve.h
-SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_spmv", "fc_residual", "fc_residual_noalloc",
+SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_update", "fc_spmv", "fc_residual", "fc_residual_noalloc",
            "fc_apply_prec", "fc_solve", "fc_spmv_adjoint", "fc_apply_prec_adjoint", "fc_solve_adjoint",
            "fc_vcycle_adjoint", "fc_aperture_gradient",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
@@ -81,6 +81,7 @@ def load(build_if_missing: bool = False):
         "fc_default_options": (None, [C.POINTER(fc_options)]),
         "fc_create": (C.c_int, [C.POINTER(vp), C.POINTER(fc_options), vp]),
         "fc_setup": (C.c_int, [vp, C.POINTER(fc_blocks)]),
+        "fc_update": (C.c_int, [vp, C.POINTER(fc_blocks)]),
         "fc_spmv": (C.c_int, [vp, vp, vp]),
         "fc_residual": (C.c_int, [vp, vp, vp, vp, pd]),
         "fc_residual_noalloc": (C.c_int, [vp, vp, vp, pd]),
@@ -167,9 +168,8 @@ class Context:
             pass
 
     # ------------------------------------------------------------ setup
-    def setup(self, blocks: dict, n_node: int, n_face: int):
-        """blocks: name -> (row_ptr, col_idx, val, n_brows, n_bcols, br, bc) with
-        int32/int32/float64 CUDA tensors."""
+    @staticmethod
+    def _blocks(blocks: dict, n_node: int, n_face: int) -> fc_blocks:
         J = fc_blocks()
         for name in ("A", "C1", "Q1", "C2", "H", "Q2", "T"):
             rp, ci, val, nbr, nbc, br, bc = blocks[name]
@@ -178,8 +178,21 @@ class Context:
             m.nnzb = int(ci.numel())
             m.d_row_ptr, m.d_col_idx, m.d_val = _ptr(rp), _ptr(ci), _ptr(val)
         J.n_node, J.n_face = n_node, n_face
+        return J
+
+    def setup(self, blocks: dict, n_node: int, n_face: int):
+        """blocks: name -> (row_ptr, col_idx, val, n_brows, n_bcols, br, bc) with
+        int32/int32/float64 CUDA tensors."""
+        J = self._blocks(blocks, n_node, n_face)
         self._check(self.lib.fc_setup(self.h, C.byref(J)), self.h)
         self.n = 3 * n_node + 4 * n_face
+        self.n_node, self.n_face = n_node, n_face
+
+    def update(self, blocks: dict, n_node: int, n_face: int):
+        """fc_update: numeric refresh for new values on the patterns of the
+        last setup."""
+        J = self._blocks(blocks, n_node, n_face)
+        self._check(self.lib.fc_update(self.h, C.byref(J)), self.h)
         self.n_node, self.n_face = n_node, n_face
 
     # ------------------------------------------------------------ apply

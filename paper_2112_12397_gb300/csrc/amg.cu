@@ -632,6 +632,35 @@ void build_prolongator(LevelSetup &L, const DBuf<int> &asize, int nc, double ome
   FS_REQUIRE(!hl[0], FC_INTERNAL, "prolongator row exceeds the shared capacity");
 }
 
+// Values of the smoothed prolongator on its existing pattern (the pattern
+// depends only on the pattern of S and the aggregates).
+template <int B>
+void prolongator_values(LevelSetup &L, double omega, cudaStream_t s) {
+  const BsrView<double> S = L.S.view();
+  Bsr<double> &P = L.P;
+  DBuf<int> flag(2);
+  FS_CUDA(cudaMemsetAsync(flag.p, 0, 2 * sizeof(int), s));
+  k_max_len_rows<<<blocks_for(L.nb, 256, kSMs * 4), 256, 0, s>>>(S.rp, L.nb, flag.p + 1);
+  FS_LAUNCHED();
+  int hl[2] = {0, 0};
+  FS_CUDA(cudaMemcpyAsync(hl, flag.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  const int cap = hl[1] > 0 ? hl[1] : 1;
+  FS_REQUIRE(cap <= 4096, FC_INTERNAL, "level operator row longer than 4096 blocks");
+  int wpb = 8;
+  while (wpb > 1 && (size_t)wpb * 3 * cap * sizeof(int) > 96 * 1024) wpb >>= 1;
+  const size_t shm = (size_t)wpb * 3 * cap * sizeof(int);
+  FS_CUDA(cudaFuncSetAttribute(k_prolong<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  if (P.nnzb) {
+    k_prolong<B><<<kSMs * 8, wpb * 32, shm, s>>>(S, L.agg.p, L.asize.p, L.Dinv.p, omega, 1, nullptr, P.rp.p,
+                                                 P.ci.p, P.val.p, cap, flag.p);
+    FS_LAUNCHED();
+  }
+  FS_CUDA(cudaMemcpyAsync(hl, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  FS_REQUIRE(!hl[0], FC_INTERNAL, "prolongator row exceeds the shared capacity");
+}
+
 void invert_coarsest(Hierarchy &H, cudaStream_t s) {
   LevelSetup &L = H.lev.back();
   const int n = L.nb * L.B;
@@ -714,6 +743,39 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
   FS_CUDA(cudaStreamSynchronize(s));
 }
 
+// D^-1 of level l (3x3 or 1x1 block inverses); dn receives the block norms
+// the strength test uses.
+template <int B>
+void level_diag(LevelSetup &L, int l, DBuf<double> &dn, cudaStream_t s) {
+  const int nb = L.nb;
+  L.Dinv.alloc((size_t)nb * B * B);
+  dn.alloc(nb > 0 ? nb : 1);
+  DBuf<int> flag(1);
+  FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+  k_diag<B><<<grid_rows(nb), kT, 0, s>>>(L.S.view(), L.Dinv.p, dn.p, flag.p);
+  FS_LAUNCHED();
+  int hf = 0;
+  FS_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  FS_REQUIRE(!hf, FC_SINGULAR_BLOCK, "singular diagonal block in AMG level " + std::to_string(l));
+}
+
+// power estimate of the largest eigenvalue of D^-1 S on the sliced-ELL copy
+// of S in the cycle precision (the copy is handed to the cycle afterwards)
+template <int B>
+void level_lambda(LevelSetup &L, const AmgParams &p, int l, int precision, cudaStream_t s) {
+  const int nb = L.nb;
+  if (precision == FC_MIXED) {
+    L.Ssf = to_sell<float>(L.S.view(), s);
+    L.Dinvf.alloc((size_t)nb * B * B);
+    cast(L.Dinvf.p, L.Dinv.p, (int64_t)nb * B * B, s);
+    L.lam = power_lambda<B, float>(L.Ssf.view(), L.Dinvf.p, p.seed, l, p.power_steps, s);
+  } else {
+    L.Ssd = to_sell<double>(L.S.view(), s);
+    L.lam = power_lambda<B, double>(L.Ssd.view(), L.Dinv.p, p.seed, l, p.power_steps, s);
+  }
+}
+
 template <int B>
 void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s) {
   const AmgParams &p = H.prm;
@@ -728,47 +790,31 @@ void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s)
     const int nb = L.nb;
     if (p.verbose) fprintf(stderr, "[fracsolve] AMG(B=%d) level %d: %d block rows, %lld blocks\n", B, l, nb, (long long)L.S.nnzb);
     if (nb <= p.coarse_max || l + 1 >= p.max_levels) break;
-    // diagonal blocks
-    L.Dinv.alloc((size_t)nb * B * B);
-    DBuf<double> dn(nb);
-    DBuf<int> flag(1);
-    FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
-    k_diag<B><<<grid_rows(nb), kT, 0, s>>>(L.S.view(), L.Dinv.p, dn.p, flag.p);
-    FS_LAUNCHED();
-    int hf = 0;
-    FS_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FS_CUDA(cudaStreamSynchronize(s));
-    FS_REQUIRE(!hf, FC_SINGULAR_BLOCK, "singular diagonal block in AMG level " + std::to_string(l));
+    DBuf<double> dn;
+    level_diag<B>(L, l, dn, s);
     pt.mark("diag");
     // strength graph and aggregates
     const double theta = p.theta0 * std::pow(p.theta_decay, l);
     Graph G = strength_graph(L.S.view(), dn.p, theta, s);
     pt.mark("strength");
-    DBuf<int> asize;
-    int nc = aggregate(G, p.seed, l, L.agg, asize, p.verbose, s);
+    int nc = aggregate(G, p.seed, l, L.agg, L.asize, p.verbose, s);
     pt.mark("aggregate");
     if (nc == 0 || nc > p.max_ratio * nb) {
       L.Dinv.release();
       L.agg.release();
+      L.asize.release();
       break;
     }
-    if (precision == FC_MIXED) {
-      L.Ssf = to_sell<float>(L.S.view(), s);
-      L.Dinvf.alloc((size_t)nb * B * B);
-      cast(L.Dinvf.p, L.Dinv.p, (int64_t)nb * B * B, s);
-      L.lam = power_lambda<B, float>(L.Ssf.view(), L.Dinvf.p, p.seed, l, p.power_steps, s);
-    } else {
-      L.Ssd = to_sell<double>(L.S.view(), s);
-      L.lam = power_lambda<B, double>(L.Ssd.view(), L.Dinv.p, p.seed, l, p.power_steps, s);
-    }
+    L.nc = nc;
+    level_lambda<B>(L, p, l, precision, s);
     pt.mark("power");
-    build_prolongator<B>(L, asize, nc, p.omega_num / L.lam, s);
+    build_prolongator<B>(L, L.asize, nc, p.omega_num / L.lam, s);
     pt.mark("prolongator");
     L.R = transpose(L.P.view(), s);
     pt.mark("transpose");
-    Bsr<double> SP = spgemm(L.S.view(), L.P.view(), s);
+    L.SP = spgemm(L.S.view(), L.P.view(), s);
     pt.mark("spgemm S P");
-    Bsr<double> Sc = spgemm(L.R.view(), SP.view(), s);
+    Bsr<double> Sc = spgemm(L.R.view(), L.SP.view(), s);
     pt.mark("spgemm R (S P)");
     LevelSetup next;
     next.B = B;
@@ -786,7 +832,53 @@ void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s)
   H.built = true;
 }
 
+// Numeric rebuild on new values of the level-0 operator with the same
+// pattern: aggregates, tentative prolongators and every sparsity pattern of
+// the hierarchy are kept; D^-1, lambda, the smoothed prolongator values, R,
+// the Galerkin products (numeric pass only), the coarsest inverse and the
+// cycle data are recomputed.
+template <int B>
+void refresh_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s) {
+  const AmgParams &p = H.prm;
+  H.built = false;
+  H.lev[0].S = std::move(S0);
+  PhaseTimer pt(p.verbose > 0, s, B == 3 ? "amg3 refresh" : "amg1 refresh");
+  const int nl = (int)H.lev.size();
+  for (int l = 0; l + 1 < nl; l++) {
+    LevelSetup &L = H.lev[l];
+    DBuf<double> dn;
+    level_diag<B>(L, l, dn, s);
+    level_lambda<B>(L, p, l, precision, s);
+    pt.mark("diag + power");
+    prolongator_values<B>(L, p.omega_num / L.lam, s);
+    L.R = transpose(L.P.view(), s);
+    pt.mark("prolongator + transpose");
+    spgemm_numeric(L.S.view(), L.P.view(), L.SP, s);
+    spgemm_numeric(L.R.view(), L.SP.view(), H.lev[l + 1].S, s);
+    pt.mark("spgemm numeric");
+  }
+  invert_coarsest(H, s);
+  if (precision == FC_MIXED) prepare_cycle<float>(H, H.cf, s);
+  else prepare_cycle<double>(H, H.cd, s);
+  pt.mark("coarsest + cycle data");
+  H.built = true;
+}
+
 }  // namespace
+
+void amg_refresh(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s) {
+  FS_REQUIRE(H.built && !H.lev.empty(), FC_NOT_SETUP, "AMG hierarchy not built");
+  const Bsr<double> &S = H.lev[0].S;
+  FS_REQUIRE(S0.nbr == S.nbr && S0.nnzb == S.nnzb && S0.br == S.br, FC_BAD_ARG,
+             "AMG refresh: the operator's pattern differs from the one the hierarchy was built on");
+  FS_REQUIRE(same_pattern(S0.view(), S.view(), s), FC_BAD_ARG,
+             "AMG refresh: the operator's pattern differs from the one the hierarchy was built on");
+  for (auto &row : H.coarse)
+    for (auto &g : row) g.reset();
+  H.have_t = false;
+  if (H.B == 3) refresh_levels<3>(H, std::move(S0), precision, s);
+  else refresh_levels<1>(H, std::move(S0), precision, s);
+}
 
 void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int precision,
                cudaStream_t s) {

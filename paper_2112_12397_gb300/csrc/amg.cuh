@@ -29,6 +29,9 @@ struct LevelSetup {
   Bsr<double> P, R;     // prolongator (nb x nc blocks) and R = P^T (not on the coarsest)
   DBuf<double> Dinv;    // nb * B * B inverse diagonal blocks
   DBuf<int> agg;        // aggregate of each block row (-1: none)
+  DBuf<int> asize;      // size of each aggregate
+  int nc = 0;           // number of aggregates (coarse block rows)
+  Bsr<double> SP;       // S P, kept for numeric rebuilds
   double lam = 0.0;     // power estimate of the largest eigenvalue of D^-1 S
   // sliced-ELL operator and D^-1 in the cycle precision, built during setup
   // (the power iteration runs on them) and handed to the cycle
@@ -113,6 +116,11 @@ struct Hierarchy {
 // ownership of S0.  precision: FC_FP64 or FC_MIXED (casts the cycle data).
 void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int precision,
                cudaStream_t s);
+
+// Numeric rebuild of a built hierarchy for new values of its level-0
+// operator with the same pattern (aggregates and all patterns kept).
+// Takes ownership of S0; FC_BAD_ARG if the pattern differs.
+void amg_refresh(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s);
 
 // x = V-cycle(f) with zero initial guess; f and x have nb(0) * B entries.
 template <typename TP>

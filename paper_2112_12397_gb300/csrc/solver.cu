@@ -253,6 +253,7 @@ struct fc_ctx {
   DBuf<float> Zf;
   DBuf<double> Zd;
   DBuf<double> xk, rk, bk, hb, hx;
+  DBuf<double> zd;   // a float direction widened to double for J z / J^T z
   double *stat_host = nullptr;   // pinned
   Profiler prof;
   ~fc_ctx() {
@@ -392,7 +393,18 @@ void jac_spmv(fc_ctx &c, const TX *z, double *y) {
                        bsr_bytes<double>(c.C2) + bsr_bytes<double>(c.H) + bsr_bytes<double>(c.Q2) +
                        bsr_bytes<double>(c.T) + (double)c.n * (sizeof(TX) + sizeof(double));
   c.prof.start(PK_JAC, s);
-  const TX *z_u = z, *z_t = z + c.nu, *z_p = z + c.nu + c.nt;
+  // a float direction (mixed mode) is widened once: the products then run
+  // entirely in FP64 FMAs, without a float-to-double conversion per block
+  // (those occupy the same FP64 pipe as the FMAs)
+  const double *zz;
+  if constexpr (std::is_same<TX, float>::value) {
+    c.zd.ensure(c.n);
+    cast(c.zd.p, z, c.n, s);
+    zz = c.zd.p;
+  } else {
+    zz = z;
+  }
+  const double *z_u = zz, *z_t = zz + c.nu, *z_p = zz + c.nu + c.nt;
   double *y_u = y, *y_t = y + c.nu, *y_p = y + c.nu + c.nt;
   sell_axpby<3, 3>(c.sA.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
   if (c.nf) {
@@ -411,7 +423,15 @@ void jac_spmv(fc_ctx &c, const TX *z, double *y) {
 template <typename TX>
 void jac_spmv_t(fc_ctx &c, const TX *z, double *y) {
   cudaStream_t s = c.s;
-  const TX *z_u = z, *z_t = z + c.nu, *z_p = z + c.nu + c.nt;
+  const double *zz;
+  if constexpr (std::is_same<TX, float>::value) {
+    c.zd.ensure(c.n);
+    cast(c.zd.p, z, c.n, s);
+    zz = c.zd.p;
+  } else {
+    zz = z;
+  }
+  const double *z_u = zz, *z_t = zz + c.nu, *z_p = zz + c.nu + c.nt;
   double *y_u = y, *y_t = y + c.nu, *y_p = y + c.nu + c.nt;
   sell_axpby<3, 3>(c.tA.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
   if (c.nf) {
@@ -905,6 +925,79 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     if (prec == FC_MIXED) prepare_prec<float>(*c, c->pf);
     else prepare_prec<double>(*c, c->pd);
     c->xk.alloc(c->n); c->rk.alloc(c->n);
+    pt.mark("prec data");
+    FS_CUDA(cudaStreamSynchronize(s));
+    c->ready = true;
+    return FC_OK;
+  });
+}
+
+int fc_update(fc_ctx *c, const fc_blocks *J) {
+  if (!c || !J) return FC_BAD_ARG;
+  return run(c, [&]() {
+    FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_update needs a completed fc_setup");
+    const int nn = c->nn, nf = c->nf;
+    FS_REQUIRE(J->n_node == nn && J->n_face == nf, FC_BAD_ARG, "fc_update: sizes differ from the last fc_setup");
+    check_bsr(J->A, nn, nn, 3, 3, "A");
+    check_bsr(J->C1, nn, nf, 3, 3, "C1");
+    check_bsr(J->Q1, nn, nf, 3, 1, "Q1");
+    check_bsr(J->C2, nf, nn, 3, 3, "C2");
+    check_bsr(J->H, nf, nf, 3, 3, "H");
+    check_bsr(J->Q2, nf, nn, 1, 3, "Q2");
+    check_bsr(J->T, nf, nf, 1, 1, "T");
+    cudaStream_t s = c->s;
+    fs::g_verbose = c->opt.verbose;
+    PhaseTimer pt(c->opt.verbose > 0, s, "update");
+    const fc_bsr *in[7] = {&J->A, &J->C1, &J->Q1, &J->C2, &J->H, &J->Q2, &J->T};
+    Bsr<double> *own[7] = {&c->A, &c->C1, &c->Q1, &c->C2, &c->H, &c->Q2, &c->T};
+    const char *names[7] = {"A", "C1", "Q1", "C2", "H", "Q2", "T"};
+    bool changed[7];
+    for (int k = 0; k < 7; k++) {
+      BsrView<double> v;
+      v.nbr = in[k]->n_brows; v.nbc = in[k]->n_bcols; v.br = in[k]->br; v.bc = in[k]->bc;
+      v.nnzb = in[k]->nnzb; v.rp = in[k]->d_row_ptr; v.ci = in[k]->d_col_idx; v.val = in[k]->d_val;
+      FS_REQUIRE(same_pattern(v, own[k]->view(), s), FC_BAD_ARG,
+                 std::string("fc_update: the pattern of block ") + names[k] + " differs from the last fc_setup");
+      const int64_t nv = v.nnzb * v.br * v.bc;
+      changed[k] = !same_values(v.val, own[k]->val.p, nv, s);
+    }
+    c->ready = false;
+    for (int k = 0; k < 7; k++) {
+      const int64_t nv = own[k]->nnzb * own[k]->br * own[k]->bc;
+      if (changed[k] && nv)
+        FS_CUDA(cudaMemcpyAsync(own[k]->val.p, in[k]->d_val, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+    }
+    c->sA = to_sell<double>(c->A.view(), s); c->sC1 = to_sell<double>(c->C1.view(), s);
+    c->sQ1 = to_sell<double>(c->Q1.view(), s); c->sC2 = to_sell<double>(c->C2.view(), s);
+    c->sH = to_sell<double>(c->H.view(), s); c->sQ2 = to_sell<double>(c->Q2.view(), s);
+    c->sT = to_sell<double>(c->T.view(), s);
+    c->have_adj = false;
+    pt.mark("pattern check + values");
+    build_hinv(c->H.view(), c->Hinv64, s);
+    Bsr<double> S1 = build_s1(c->A.view(), c->C1.view(), c->C2.view(), c->Hinv64.p, s);
+    const bool s1_same = same_values(S1.val.p, c->S1.val.p, S1.nnzb * 9, s) && S1.nnzb == c->S1.nnzb;
+    c->S1 = std::move(S1);
+    pt.mark("S1");
+    const int prec = c->opt.precision;
+    if (c->have[FC_TPU]) {
+      Bsr<double> St = build_stilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), s);
+      const bool st_same = St.nnzb == c->St.nnzb && same_values(St.val.p, c->St.val.p, St.nnzb * 9, s);
+      c->St = std::move(St);
+      if (!st_same) amg_refresh(c->hier[FC_H_TPU_U], copy_cast<double, double>(c->St.view(), s), prec, s);
+      if (nf && changed[6]) amg_refresh(c->hier[FC_H_TPU_P], copy_cast<double, double>(c->T.view(), s), prec, s);
+    }
+    if (c->have[FC_TUP]) {
+      Bsr<double> S2 = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s);
+      const bool s2_same = S2.nnzb == c->S2t.nnzb && same_values(S2.val.p, c->S2t.val.p, S2.nnzb, s);
+      c->S2t = std::move(S2);
+      if (!s1_same) amg_refresh(c->hier[FC_H_TUP_U], copy_cast<double, double>(c->S1.view(), s), prec, s);
+      if (nf && !s2_same) amg_refresh(c->hier[FC_H_TUP_P], copy_cast<double, double>(c->S2t.view(), s), prec, s);
+    }
+    pt.mark("hierarchies");
+    c->pf = PrecData<float>();
+    c->pd = PrecData<double>();
+    if (prec == FC_MIXED) prepare_prec<float>(*c, c->pf);
+    else prepare_prec<double>(*c, c->pd);
     pt.mark("prec data");
     FS_CUDA(cudaStreamSynchronize(s));
     c->ready = true;

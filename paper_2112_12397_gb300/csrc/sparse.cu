@@ -167,22 +167,76 @@ __device__ inline bool hash_insert(WarpHash &h, int key) {
   return false;
 }
 
-// pass 0: count unique columns per row; pass 1: write sorted columns
+// Prefix of the B-row lengths over the row of A (a0, na): pre[x] = products
+// of entries 0..x-1, pre[na] = T (returned to every lane).
+__device__ inline int row_product_prefix(const BsrView<double> &A, const BsrView<double> &B, int a0, int na,
+                                         int *pre, int lane) {
+  int run = 0;
+  for (int x0 = 0; x0 < na; x0 += 32) {
+    const int x = x0 + lane;
+    int len = 0;
+    if (x < na) {
+      const int k = A.ci[a0 + x];
+      len = B.rp[k + 1] - B.rp[k];
+    }
+    int inc = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (x < na) pre[x + 1] = run + inc;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (lane == 0) pre[0] = 0;
+  __syncwarp();
+  return run;
+}
+
+// Product t of the row (enumeration order: entries of A's row, then the
+// entries of the matching B row): the A entry offset x with pre[x] <= t < pre[x+1].
+__device__ inline int product_entry(const int *pre, int na, int t) {
+  int lo = 0, hi = na - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kSymPre = 512;   // A-row entries the flattened symbolic pass takes
+
+// pass 0: count unique columns per row; pass 1: write sorted columns.  The
+// products of a row are enumerated flat (all lanes busy even when the rows
+// of B are short); rows of A longer than kSymPre take the entry-by-entry loop.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_spgemm_symbolic(BsrView<double> A, BsrView<double> B, int pass, int *cnt, const int *rpC,
                       int *ciC, int *overflow) {
   __shared__ int s_keys[kWarpsPerBlock][kHashCap];
   __shared__ int s_list[kWarpsPerBlock][kListCap];
+  __shared__ int s_pre[kWarpsPerBlock][kSymPre + 1];
   __shared__ int s_cnt[kWarpsPerBlock];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   WarpHash h{s_keys[wid], s_list[wid], &s_cnt[wid]};
+  int *pre = s_pre[wid];
   const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
   for (int64_t i = blockIdx.x * (int64_t)kWarpsPerBlock + wid; i < A.nbr; i += nwarps) {
     hash_clear(h, lane);
     bool ok = true;
-    for (int e = A.rp[i]; e < A.rp[i + 1]; e++) {
-      int k = A.ci[e];
-      for (int f = B.rp[k] + lane; f < B.rp[k + 1]; f += 32) ok &= hash_insert(h, B.ci[f]);
+    const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
+    if (na <= kSymPre) {
+      const int T = row_product_prefix(A, B, a0, na, pre, lane);
+      for (int t = lane; t < T; t += 32) {
+        const int x = product_entry(pre, na, t);
+        const int k = A.ci[a0 + x];
+        ok &= hash_insert(h, B.ci[B.rp[k] + (t - pre[x])]);
+      }
+    } else {
+      for (int e = a0; e < a0 + na; e++) {
+        int k = A.ci[e];
+        for (int f = B.rp[k] + lane; f < B.rp[k + 1]; f += 32) ok &= hash_insert(h, B.ci[f]);
+      }
     }
     __syncwarp();
     ok = __all_sync(0xffffffffu, ok);
@@ -207,6 +261,143 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
+// Numeric pass with the products of a row sorted by output slot.  One warp
+// per row of C; every lane owns the units u = lane + 32 k (k < KU) of the
+// row, unit = (slot p, block row r), and sums them in registers.  The
+// products (e, f) of the row (entries of A's row, then of B's matching row)
+// are taken in their fixed enumeration order, in segments of capT: each
+// product gets its slot (the position of B's column among C's sorted
+// columns), a stable counting sort groups the segment by slot, and each lane
+// adds the segment's products of its units in order.  Every entry of C is
+// the same ordered sum on every run (no atomics on values), all lanes work
+// even when B's rows hold a handful of blocks, and the shared memory per
+// warp is independent of the row's product count.  Rows with more than
+// 32 KU units or longer A rows than capA stay pending for the chunked kernel.
+template <int BR, int BK, int BC, int KU>
+__global__ void __launch_bounds__(256)
+    k_spgemm_numeric_seg(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC, double *valC,
+                         int *pending, int capA, int capT, int *bad) {
+  constexpr int BS = BR * BC;
+  constexpr int capC = (32 * KU) / BR;
+  extern __shared__ int ismem[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  const int per = 3 * capC + 1 + capA + 1 + 4 * capT;
+  int *cols = ismem + (size_t)wid * per;
+  int *start = cols + capC;       // capC + 1: counts, then slot offsets
+  int *off = start + capC + 1;    // capC: placed so far per slot
+  int *pre = off + capC;          // capA + 1
+  int *pl = pre + capA + 1;       // capT: slot of segment product
+  int *ee = pl + capT;            // capT: its A entry
+  int *ff = ee + capT;            // capT: its B entry
+  int *srt = ff + capT;           // capT: segment products sorted by slot
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  for (int64_t i = blockIdx.x * (int64_t)wpb + wid; i < A.nbr; i += nwarps) {
+    if (!pending[i]) continue;
+    const int cs = rpC[i], cn = rpC[i + 1] - cs;
+    const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
+    if (cn > capC || na > capA) continue;
+    const int T = row_product_prefix(A, B, a0, na, pre, lane);
+    for (int t = lane; t < cn; t += 32) cols[t] = ciC[cs + t];
+    double acc[KU][BC];
+#pragma unroll
+    for (int k = 0; k < KU; k++)
+#pragma unroll
+      for (int cc = 0; cc < BC; cc++) acc[k][cc] = 0.0;
+    bool okp = true;
+    for (int t0 = 0; t0 < T; t0 += capT) {
+      const int tn = min(capT, T - t0);
+      for (int t = lane; t < cn; t += 32) {
+        start[t] = 0;
+        off[t] = 0;
+      }
+      __syncwarp();
+      for (int tl = lane; tl < tn; tl += 32) {
+        const int t = t0 + tl;
+        const int x = product_entry(pre, na, t);
+        const int e = a0 + x;
+        const int f = B.rp[A.ci[e]] + (t - pre[x]);
+        int p = find_sorted(cols, cn, B.ci[f]);
+        if (p < 0) { okp = false; p = 0; }   // cannot happen: the symbolic pass saw every column
+        ee[tl] = e;
+        ff[tl] = f;
+        pl[tl] = p;
+        atomicAdd(&start[p], 1);
+      }
+      __syncwarp();
+      int run = 0;
+      for (int x0 = 0; x0 < cn; x0 += 32) {
+        const int x = x0 + lane;
+        const int c = x < cn ? start[x] : 0;
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        if (x < cn) start[x] = run + inc - c;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) start[cn] = run;
+      __syncwarp();
+      for (int c0 = 0; c0 < tn; c0 += 32) {
+        const int tl = c0 + lane;
+        const bool act = tl < tn;
+        const unsigned am = __ballot_sync(0xffffffffu, act);
+        int p = 0, o = 0;
+        unsigned m = 0;
+        if (act) {
+          p = pl[tl];
+          m = __match_any_sync(am, p);
+          o = off[p];
+          srt[start[p] + o + __popc(m & lt)] = tl;
+        }
+        __syncwarp();
+        if (act && (m & lt) == 0) off[p] = o + __popc(m);
+        __syncwarp();
+      }
+#pragma unroll
+      for (int k = 0; k < KU; k++) {
+        const int u = lane + 32 * k;
+        if (u < cn * BR) {
+          const int p = u / BR, r = u - p * BR;
+          const int q1 = start[p + 1];
+#pragma unroll 2
+          for (int q = start[p]; q < q1; q++) {
+            const int tl = srt[q];
+            const double *a = A.val + (int64_t)ee[tl] * BR * BK + r * BK;
+            const double *b = B.val + (int64_t)ff[tl] * BK * BC;
+            double av[BK];
+#pragma unroll
+            for (int tt = 0; tt < BK; tt++) av[tt] = a[tt];
+            // straight FMA accumulation: the FP64 pipe bounds this kernel
+#pragma unroll
+            for (int cc = 0; cc < BC; cc++)
+#pragma unroll
+              for (int tt = 0; tt < BK; tt++) acc[k][cc] = fma(av[tt], b[tt * BC + cc], acc[k][cc]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (!__all_sync(0xffffffffu, okp)) {
+      if (lane == 0) atomicExch(bad, 1);
+      continue;
+    }
+#pragma unroll
+    for (int k = 0; k < KU; k++) {
+      const int u = lane + 32 * k;
+      if (u < cn * BR) {
+        const int p = u / BR, r = u - p * BR;
+#pragma unroll
+        for (int cc = 0; cc < BC; cc++) valC[(int64_t)(cs + p) * BS + r * BC + cc] = acc[k][cc];
+      }
+    }
+    __syncwarp();
+    if (lane == 0) pending[i] = 0;
+  }
+}
+
 // Numeric pass, one warp per row of C, FP64 work spread over all lanes.
 // The row's sorted columns and accumulators live in shared memory.  The
 // products (e, f) of the row (e: entry k of A's row, f: entry j of B's row
@@ -219,7 +410,7 @@ constexpr int kProdChunk = 128;
 
 template <int BR, int BK, int BC>
 __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC,
-                                    double *valC, int ulo, int ucap) {
+                                    double *valC, const int *pending, int ulo, int ucap) {
   constexpr int BS = BR * BC;
   extern __shared__ double smem[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -233,8 +424,9 @@ __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const 
   int *list = ch_p + kProdChunk;              // kProdChunk * BR unit-product slots
   const int64_t nwarps = (int64_t)gridDim.x * wpb;
   for (int64_t i = blockIdx.x * (int64_t)wpb + wid; i < A.nbr; i += nwarps) {
+    if (!pending[i]) continue;              // done by the sorted-product kernel
     const int cs = rpC[i], cn = rpC[i + 1] - cs;
-    if (cn <= ulo || cn > ucap) continue;   // another tier (or the global kernel)
+    if (cn <= ulo || cn > ucap) continue;   // another tier
     for (int t = lane; t < cn; t += 32) cols[t] = ciC[cs + t];
     for (int t = lane; t < cn * BS; t += 32) acc[t] = 0.0;
     __syncwarp();
@@ -279,10 +471,10 @@ __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const 
           for (int tt = 0; tt < BK; tt++) av[tt] = a[tt];
 #pragma unroll
           for (int cc = 0; cc < BC; cc++) {
-            double sum = 0;
+            double v = c[cc];
 #pragma unroll
-            for (int tt = 0; tt < BK; tt++) sum += av[tt] * b[tt * BC + cc];
-            c[cc] += sum;
+            for (int tt = 0; tt < BK; tt++) v = fma(av[tt], b[tt * BC + cc], v);
+            c[cc] = v;
           }
         }
       }
@@ -311,46 +503,131 @@ __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const 
   }
 }
 
-__global__ void k_max_row_len(const int *rp, int n, int *out) {
+__global__ void k_max_pending_len(const int *rp, int n, const int *pending, int *out) {
   int m = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    m = max(m, rp[i + 1] - rp[i]);
+    if (pending[i]) m = max(m, rp[i + 1] - rp[i]);
   atomicMax(out, m);
+}
+
+template <int BR, int BK, int BC, int KU>
+void launch_seg(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, int *pending, int *flags,
+                cudaStream_t s) {
+  const int capA = 512, capT = 192, wpb = 8;
+  constexpr int capC = (32 * KU) / BR;
+  const size_t shm = (size_t)wpb * (3 * capC + 1 + capA + 1 + 4 * capT) * sizeof(int);
+  auto kern = k_spgemm_numeric_seg<BR, BK, BC, KU>;
+  FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  kern<<<kSMs * 8, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, pending, capA, capT, flags);
+  FS_LAUNCHED();
 }
 
 template <int BR, int BK, int BC>
 void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s) {
   constexpr int BS = BR * BC;
-  DBuf<int> mx(1);
-  FS_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
-  k_max_row_len<<<blocks_for(C.nbr, 256, kSMs * 4), 256, 0, s>>>(C.rp.p, C.nbr, mx.p);
+  if (C.nbr == 0) return;
+  DBuf<int> pending(C.nbr), flags(2);
+  FS_CUDA(cudaMemsetAsync(pending.p, 1, sizeof(int) * C.nbr, s));   // nonzero = pending
+  FS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
+  // segmented sorted-product kernel in two tiers of units per lane (KU = 4
+  // keeps the register accumulators small for the common short rows; KU = 9
+  // takes C rows up to 96 block columns): A-row entries capA, products per
+  // segment capT, 8 warps per block
+  launch_seg<BR, BK, BC, 4>(A, B, C, pending.p, flags.p, s);
+  launch_seg<BR, BK, BC, 9>(A, B, C, pending.p, flags.p, s);
+  // rows beyond the tiers (very long rows of A or many products): longest C row among them
+  k_max_pending_len<<<blocks_for(C.nbr, 256, kSMs * 4), 256, 0, s>>>(C.rp.p, C.nbr, pending.p, flags.p + 1);
   FS_LAUNCHED();
-  int umax = 0;
-  FS_CUDA(cudaMemcpyAsync(&umax, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int hf[2] = {0, 0};
+  FS_CUDA(cudaMemcpyAsync(hf, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   FS_CUDA(cudaStreamSynchronize(s));
-  // rows are processed in tiers of increasing length so that the shared
-  // accumulators of short rows do not limit the occupancy: per warp, ucap
-  // slots (accumulator + column) and the product chunk
+  FS_REQUIRE(!hf[0], FC_INTERNAL, "spgemm: a product column is missing from the symbolic pattern");
+  const int umax = hf[1];
+  if (umax == 0) return;
+  // the chunked kernel, in tiers of C-row length so that short rows run at
+  // higher occupancy: per warp, ucap slots (accumulator + column) and the
+  // product chunk
   const size_t per_slot = BS * sizeof(double) + sizeof(int);
   const size_t fixed = (size_t)4 * kProdChunk * BR * sizeof(int);
-  const int tiers[3] = {64, 256, kListCap};
+  const int ctiers[3] = {64, 256, kListCap};
   FS_REQUIRE(umax <= kListCap, FC_INTERNAL, "spgemm: product row longer than the symbolic pass allows");
-  int ulo = 0, ucap = 0;
+  int ulo = 0;
   for (int t = 0; t < 3 && ulo < umax; t++) {
-    ucap = tiers[t];
+    const int ucap = ctiers[t];
     int wpb = 8;
     while (wpb > 1 && (size_t)wpb * (ucap * per_slot + fixed) > 200 * 1024) wpb >>= 1;
     const size_t shm = (size_t)wpb * (ucap * per_slot + fixed);
     auto kern = k_spgemm_numeric_sh<BR, BK, BC>;
     FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    kern<<<kSMs * 8, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, ulo, ucap);
+    kern<<<kSMs * 8, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, pending.p, ulo, ucap);
     FS_LAUNCHED();
     ulo = ucap;
   }
 }
 
 }  // namespace
+
+void spgemm_numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s) {
+  FS_REQUIRE(A.bc == B.br && A.nbc == B.nbr && C.nbr == A.nbr && C.nbc == B.nbc && C.br == A.br && C.bc == B.bc,
+             FC_BAD_ARG, "spgemm_numeric: shape mismatch");
+  if (C.nnzb == 0) return;
+  const int sh = A.br * 100 + A.bc * 10 + B.bc;
+  switch (sh) {
+    case 333: numeric<3, 3, 3>(A, B, C, s); break;
+    case 313: numeric<3, 1, 3>(A, B, C, s); break;
+    case 111: numeric<1, 1, 1>(A, B, C, s); break;
+    case 331: numeric<3, 3, 1>(A, B, C, s); break;
+    case 133: numeric<1, 3, 3>(A, B, C, s); break;
+    default: throw Error(FC_BAD_ARG, "spgemm: unsupported block shapes");
+  }
+}
+
+namespace {
+__global__ void k_diff_int(const int *a, const int *b, int64_t n, int *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] != b[i]) {
+      atomicExch(out, 1);
+      return;
+    }
+}
+__global__ void k_diff_bits(const unsigned long long *a, const unsigned long long *b, int64_t n, int *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] != b[i]) {
+      atomicExch(out, 1);
+      return;
+    }
+}
+}  // namespace
+
+bool same_values(const double *a, const double *b, int64_t n, cudaStream_t s) {
+  if (n <= 0) return true;
+  DBuf<int> d(1);
+  FS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(int), s));
+  k_diff_bits<<<blocks_for(n, 256, kSMs * 8), 256, 0, s>>>(reinterpret_cast<const unsigned long long *>(a),
+                                                           reinterpret_cast<const unsigned long long *>(b), n, d.p);
+  FS_LAUNCHED();
+  int h = 0;
+  FS_CUDA(cudaMemcpyAsync(&h, d.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  return h == 0;
+}
+
+bool same_pattern(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s) {
+  if (A.nbr != B.nbr || A.nbc != B.nbc || A.br != B.br || A.bc != B.bc || A.nnzb != B.nnzb) return false;
+  DBuf<int> d(1);
+  FS_CUDA(cudaMemsetAsync(d.p, 0, sizeof(int), s));
+  k_diff_int<<<blocks_for((int64_t)A.nbr + 1, 256, kSMs * 8), 256, 0, s>>>(A.rp, B.rp, (int64_t)A.nbr + 1, d.p);
+  FS_LAUNCHED();
+  if (A.nnzb) {
+    k_diff_int<<<blocks_for(A.nnzb, 256, kSMs * 8), 256, 0, s>>>(A.ci, B.ci, A.nnzb, d.p);
+    FS_LAUNCHED();
+  }
+  int h = 0;
+  FS_CUDA(cudaMemcpyAsync(&h, d.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  return h == 0;
+}
 
 Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s) {
   FS_REQUIRE(A.bc == B.br && A.nbc == B.nbr, FC_BAD_ARG, "spgemm: shape mismatch");

@@ -27,6 +27,16 @@ Bsr<double> transpose(const BsrView<double> &A, cudaStream_t s);
 // Rows of C sorted; entries that cancel to zero are kept.
 Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s);
 
+// Numeric pass only: C (whose pattern is that of A B, e.g. from an earlier
+// spgemm of the same patterns) receives the values of A B.
+void spgemm_numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s);
+
+// True when the n doubles at a and b are bitwise identical (device arrays).
+bool same_values(const double *a, const double *b, int64_t n, cudaStream_t s);
+
+// True when A and B have identical row pointers and column indices.
+bool same_pattern(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s);
+
 // C = alpha A + beta B (same shape and block size), rows sorted.
 Bsr<double> spadd(const BsrView<double> &A, const BsrView<double> &B, double alpha, double beta,
                   cudaStream_t s);
