@@ -35,7 +35,10 @@ inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
 
 // levels whose rows hold more blocks than this on average use the
 // lane-group BSR kernel instead of sliced ELL (coarse levels)
-constexpr double kSellMaxMeanRow = 40.0;
+#ifndef FS_SELL_MAX_MEAN_ROW
+#define FS_SELL_MAX_MEAN_ROW 40.0
+#endif
+constexpr double kSellMaxMeanRow = FS_SELL_MAX_MEAN_ROW;
 
 __device__ inline double frob2(const double *v, int bs) {
   double s = 0.0;

@@ -261,44 +261,59 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
-// Numeric pass with the products of a row sorted by output slot.  One warp
-// per row of C; every lane owns the units u = lane + 32 k (k < KU) of the
-// row, unit = (slot p, block row r), and sums them in registers.  The
-// products (e, f) of the row (entries of A's row, then of B's matching row)
-// are taken in their fixed enumeration order, in segments of capT: each
-// product gets its slot (the position of B's column among C's sorted
-// columns), a stable counting sort groups the segment by slot, and each lane
-// adds the segment's products of its units in order.  Every entry of C is
-// the same ordered sum on every run (no atomics on values), all lanes work
-// even when B's rows hold a handful of blocks, and the shared memory per
-// warp is independent of the row's product count.  Rows with more than
-// 32 KU units or longer A rows than capA stay pending for the chunked kernel.
-template <int BR, int BK, int BC, int KU>
+// Numeric pass with the products of a row sorted by output slot.  A group
+// of W warps takes one row of C; warp w of the group owns the slots
+// [w ceil(cn / W), (w + 1) ceil(cn / W)) and, in it, lane l the units
+// u = l + 32 k (k < KU), unit = (slot p, block row r), summed in registers.
+// The products (e, f) of the row (entries of A's row, then of B's matching
+// row) are taken in their fixed enumeration order, in segments of capT:
+// each product gets its slot (the position of B's column among C's sorted
+// columns), products outside the warp's slots are dropped, a stable counting
+// sort groups the rest by slot, and each lane adds the segment's products of
+// its units in order.  Every entry of C is the same ordered sum on every run
+// (no atomics on values), all lanes work even when B's rows hold a handful
+// of blocks, and the shared memory per warp does not grow with the row's
+// product count.  W > 1 splits long rows of C over a whole block (one group
+// per block).  Rows with more slots than W warps hold or longer A rows than
+// capA stay pending for the chunked kernel.
+template <int BR, int BK, int BC, int KU, int W>
 __global__ void __launch_bounds__(256)
     k_spgemm_numeric_seg(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC, double *valC,
                          int *pending, int capA, int capT, int *bad) {
   constexpr int BS = BR * BC;
-  constexpr int capC = (32 * KU) / BR;
+  constexpr int capC = (32 * KU) / BR;      // slots per warp
+  constexpr int capR = capC * W;            // slots per row
   extern __shared__ int ismem[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  const int per = 3 * capC + 1 + capA + 1 + 4 * capT;
-  int *cols = ismem + (size_t)wid * per;
-  int *start = cols + capC;       // capC + 1: counts, then slot offsets
-  int *off = start + capC + 1;    // capC: placed so far per slot
-  int *pre = off + capC;          // capA + 1
-  int *pl = pre + capA + 1;       // capT: slot of segment product
+  const int G = wpb / W;                    // row groups per block (1 when W > 1)
+  const int g = wid / W, wr = wid - g * W;
+  // per group: cols (capR), pre (capA + 1); per warp: start, off, products
+  const int per_group = capR + capA + 1;
+  const int per_warp = 2 * capC + 1 + 4 * capT;
+  int *cols = ismem + (size_t)g * per_group;
+  int *pre = cols + capR;
+  int *start = ismem + (size_t)G * per_group + (size_t)wid * per_warp;   // capC + 1
+  int *off = start + capC + 1;    // capC
+  int *pl = off + capC;           // capT: local slot of a kept segment product
   int *ee = pl + capT;            // capT: its A entry
   int *ff = ee + capT;            // capT: its B entry
-  int *srt = ff + capT;           // capT: segment products sorted by slot
+  int *srt = ff + capT;           // capT: kept products sorted by slot
   const unsigned lt = (1u << lane) - 1u;
-  const int64_t nwarps = (int64_t)gridDim.x * wpb;
-  for (int64_t i = blockIdx.x * (int64_t)wpb + wid; i < A.nbr; i += nwarps) {
+  auto sync = [&]() {
+    if constexpr (W == 1) __syncwarp();
+    else __syncthreads();
+  };
+  for (int64_t i = blockIdx.x * (int64_t)G + g; i < A.nbr; i += (int64_t)gridDim.x * G) {
     if (!pending[i]) continue;
     const int cs = rpC[i], cn = rpC[i + 1] - cs;
     const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
-    if (cn > capC || na > capA) continue;
-    const int T = row_product_prefix(A, B, a0, na, pre, lane);
-    for (int t = lane; t < cn; t += 32) cols[t] = ciC[cs + t];
+    const int chunk = (cn + W - 1) / W;
+    if (chunk > capC || na > capA) continue;
+    if (wr == 0) row_product_prefix(A, B, a0, na, pre, lane);
+    for (int t = wr * 32 + lane; t < cn; t += 32 * W) cols[t] = ciC[cs + t];
+    sync();
+    const int T = pre[na];
+    const int p_lo = wr * chunk, p_n = max(0, min(cn, p_lo + chunk) - p_lo);
     double acc[KU][BC];
 #pragma unroll
     for (int k = 0; k < KU; k++)
@@ -307,42 +322,56 @@ __global__ void __launch_bounds__(256)
     bool okp = true;
     for (int t0 = 0; t0 < T; t0 += capT) {
       const int tn = min(capT, T - t0);
-      for (int t = lane; t < cn; t += 32) {
+      for (int t = lane; t < p_n; t += 32) {
         start[t] = 0;
         off[t] = 0;
       }
       __syncwarp();
-      for (int tl = lane; tl < tn; tl += 32) {
-        const int t = t0 + tl;
-        const int x = product_entry(pre, na, t);
-        const int e = a0 + x;
-        const int f = B.rp[A.ci[e]] + (t - pre[x]);
-        int p = find_sorted(cols, cn, B.ci[f]);
-        if (p < 0) { okp = false; p = 0; }   // cannot happen: the symbolic pass saw every column
-        ee[tl] = e;
-        ff[tl] = f;
-        pl[tl] = p;
-        atomicAdd(&start[p], 1);
+      // slots of the segment's products; the warp keeps those in its range,
+      // in enumeration order (ballot + prefix count)
+      int kept = 0;
+      for (int c0 = 0; c0 < tn; c0 += 32) {
+        const int tl = c0 + lane;
+        int e = 0, f = 0, p = -1;
+        if (tl < tn) {
+          const int t = t0 + tl;
+          const int x = product_entry(pre, na, t);
+          e = a0 + x;
+          f = B.rp[A.ci[e]] + (t - pre[x]);
+          p = find_sorted(cols, cn, B.ci[f]);
+          if (p < 0 && tl < tn) okp = false;   // cannot happen: the symbolic pass saw every column
+          p -= p_lo;
+        }
+        const bool keep = tl < tn && p >= 0 && p < p_n;
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int pos = kept + __popc(km & lt);
+          ee[pos] = e;
+          ff[pos] = f;
+          pl[pos] = p;
+          atomicAdd(&start[p], 1);
+        }
+        kept += __popc(km);
       }
       __syncwarp();
       int run = 0;
-      for (int x0 = 0; x0 < cn; x0 += 32) {
+      for (int x0 = 0; x0 < p_n; x0 += 32) {
         const int x = x0 + lane;
-        const int c = x < cn ? start[x] : 0;
+        const int c = x < p_n ? start[x] : 0;
         int inc = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const int y = __shfl_up_sync(0xffffffffu, inc, o);
           if (lane >= o) inc += y;
         }
-        if (x < cn) start[x] = run + inc - c;
+        if (x < p_n) start[x] = run + inc - c;
         run += __shfl_sync(0xffffffffu, inc, 31);
       }
-      if (lane == 0) start[cn] = run;
+      if (lane == 0) start[p_n] = run;
       __syncwarp();
-      for (int c0 = 0; c0 < tn; c0 += 32) {
+      for (int c0 = 0; c0 < kept; c0 += 32) {
         const int tl = c0 + lane;
-        const bool act = tl < tn;
+        const bool act = tl < kept;
         const unsigned am = __ballot_sync(0xffffffffu, act);
         int p = 0, o = 0;
         unsigned m = 0;
@@ -359,7 +388,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int k = 0; k < KU; k++) {
         const int u = lane + 32 * k;
-        if (u < cn * BR) {
+        if (u < p_n * BR) {
           const int p = u / BR, r = u - p * BR;
           const int q1 = start[p + 1];
 #pragma unroll 2
@@ -382,19 +411,19 @@ __global__ void __launch_bounds__(256)
     }
     if (!__all_sync(0xffffffffu, okp)) {
       if (lane == 0) atomicExch(bad, 1);
-      continue;
-    }
+    } else {
 #pragma unroll
-    for (int k = 0; k < KU; k++) {
-      const int u = lane + 32 * k;
-      if (u < cn * BR) {
-        const int p = u / BR, r = u - p * BR;
+      for (int k = 0; k < KU; k++) {
+        const int u = lane + 32 * k;
+        if (u < p_n * BR) {
+          const int p = u / BR, r = u - p * BR;
 #pragma unroll
-        for (int cc = 0; cc < BC; cc++) valC[(int64_t)(cs + p) * BS + r * BC + cc] = acc[k][cc];
+          for (int cc = 0; cc < BC; cc++) valC[(int64_t)(cs + p_lo + p) * BS + r * BC + cc] = acc[k][cc];
+        }
       }
     }
-    __syncwarp();
-    if (lane == 0) pending[i] = 0;
+    sync();
+    if (wr == 0 && lane == 0) pending[i] = 0;
   }
 }
 
@@ -511,15 +540,19 @@ __global__ void k_max_pending_len(const int *rp, int n, const int *pending, int 
   atomicMax(out, m);
 }
 
-template <int BR, int BK, int BC, int KU>
+template <int BR, int BK, int BC, int KU, int W>
 void launch_seg(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, int *pending, int *flags,
                 cudaStream_t s) {
-  const int capA = 512, capT = 192, wpb = 8;
+  // a block per row (W > 1) also takes long rows of A (coarse restrictions)
+  const int capA = W == 1 ? 512 : 4096, capT = 192;
+  const int wpb = W == 1 ? 8 : W;
+  const int G = wpb / W;
   constexpr int capC = (32 * KU) / BR;
-  const size_t shm = (size_t)wpb * (3 * capC + 1 + capA + 1 + 4 * capT) * sizeof(int);
-  auto kern = k_spgemm_numeric_seg<BR, BK, BC, KU>;
+  const size_t ints = (size_t)G * (capC * W + capA + 1) + (size_t)wpb * (2 * capC + 1 + 4 * capT);
+  const size_t shm = ints * sizeof(int);
+  auto kern = k_spgemm_numeric_seg<BR, BK, BC, KU, W>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  kern<<<kSMs * 8, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, pending, capA, capT, flags);
+  kern<<<kSMs * (W == 1 ? 8 : 2), wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, pending, capA, capT, flags);
   FS_LAUNCHED();
 }
 
@@ -530,12 +563,13 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   DBuf<int> pending(C.nbr), flags(2);
   FS_CUDA(cudaMemsetAsync(pending.p, 1, sizeof(int) * C.nbr, s));   // nonzero = pending
   FS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
-  // segmented sorted-product kernel in two tiers of units per lane (KU = 4
-  // keeps the register accumulators small for the common short rows; KU = 9
-  // takes C rows up to 96 block columns): A-row entries capA, products per
-  // segment capT, 8 warps per block
-  launch_seg<BR, BK, BC, 4>(A, B, C, pending.p, flags.p, s);
-  launch_seg<BR, BK, BC, 9>(A, B, C, pending.p, flags.p, s);
+  // segmented sorted-product kernel in tiers of units per lane (KU = 4 keeps
+  // the register accumulators small for the common short rows; KU = 9 takes
+  // C rows up to 96 block columns per warp; eight warps per row take rows up
+  // to 768 block columns): A-row entries capA, products per segment capT
+  launch_seg<BR, BK, BC, 4, 1>(A, B, C, pending.p, flags.p, s);
+  launch_seg<BR, BK, BC, 9, 1>(A, B, C, pending.p, flags.p, s);
+  launch_seg<BR, BK, BC, 9, 8>(A, B, C, pending.p, flags.p, s);   // long rows: a block per row
   // rows beyond the tiers (very long rows of A or many products): longest C row among them
   k_max_pending_len<<<blocks_for(C.nbr, 256, kSMs * 4), 256, 0, s>>>(C.rp.p, C.nbr, pending.p, flags.p + 1);
   FS_LAUNCHED();
@@ -767,8 +801,8 @@ __global__ void k_sell_width(BsrView<double> A, int nslice, int *w) {
   for (int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sl < nslice;
        sl += (int64_t)gridDim.x * blockDim.x) {
     int m = 0;
-    for (int r = 0; r < 32; r++) {
-      int64_t row = sl * 32 + r;
+    for (int r = 0; r < kSellH; r++) {
+      int64_t row = sl * kSellH + r;
       if (row >= A.nbr) break;
       int len = A.rp[row + 1] - A.rp[row];
       m = len > m ? len : m;
@@ -786,10 +820,10 @@ __global__ void k_to_i64(const int *in, int64_t *out, int n) {
 template <typename T>
 __global__ void k_sell_fill(BsrView<double> A, int nslice, const int64_t *sp, int *ci, T *val) {
   const int bs = A.br * A.bc;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nslice * 32;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nslice * kSellH;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sl = t >> 5;
-    const int lane = (int)(t & 31);
+    const int64_t sl = t / kSellH;
+    const int lane = (int)(t % kSellH);
     const int64_t s0 = sp[sl], w = sp[sl + 1] - s0;
     const bool real = t < A.nbr;
     const int b0 = real ? A.rp[t] : 0;
@@ -797,11 +831,11 @@ __global__ void k_sell_fill(BsrView<double> A, int nslice, const int64_t *sp, in
     for (int64_t k = 0; k < w; k++) {
       const int64_t slot = s0 + k;
       if (k < len) {
-        ci[slot * 32 + lane] = A.ci[b0 + k];
-        for (int q = 0; q < bs; q++) val[(slot * bs + q) * 32 + lane] = (T)A.val[(int64_t)(b0 + k) * bs + q];
+        ci[slot * kSellH + lane] = A.ci[b0 + k];
+        for (int q = 0; q < bs; q++) val[(slot * bs + q) * kSellH + lane] = (T)A.val[(int64_t)(b0 + k) * bs + q];
       } else {
-        ci[slot * 32 + lane] = 0;
-        for (int q = 0; q < bs; q++) val[(slot * bs + q) * 32 + lane] = T(0);
+        ci[slot * kSellH + lane] = 0;
+        for (int q = 0; q < bs; q++) val[(slot * bs + q) * kSellH + lane] = T(0);
       }
     }
   }
@@ -812,7 +846,7 @@ template <typename T>
 Sell<T> to_sell(const BsrView<double> &A, cudaStream_t s) {
   Sell<T> S;
   S.nbr = A.nbr; S.nbc = A.nbc; S.br = A.br; S.bc = A.bc; S.nnzb = A.nnzb;
-  S.nslice = (A.nbr + 31) / 32;
+  S.nslice = (A.nbr + kSellH - 1) / kSellH;
   S.sp.alloc(S.nslice + 1);
   if (S.nslice == 0) {
     FS_CUDA(cudaMemsetAsync(S.sp.p, 0, sizeof(int64_t), s));
@@ -824,10 +858,10 @@ Sell<T> to_sell(const BsrView<double> &A, cudaStream_t s) {
   S.slots = exclusive_scan(w.p, wp.p, S.nslice, s);
   k_to_i64<<<blocks_for(S.nslice + 1, 256, kSMs * 4), 256, 0, s>>>(wp.p, S.sp.p, S.nslice);
   FS_LAUNCHED();
-  S.ci.alloc(S.slots * 32);
-  S.val.alloc(S.slots * 32 * A.br * A.bc);
+  S.ci.alloc(S.slots * kSellH);
+  S.val.alloc(S.slots * kSellH * A.br * A.bc);
   if (S.slots) {
-    k_sell_fill<T><<<blocks_for((int64_t)S.nslice * 32, 128, kSMs * 16), 128, 0, s>>>(A, S.nslice, S.sp.p, S.ci.p,
+    k_sell_fill<T><<<blocks_for((int64_t)S.nslice * kSellH, 128, kSMs * 16), 128, 0, s>>>(A, S.nslice, S.sp.p, S.ci.p,
                                                                                        S.val.p);
     FS_LAUNCHED();
   }
