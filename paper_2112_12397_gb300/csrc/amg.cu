@@ -23,6 +23,9 @@
 #include <type_traits>
 
 #include "amg.cuh"
+
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
 #include "sparse.cuh"
 #include "spmv.cuh"
 
@@ -89,28 +92,47 @@ __global__ void k_diag(BsrView<double> S, double *Dinv, double *dn, int *flag) {
 
 // ------------------------------------------------------------ 2. strength
 // pass 0: count strong entries per row; pass 1: write (col, weight)
+// Strong couplings of each row, in column order: ||S_ij||_F^2 > theta^2
+// ||S_ii||_F ||S_jj||_F (dn holds the diagonal-block norms), weight
+// ||S_ij||_F^2 / (||S_ii||_F ||S_jj||_F).  A group of G lanes takes a row and
+// G consecutive blocks at a time (coalesced block reads); a ballot keeps the
+// column order when pass 1 writes the strong entries.
+template <int G>
 __global__ void k_strength(BsrView<double> S, const double *dn, double theta2, int pass, int *cnt,
                            const int *rpG, int *ciG, double *wG) {
   const int bs = S.br * S.bc;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.nbr;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & (G - 1);
+  const int base = threadIdx.x & 31 & ~(G - 1);
+  const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << base;
+  const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; i < S.nbr; i += ngroups) {
     int n = 0;
-    int o = pass ? rpG[i] : 0;
+    const int o = pass ? rpG[i] : 0;
     const double di = dn[i];
-    for (int e = S.rp[i]; e < S.rp[i + 1]; e++) {
-      int j = S.ci[e];
-      if (j == i) continue;
-      double s = frob2(S.val + (int64_t)e * bs, bs);
-      double dd = __dmul_rn(di, dn[j]);
-      if (s > __dmul_rn(theta2, dd)) {
-        if (pass) {
-          ciG[o + n] = j;
-          wG[o + n] = __ddiv_rn(s, dd);
+    const int e1 = S.rp[i + 1];
+    for (int eb = S.rp[i]; eb < e1; eb += G) {
+      const int e = eb + lane;
+      bool strong = false;
+      int j = 0;
+      double w = 0.0;
+      if (e < e1) {
+        j = S.ci[e];
+        if (j != i) {
+          const double sv = frob2(S.val + (int64_t)e * bs, bs);
+          const double dd = __dmul_rn(di, dn[j]);
+          strong = sv > __dmul_rn(theta2, dd);
+          if (strong && pass) w = __ddiv_rn(sv, dd);
         }
-        n++;
       }
+      const unsigned m = __ballot_sync(gmask, strong) >> base;
+      if (pass && strong) {
+        const int pos = n + __popc(m & ((1u << lane) - 1u));
+        ciG[o + pos] = j;
+        wG[o + pos] = w;
+      }
+      n += __popc(m);
     }
-    if (!pass) cnt[i] = n;
+    if (!pass && lane == 0) cnt[i] = n;
   }
 }
 
@@ -282,6 +304,54 @@ __global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, c
       if (lane == 0) { atomicExch(flag, 1); if (!pass) cnt[i] = 0; }
       continue;
     }
+    if (len <= 32) {
+      // short rows: one entry per lane; lanes with equal aggregates found
+      // by a match, ranks by counting the distinct smaller aggregates
+      const int a = lane < len ? agg[S.ci[s0 + lane]] : -1;
+      const unsigned act = __ballot_sync(0xffffffffu, lane < len);
+      const unsigned same = __match_any_sync(0xffffffffu, a);
+      const bool first = lane < len && a >= 0 && (same & ((1u << lane) - 1u)) == 0;
+      const unsigned firsts = __ballot_sync(0xffffffffu, first);
+      int r = 0;
+      for (unsigned m = firsts; m; m &= m - 1) {
+        const int u = __ffs(m) - 1;
+        r += __shfl_sync(0xffffffffu, a, u) < a;
+      }
+      const int nu = __popc(firsts);
+      (void)act;
+      if (!pass) {
+        if (lane == 0) cnt[i] = nu;
+        continue;
+      }
+      if (first) {
+        // blocks of this aggregate in row order (ascending lanes of the match)
+        double acc[BS];
+#pragma unroll
+        for (int q = 0; q < BS; q++) acc[q] = 0.0;
+        for (unsigned m = same; m; m &= m - 1) {
+          const double *v = S.val + (int64_t)(s0 + __ffs(m) - 1) * BS;
+#pragma unroll
+          for (int q = 0; q < BS; q++) acc[q] += v[q];
+        }
+        const int o = rpP[i];
+        const double *Di = Dinv + i * BS;
+        const int ai = agg[i];
+        const double isz = 1.0 / sqrt((double)asize[a]);
+        double *out = valP + (int64_t)(o + r) * BS;
+#pragma unroll
+        for (int rr = 0; rr < B; rr++)
+#pragma unroll
+          for (int cc = 0; cc < B; cc++) {
+            double mm = 0.0;
+#pragma unroll
+            for (int q = 0; q < B; q++) mm += Di[rr * B + q] * (acc[q * B + cc] * isz);
+            const double pt = (ai == a && rr == cc) ? isz : 0.0;
+            out[rr * B + cc] = pt - omega * mm;
+          }
+        ciP[o + r] = a;
+      }
+      continue;
+    }
     for (int t = lane; t < len; t += 32) al[t] = agg[S.ci[s0 + t]];
     __syncwarp();
     for (int t = lane; t < len; t += 32) {
@@ -353,9 +423,11 @@ __global__ void k_bsr_to_dense(BsrView<double> S, double *Dn) {
 
 // Gauss-Jordan step k, part 1 (one block): partial pivoting (lowest index on
 // ties), row swap, scaling of the pivot row, copy of column k
-__global__ void k_gj_pivot(double *M, int n, int k, int *perm, double *colk, int *flag) {
-  __shared__ double sv[1024];
-  __shared__ int si[1024];
+// One Gauss-Jordan pivot step on a single block of 1024 threads (shared
+// arrays sv, si of blockDim entries): choose the pivot row, swap it into
+// row k, scale row k and save the multipliers of column k.
+__device__ void gj_pivot_step(double *M, int n, int k, int *perm, double *colk, int *flag, double *sv,
+                              int *si) {
   double best = -1.0;
   int bi = n;
   for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
@@ -398,8 +470,14 @@ __global__ void k_gj_pivot(double *M, int n, int k, int *perm, double *colk, int
   for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = (i == k) ? 0.0 : M[(int64_t)i * n + k];
 }
 
+__global__ void k_gj_pivot(double *M, int n, int k, int *perm, double *colk, int *flag) {
+  __shared__ double sv[1024];
+  __shared__ int si[1024];
+  gj_pivot_step(M, n, k, perm, colk, flag, sv, si);
+}
+
 // part 2: a_ij -= a_ik a_kj for i != k (column k becomes -a_ik / piv)
-__global__ void k_gj_elim(double *M, int n, int k, const double *colk) {
+__device__ inline void gj_elim_step(double *M, int n, int k, const double *colk) {
   int64_t total = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -408,6 +486,23 @@ __global__ void k_gj_elim(double *M, int n, int k, const double *colk) {
     double f = colk[i];
     double base = (j == k) ? 0.0 : M[t];
     M[t] = base - f * M[(int64_t)k * n + j];
+  }
+}
+
+__global__ void k_gj_elim(double *M, int n, int k, const double *colk) { gj_elim_step(M, n, k, colk); }
+
+// All n steps in one cooperative launch (co-resident blocks, grid-wide
+// barriers between the pivot and elimination phases): the same arithmetic
+// as the two kernels per step, without 2 n launches.
+__global__ void __launch_bounds__(1024) k_gj_coop(double *M, int n, int *perm, double *colk, int *flag) {
+  __shared__ double sv[1024];
+  __shared__ int si[1024];
+  cg::grid_group grid = cg::this_grid();
+  for (int k = 0; k < n; k++) {
+    if (blockIdx.x == 0) gj_pivot_step(M, n, k, perm, colk, flag, sv, si);
+    grid.sync();
+    gj_elim_step(M, n, k, colk);
+    grid.sync();
   }
 }
 
@@ -479,13 +574,15 @@ Graph strength_graph(const BsrView<double> &S, const double *dn, double theta, c
   Gd.rp.alloc(n + 1);
   DBuf<int> cnt(n + 1);
   const double th2 = theta * theta;
-  k_strength<<<grid_rows(n), kT, 0, s>>>(S, dn, th2, 0, cnt.p, nullptr, nullptr, nullptr);
+  constexpr int SG = 8;   // lanes per row
+  const int sgrid = blocks_for((int64_t)n * SG, kT, kSMs * 32);
+  k_strength<SG><<<sgrid, kT, 0, s>>>(S, dn, th2, 0, cnt.p, nullptr, nullptr, nullptr);
   FS_LAUNCHED();
   Gd.nnz = exclusive_scan(cnt.p, Gd.rp.p, n, s);
   Gd.ci.alloc(Gd.nnz);
   Gd.w.alloc(Gd.nnz);
   if (Gd.nnz) {
-    k_strength<<<grid_rows(n), kT, 0, s>>>(S, dn, th2, 1, nullptr, Gd.rp.p, Gd.ci.p, Gd.w.p);
+    k_strength<SG><<<sgrid, kT, 0, s>>>(S, dn, th2, 1, nullptr, Gd.rp.p, Gd.ci.p, Gd.w.p);
     FS_LAUNCHED();
   }
   // transpose of the directed strong pattern (weights as 1x1 blocks)
@@ -676,12 +773,30 @@ void invert_coarsest(Hierarchy &H, cudaStream_t s) {
   DBuf<int> perm(n), flag(1);
   DBuf<double> colk(n);
   FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
-  const int eg = blocks_for((int64_t)n * n, 256, kSMs * 8);
-  for (int k = 0; k < n; k++) {
-    k_gj_pivot<<<1, 1024, 0, s>>>(H.cinv.p, n, k, perm.p, colk.p, flag.p);
+  int dev = 0, coop = 0, per_sm = 0;
+  FS_CUDA(cudaGetDevice(&dev));
+  FS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (coop) FS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_coop, 1024, 0));
+  if (coop && per_sm > 0) {
+    int nsm = 0;
+    FS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int want = (int)std::min<int64_t>(((int64_t)n * n + 1023) / 1024, (int64_t)nsm * per_sm);
+    const int blocks = std::max(1, want);
+    double *Mp = H.cinv.p;
+    int *pp = perm.p, *fp = flag.p;
+    double *cp = colk.p;
+    int nn = n;
+    void *args[] = {&Mp, &nn, &pp, &cp, &fp};
+    FS_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_coop, dim3(blocks), dim3(1024), args, 0, s));
     FS_LAUNCHED();
-    k_gj_elim<<<eg, 256, 0, s>>>(H.cinv.p, n, k, colk.p);
-    FS_LAUNCHED();
+  } else {
+    const int eg = blocks_for((int64_t)n * n, 256, kSMs * 8);
+    for (int k = 0; k < n; k++) {
+      k_gj_pivot<<<1, 1024, 0, s>>>(H.cinv.p, n, k, perm.p, colk.p, flag.p);
+      FS_LAUNCHED();
+      k_gj_elim<<<eg, 256, 0, s>>>(H.cinv.p, n, k, colk.p);
+      FS_LAUNCHED();
+    }
   }
   k_gj_unpermute<<<blocks_for(n, 128, kSMs), 128, 0, s>>>(H.cinv.p, n, perm.p);
   FS_LAUNCHED();
