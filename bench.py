@@ -62,6 +62,8 @@ def parse():
                     help="timed solves per preconditioner variant on one shared setup (0: skip)")
     ap.add_argument("--update-steps", type=int, default=1,
                     help="timed fc_update calls per update case (0: skip)")
+    ap.add_argument("--adjoint-steps", type=int, default=1,
+                    help="timed adjoint solves + aperture gradients after the timed region (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -348,6 +350,19 @@ def ours(args, rank, world, local_rank):
             cv.profile(False)
             variants[name] = {"solve_s": statistics.mean(ts) / 1e3, "iters": it_v, "relres": rr_v,
                               "prec_apply_ms": pr[1] / max(pr[0], 1)}
+        # t-u-p with the geometric fixed stress (Eq. FS) instead of the
+        # algebraic one: cell volume 2 h^3 and mean bulk modulus per face
+        omega = torch.full((P.n_face,), 2.0 * P.h ** 3, dtype=torch.float64, device="cuda")
+        kbar = torch.from_numpy(P.Ebar_face / (3.0 * (1.0 - 2.0 * P.nu))).cuda()
+        cv.set_geometric_fs(omega, kbar, P.dt)
+        cv.update(blocks, P.n_node, P.n_face)
+        cv.solve("tup", b, x, args.tol, args.maxit, allow_fail=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, it_v, rr_v = cv.solve("tup", b, x, args.tol, args.maxit, allow_fail=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        variants["tup_geometric_fs"] = {"solve_s": e0.elapsed_time(e1) / 1e3, "iters": it_v, "relres": rr_v}
         del cv
         ctx = make_ctx(args.precision)
 
@@ -381,6 +396,35 @@ def ours(args, rank, world, local_rank):
             update[name] = {"update_s": statistics.mean(ts) / 1e3, "solve_iters_after": its_u,
                             "relres_after": rr_u}
         update["full_setup_s"] = statistics.mean(setup_ms) / 1e3
+
+    # adjoint (the gradient of 0.5 ||p - p_obs||^2 through J^T lambda = g):
+    # the transposed solve with the transposed preconditioner, and dJ/da by
+    # the aperture-derivative contraction, after one forward solve
+    adjoint = None
+    if args.adjoint_steps > 0:
+        ctx.setup(blocks, P.n_node, P.n_face)
+        ctx.solve(args.variant, b, x, args.tol, args.maxit, allow_fail=True)
+        g = torch.zeros_like(b)
+        pn = P.n_face
+        p_obs = torch.from_numpy(np.random.default_rng(12).standard_normal(pn)).cuda()
+        g[-pn:] = x[-pn:] - p_obs
+        lam = torch.zeros_like(b)
+        ctx.solve_adjoint(args.variant, g, lam, args.tol, args.maxit, allow_fail=True)   # builds J^T data
+        dk = fs.device_dk(P)
+        grad = torch.zeros(pn, dtype=torch.float64, device="cuda")
+        ts, tg = [], []
+        for _ in range(args.adjoint_steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            rc, it_a, rr_a = ctx.solve_adjoint(args.variant, g, lam, args.tol, args.maxit, allow_fail=True)
+            e1.record(stream)
+            ctx.aperture_gradient(dk, x, lam, grad)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            tg.append(e1.elapsed_time(e2))
+        adjoint = {"solve_s": statistics.mean(ts) / 1e3, "iters": it_a, "relres": rr_a,
+                   "aperture_gradient_ms": statistics.mean(tg), "dk_entries": int(dk["val"].numel())}
 
     # end to end through the C-ABI with host buffers
     e2e = None
@@ -448,6 +492,7 @@ def ours(args, rank, world, local_rank):
         "fp64": fp64,
         "variants": variants,
         "update": update,
+        "adjoint": adjoint,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

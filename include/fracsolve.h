@@ -135,6 +135,19 @@ int fc_create(fc_ctx **ctx, const fc_options *opt, void *cuda_stream);
  * FC_INTERNAL, FC_CUDA_ERROR. */
 int fc_setup(fc_ctx *ctx, const fc_blocks *J);
 
+/* Replace the algebraic fixed stress of S~2 (Eq. FS_algebraic) by the
+ * geometric one (Eq. FS, the cheaper form the paper starts from) at the next
+ * fc_setup or fc_update: [S_K]_k = -omega[k] / (kbar[k] dt) on faces whose
+ * row of Q2 holds a nonzero entry, 0 elsewhere, S~2 = T - S_K.  omega[k] is
+ * the volume of the cells around face k, kbar[k] their bulk modulus, dt the
+ * time step of the flow equation (the sign and 1/dt follow Q2 = -Q1^T / dt
+ * on open faces).  Device arrays of n_face doubles, copied; call after the
+ * first fc_setup (the face count is taken from it).  omega == NULL restores
+ * the algebraic form.  Errors: FC_BAD_ARG (kbar NULL, dt <= 0), FC_NOT_SETUP
+ * (no fc_setup yet, or no faces); a later fc_setup with another face count
+ * fails with FC_BAD_ARG until this is reset. */
+int fc_set_geometric_fs(fc_ctx *ctx, const double *d_omega, const double *d_kbar, double dt);
+
 /* Numeric refresh of the last fc_setup for new block values with exactly the
  * same sparsity patterns and sizes (the same mesh and contact states: the
  * next Newton iteration of an active set, or new apertures and pressures

@@ -94,7 +94,25 @@ def fixed_stress(P, S1: sp.csr_matrix, blk=None) -> np.ndarray:
     return out
 
 
-def s2_tilde(P, S1: sp.csr_matrix, blk=None) -> sp.csr_matrix:
-    """S~2 = T - S_K (Eq. app_Schur2_2), S_K diagonal."""
+def fixed_stress_geometric(P, omega: np.ndarray, kbar: np.ndarray, dt: float, blk=None) -> np.ndarray:
+    """Diagonal of the geometric fixed stress (Eq. FS): the volume |Omega_k|
+    of the cells around face k over their bulk modulus Kbar_k, in the units
+    and sign of Q2 S1^-1 Q1 here: Q2 carries -Q1^T / dt on open faces, so
+    [S_K]_k = -|Omega_k| / (Kbar_k dt).  Faces whose row of Q2 is zero get 0,
+    the index rule of the algebraic form."""
     b = blk or osp.blocks(P)
-    return (b["T"] - sp.diags(fixed_stress(P, S1, b))).tocsr()
+    Q2r = b["Q2"].tocsr()
+    out = np.zeros(P.n_face)
+    for k in range(P.n_face):
+        r0, r1 = Q2r.indptr[k], Q2r.indptr[k + 1]
+        if np.any(Q2r.data[r0:r1] != 0.0):
+            out[k] = -omega[k] / (kbar[k] * dt)
+    return out
+
+
+def s2_tilde(P, S1: sp.csr_matrix, blk=None, sk: np.ndarray | None = None) -> sp.csr_matrix:
+    """S~2 = T - S_K (Eq. app_Schur2_2), S_K diagonal: the algebraic fixed
+    stress, or the given diagonal ``sk`` (e.g. the geometric form)."""
+    b = blk or osp.blocks(P)
+    d = fixed_stress(P, S1, b) if sk is None else sk
+    return (b["T"] - sp.diags(d)).tocsr()

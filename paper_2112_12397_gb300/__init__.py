@@ -24,7 +24,7 @@ FC_M_LEVEL, FC_M_PROLONG, FC_M_S1, FC_M_STILDE, FC_M_S2TILDE = range(5)
 VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP, "tup_star": FC_TUP_STAR}
 
 # exported symbols declared by include/fracsolve.h
-SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_update", "fc_spmv", "fc_residual", "fc_residual_noalloc",
+SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_update", "fc_set_geometric_fs", "fc_spmv", "fc_residual", "fc_residual_noalloc",
            "fc_apply_prec", "fc_solve", "fc_spmv_adjoint", "fc_apply_prec_adjoint", "fc_solve_adjoint",
            "fc_vcycle_adjoint", "fc_aperture_gradient",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = False):
         "fc_create": (C.c_int, [C.POINTER(vp), C.POINTER(fc_options), vp]),
         "fc_setup": (C.c_int, [vp, C.POINTER(fc_blocks)]),
         "fc_update": (C.c_int, [vp, C.POINTER(fc_blocks)]),
+        "fc_set_geometric_fs": (C.c_int, [vp, vp, vp, d]),
         "fc_spmv": (C.c_int, [vp, vp, vp]),
         "fc_residual": (C.c_int, [vp, vp, vp, vp, pd]),
         "fc_residual_noalloc": (C.c_int, [vp, vp, vp, pd]),
@@ -194,6 +195,15 @@ class Context:
         J = self._blocks(blocks, n_node, n_face)
         self._check(self.lib.fc_update(self.h, C.byref(J)), self.h)
         self.n_node, self.n_face = n_node, n_face
+
+    def set_geometric_fs(self, omega=None, kbar=None, dt: float = 0.0):
+        """fc_set_geometric_fs: per-face cell volume and bulk modulus (CUDA
+        float64 tensors) for the geometric fixed stress; None restores the
+        algebraic form.  Takes effect at the next setup or update."""
+        if omega is None:
+            self._check(self.lib.fc_set_geometric_fs(self.h, None, None, 0.0), self.h)
+        else:
+            self._check(self.lib.fc_set_geometric_fs(self.h, _ptr(omega), _ptr(kbar), dt), self.h)
 
     # ------------------------------------------------------------ apply
     def spmv(self, x, y):

@@ -985,6 +985,7 @@ void refresh_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t 
 }  // namespace
 
 void amg_refresh(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s) {
+  NvtxRange nvtx("amg_refresh");
   FS_REQUIRE(H.built && !H.lev.empty(), FC_NOT_SETUP, "AMG hierarchy not built");
   const Bsr<double> &S = H.lev[0].S;
   FS_REQUIRE(S0.nbr == S.nbr && S0.nnzb == S.nnzb && S0.br == S.br, FC_BAD_ARG,
@@ -1000,6 +1001,7 @@ void amg_refresh(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s) 
 
 void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int precision,
                cudaStream_t s) {
+  NvtxRange nvtx("amg_setup");
   H.prm = prm;
   H.B = B;
   H.built = false;
@@ -1144,6 +1146,7 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
 
 template <typename TP>
 void amg_vcycle(Hierarchy &H, const TP *f, TP *x, cudaStream_t s) {
+  NvtxRange nvtx("vcycle");
   FS_REQUIRE(H.built, FC_NOT_SETUP, "AMG hierarchy not built");
   std::vector<LevelCycle<TP>> *C;
   if constexpr (std::is_same<TP, float>::value) C = &H.cf;
@@ -1215,6 +1218,7 @@ void amg_prepare_transpose(Hierarchy &H, int precision, cudaStream_t s) {
 
 template <typename TP>
 void amg_vcycle_t(Hierarchy &H, const TP *f, TP *x, cudaStream_t s) {
+  NvtxRange nvtx("vcycle_t");
   FS_REQUIRE(H.built && H.have_t, FC_NOT_SETUP, "transposed AMG cycle not prepared");
   std::vector<LevelCycle<TP>> *C;
   if constexpr (std::is_same<TP, float>::value) C = &H.cf;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <cstdio>
@@ -140,6 +141,15 @@ extern int g_verbose;
 
 // Wall-clock phase timer for setup diagnostics (verbose only): synchronises
 // the stream at each mark.
+// NVTX range for the duration of a scope (visible in Nsight timelines; a
+// no-op unless a tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 struct PhaseTimer {
   bool on;
   cudaStream_t s;

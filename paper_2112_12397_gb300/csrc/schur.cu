@@ -212,6 +212,20 @@ __global__ void k_sub_diag(BsrView<double> T, const double *SK, double *val) {
 
 inline int g(int64_t n) { return blocks_for(n, 256, kSMs * 16); }
 
+// geometric fixed stress (Eq. FS): [S_K]_k = -omega_k / (kbar_k dt) on faces
+// whose row of Q2 holds a nonzero entry, 0 elsewhere (the sign and the 1/dt
+// of Q2 = -Q1^T / dt on open faces)
+__global__ void k_fixed_stress_geometric(BsrView<double> Q2, const double *omega, const double *kbar,
+                                         double dt, double *SK) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < Q2.nbr;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    bool nz = false;
+    for (int e = Q2.rp[k]; e < Q2.rp[k + 1] && !nz; e++)
+      for (int q = 0; q < 3; q++) nz |= Q2.val[(int64_t)e * 3 + q] != 0.0;
+    SK[k] = nz ? -omega[k] / (kbar[k] * dt) : 0.0;
+  }
+}
+
 }  // namespace
 
 void build_hinv(const BsrView<double> &H, DBuf<double> &Hinv, cudaStream_t s) {
@@ -275,21 +289,28 @@ Bsr<double> build_stilde(const BsrView<double> &S1, const BsrView<double> &Q1, c
 }
 
 Bsr<double> build_s2tilde(const BsrView<double> &S1, const BsrView<double> &Q1, const BsrView<double> &Q2,
-                          const BsrView<double> &T, DBuf<double> &SK, cudaStream_t s) {
+                          const BsrView<double> &T, DBuf<double> &SK, cudaStream_t s, const GeoFs *geo) {
   const int nf = Q2.nbr;
   SK.alloc(nf > 0 ? nf : 1);
-  Bsr<double> Q1T = transpose(Q1, s);
-  DBuf<int> flag(1);
-  FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
-  if (nf) {
-    k_fixed_stress<<<kSMs * 16, kFsThreads, 0, s>>>(S1, Q1T.view(), Q2, SK.p, flag.p);
-    FS_LAUNCHED();
+  if (geo && geo->omega) {
+    if (nf) {
+      k_fixed_stress_geometric<<<g(nf), 256, 0, s>>>(Q2, geo->omega, geo->kbar, geo->dt, SK.p);
+      FS_LAUNCHED();
+    }
+  } else {
+    Bsr<double> Q1T = transpose(Q1, s);
+    DBuf<int> flag(1);
+    FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    if (nf) {
+      k_fixed_stress<<<kSMs * 16, kFsThreads, 0, s>>>(S1, Q1T.view(), Q2, SK.p, flag.p);
+      FS_LAUNCHED();
+    }
+    int h = 0;
+    FS_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+    FS_REQUIRE(h != 2, FC_INTERNAL, "fixed-stress index set larger than 64");
+    FS_REQUIRE(h != 1, FC_SINGULAR_BLOCK, "singular local block S1^(k) in the fixed-stress diagonal");
   }
-  int h = 0;
-  FS_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  FS_CUDA(cudaStreamSynchronize(s));
-  FS_REQUIRE(h != 2, FC_INTERNAL, "fixed-stress index set larger than 64");
-  FS_REQUIRE(h != 1, FC_SINGULAR_BLOCK, "singular local block S1^(k) in the fixed-stress diagonal");
   Bsr<double> S2 = copy_cast<double, double>(T, s);
   if (nf) {
     k_sub_diag<<<g(nf), 256, 0, s>>>(T, SK.p, S2.val.p);

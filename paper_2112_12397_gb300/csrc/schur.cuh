@@ -16,8 +16,18 @@ Bsr<double> build_s1(const BsrView<double> &A, const BsrView<double> &C1, const 
 Bsr<double> build_stilde(const BsrView<double> &S1, const BsrView<double> &Q1, const BsrView<double> &Q2,
                          const BsrView<double> &T, cudaStream_t s);
 
-// S~2 = T - S_K with the algebraic fixed-stress diagonal S_K (written to SK).
+// Data of the geometric fixed stress (Eq. FS): per face the volume of the
+// cells around it and their bulk modulus (device arrays), and the time step.
+struct GeoFs {
+  const double *omega = nullptr;
+  const double *kbar = nullptr;
+  double dt = 0.0;
+};
+
+// S~2 = T - S_K (written to SK) with the algebraic fixed-stress diagonal
+// (Eq. FS_algebraic), or the geometric one when geo carries data.
 Bsr<double> build_s2tilde(const BsrView<double> &S1, const BsrView<double> &Q1, const BsrView<double> &Q2,
-                          const BsrView<double> &T, DBuf<double> &SK, cudaStream_t s);
+                          const BsrView<double> &T, DBuf<double> &SK, cudaStream_t s,
+                          const GeoFs *geo = nullptr);
 
 }  // namespace fs

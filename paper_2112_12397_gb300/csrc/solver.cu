@@ -254,6 +254,9 @@ struct fc_ctx {
   DBuf<double> Zd;
   DBuf<double> xk, rk, bk, hb, hx;
   DBuf<double> zd;   // a float direction widened to double for J z / J^T z
+  DBuf<double> geo_omega, geo_kbar;   // geometric fixed stress data (empty: algebraic)
+  GeoFs geo;
+  int64_t geo_n = 0;
   double *stat_host = nullptr;   // pinned
   Profiler prof;
   ~fc_ctx() {
@@ -324,6 +327,7 @@ void prepare_prec(fc_ctx &c, PrecData<TP> &P) {
 // t-u-p form D2^-1 L2^-1 of Eq. P2)
 template <typename TP>
 void apply_prec(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
+  NvtxRange nvtx("apply_prec");
   cudaStream_t s = c.s;
   const int64_t nu = c.nu, nt = c.nt;
   const int64_t nf = c.nf;
@@ -388,6 +392,7 @@ double bsr_bytes(const Bsr<double> &m) {
 
 template <typename TX>
 void jac_spmv(fc_ctx &c, const TX *z, double *y) {
+  NvtxRange nvtx("J z");
   cudaStream_t s = c.s;
   const double bytes = bsr_bytes<double>(c.A) + bsr_bytes<double>(c.C1) + bsr_bytes<double>(c.Q1) +
                        bsr_bytes<double>(c.C2) + bsr_bytes<double>(c.H) + bsr_bytes<double>(c.Q2) +
@@ -449,6 +454,7 @@ void jac_spmv_t(fc_ctx &c, const TX *z, double *y) {
 // S~2 are symmetric and so are their scalar V-cycles)
 template <typename TP>
 void apply_prec_t(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
+  NvtxRange nvtx("apply_prec_t");
   cudaStream_t s = c.s;
   const int64_t nu = c.nu, nt = c.nt, nf = c.nf;
   const TP *w_u = w, *w_t = w + nu, *w_p = w + nu + nt;
@@ -531,6 +537,7 @@ void ensure_krylov(fc_ctx &c, int maxit) {
 //   h = V^T w; w -= V h; h' = V^T w; w -= V h'; h += h'
 // with ||w||^2 before (w02) and after (w2) folded into the passes.
 void cgs2(fc_ctx &c, int m, double *w) {
+  NvtxRange nvtx("CGS2");
   const int64_t n = c.n;
   cudaStream_t s = c.s;
   const int nd = kCgsDotGrid, ns = kCgsSubGrid;
@@ -624,6 +631,7 @@ FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rt
 template <typename TP, bool ADJ = false>
 int solve_impl(fc_ctx &c, int variant, const double *b, double *x, double tol, int maxit, int *iters,
                double *relres) {
+  NvtxRange nvtx(ADJ ? "fc_solve_adjoint" : "fc_solve");
   cudaStream_t s = c.s;
   const int64_t n = c.n;
   c.xk.ensure(n); c.rk.ensure(n);
@@ -882,7 +890,10 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     check_bsr(J->H, nf, nf, 3, 3, "H");
     check_bsr(J->Q2, nf, nn, 1, 3, "Q2");
     check_bsr(J->T, nf, nf, 1, 1, "T");
+    NvtxRange nvtx("fc_setup");
     cudaStream_t s = c->s;
+    FS_REQUIRE(!c->geo.omega || c->geo_n == nf, FC_BAD_ARG,
+               "geometric fixed-stress data was given for another face count; reset it with fc_set_geometric_fs");
     c->nn = nn; c->nf = nf;
     c->nu = 3LL * nn; c->nt = 3LL * nf; c->n = c->nu + c->nt + nf;
     fs::g_verbose = c->opt.verbose;
@@ -914,7 +925,7 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
       if (nf) amg_setup(c->hier[FC_H_TPU_P], copy_cast<double, double>(c->T.view(), s), 1, amg_params(c->opt, true), prec, s);
     }
     if (c->have[FC_TUP]) {
-      c->S2t = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s);  // Alg. 3 line 3
+      c->S2t = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s, &c->geo);  // Alg. 3 line 3
       pt.mark("S2tilde (fixed stress)");
       amg_setup(c->hier[FC_H_TUP_U], copy_cast<double, double>(c->S1.view(), s), 3, amg_params(c->opt, false), prec, s);
       if (nf) amg_setup(c->hier[FC_H_TUP_P], copy_cast<double, double>(c->S2t.view(), s), 1, amg_params(c->opt, true), prec, s);
@@ -945,6 +956,7 @@ int fc_update(fc_ctx *c, const fc_blocks *J) {
     check_bsr(J->H, nf, nf, 3, 3, "H");
     check_bsr(J->Q2, nf, nn, 1, 3, "Q2");
     check_bsr(J->T, nf, nf, 1, 1, "T");
+    NvtxRange nvtx("fc_update");
     cudaStream_t s = c->s;
     fs::g_verbose = c->opt.verbose;
     PhaseTimer pt(c->opt.verbose > 0, s, "update");
@@ -987,7 +999,7 @@ int fc_update(fc_ctx *c, const fc_blocks *J) {
       if (nf && changed[6]) amg_refresh(c->hier[FC_H_TPU_P], copy_cast<double, double>(c->T.view(), s), prec, s);
     }
     if (c->have[FC_TUP]) {
-      Bsr<double> S2 = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s);
+      Bsr<double> S2 = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s, &c->geo);
       const bool s2_same = S2.nnzb == c->S2t.nnzb && same_values(S2.val.p, c->S2t.val.p, S2.nnzb, s);
       c->S2t = std::move(S2);
       if (!s1_same) amg_refresh(c->hier[FC_H_TUP_U], copy_cast<double, double>(c->S1.view(), s), prec, s);
@@ -1001,6 +1013,31 @@ int fc_update(fc_ctx *c, const fc_blocks *J) {
     pt.mark("prec data");
     FS_CUDA(cudaStreamSynchronize(s));
     c->ready = true;
+    return FC_OK;
+  });
+}
+
+int fc_set_geometric_fs(fc_ctx *c, const double *omega, const double *kbar, double dt) {
+  if (!c) return FC_BAD_ARG;
+  return run(c, [&]() {
+    if (!omega) {
+      c->geo = GeoFs();
+      c->geo_omega.release();
+      c->geo_kbar.release();
+      return FC_OK;
+    }
+    FS_REQUIRE(kbar && dt > 0.0, FC_BAD_ARG, "geometric fixed stress needs kbar and dt > 0");
+    FS_REQUIRE(c->nf > 0, FC_NOT_SETUP, "geometric fixed stress: call fc_setup first (face count)");
+    const int64_t nf = c->nf;
+    c->geo_omega.alloc(nf);
+    c->geo_kbar.alloc(nf);
+    FS_CUDA(cudaMemcpyAsync(c->geo_omega.p, omega, sizeof(double) * nf, cudaMemcpyDeviceToDevice, c->s));
+    FS_CUDA(cudaMemcpyAsync(c->geo_kbar.p, kbar, sizeof(double) * nf, cudaMemcpyDeviceToDevice, c->s));
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    c->geo.omega = c->geo_omega.p;
+    c->geo.kbar = c->geo_kbar.p;
+    c->geo.dt = dt;
+    c->geo_n = nf;
     return FC_OK;
   });
 }

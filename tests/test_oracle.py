@@ -301,3 +301,25 @@ def test_amg_numeric_rebuild_on_kept_aggregates():
     for La, Ld in zip(a.levels[:-1], dbl.levels[:-1]):
         assert La.lam == pytest.approx(Ld.lam, rel=1e-13)
         assert abs(Ld.P - La.P).max() <= 1e-14 * abs(La.P).max()
+
+
+def test_geometric_fixed_stress():
+    """Eq. FS in the units of Q2 S1^-1 Q1: on a case whose only face
+    coupling in Q2 is -Q1^T / dt (p^l = 0 removes F_u), the algebraic and
+    geometric diagonals share sign and support, and agree within the order of
+    magnitude their derivation allows (|Omega| / K against the local
+    compliance seen through Q1); faces with a zero row of Q2 get 0."""
+    P = fracgen.generate("planes64", N=8, seed=2, pl_scale=0.0)
+    S1 = schur.s1(P)
+    alg = schur.fixed_stress(P, S1)
+    h = 1.0 / P.N
+    omega = np.full(P.n_face, 2.0 * h ** 3)
+    kbar = P.Ebar_face / (3.0 * (1.0 - 2.0 * P.nu))
+    geo = schur.fixed_stress_geometric(P, omega, kbar, P.dt)
+    open_ = P.state == 2
+    assert np.array_equal(geo != 0, alg != 0) and np.array_equal(geo != 0, open_)
+    assert np.all(geo[open_] < 0) and np.all(alg[open_] < 0)
+    ratio = geo[open_] / alg[open_]
+    assert 0.1 < np.median(ratio) < 10.0
+    S2 = schur.s2_tilde(P, S1, sk=geo)
+    assert np.abs(S2 - S2.T).max() <= 1e-14 * np.abs(S2).max()
