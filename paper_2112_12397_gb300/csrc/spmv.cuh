@@ -131,11 +131,17 @@ struct EpiHinvUpdate {
   }
 };
 
-// lanes per row from the mean number of blocks per row
+// lanes per row from the mean number of blocks per row (a sweep on the
+// 128^3 workload: 16 lanes for the ~69-block rows of the first coarse level
+// beat 32 by 11% on the coarse part of the cycle; the ~126-block rows of
+// the finest restriction keep 32)
+#ifndef FS_BSR_LANES32_ABOVE
+#define FS_BSR_LANES32_ABOVE 100.0
+#endif
 inline int lanes_for(int64_t nnzb, int nbr, int bs) {
   (void)bs;
   double per = nbr > 0 ? (double)nnzb / nbr : 0.0;
-  if (per > 24) return 32;
+  if (per > FS_BSR_LANES32_ABOVE) return 32;
   if (per > 12) return 16;
   if (per > 6) return 8;
   return 4;

@@ -367,3 +367,22 @@ def test_full_size_planes64_fp64(fs):
     agg, lam = ctx.get_aggregates(fs.FC_H_TUP_U, 0, P.n_node)
     assert np.array_equal(agg, agg_ref)
     ctx.close()
+
+
+def test_iterations_roughly_flat_in_mesh_size(fs):
+    """Sec. 4 reports t-u-p iteration counts roughly independent of the mesh
+    size; on the three-plane family from 16^3 to 64^3 the counts stay within
+    a factor 1.5 of each other (both variants, mixed precision)."""
+    its = {"tpu": [], "tup": []}
+    for N in (16, 32, 64):
+        P = fracgen.generate("planes64", N=N)
+        ctx = fs.context_for(P, fs.default_options(precision="mixed"))
+        b = cuda(P.b)
+        for variant in its:
+            x = torch.zeros_like(b)
+            rc, it, rr = ctx.solve(variant, b, x, 1e-8, 600)
+            assert rr <= 1e-8
+            its[variant].append(it)
+        ctx.close()
+    for variant, v in its.items():
+        assert max(v) <= 1.5 * min(v), (variant, v)
