@@ -248,7 +248,9 @@ struct fc_ctx {
   PrecData<float> pf;
   PrecData<double> pd;
   // Krylov workspace
-  int kcap = 0;
+  int kcap = 0;          // iterations the Krylov workspace holds ...
+  int64_t kn = 0;        // ... for vectors of this length
+  int kprec = -1;        // ... in this precision mode
   DBuf<double> V, Hm, cs, sn, g, y, hacc, htmp, partial, stat, w2, w02, red;
   DBuf<float> Zf;
   DBuf<double> Zd;
@@ -521,7 +523,10 @@ template <>
 double *zbase<double>(fc_ctx &c) { return c.Zd.p; }
 
 void ensure_krylov(fc_ctx &c, int maxit) {
-  if (c.kcap >= maxit) return;
+  if (c.kcap >= maxit && c.kn == c.n && c.kprec == c.opt.precision) return;
+  // invalidate first: a failed allocation below must not leave a workspace
+  // that looks large enough
+  c.kcap = 0;
   const int64_t n = c.n;
   c.V.alloc((size_t)(maxit + 1) * n);
   if (c.opt.precision == FC_MIXED) c.Zf.alloc((size_t)maxit * n);
@@ -531,6 +536,8 @@ void ensure_krylov(fc_ctx &c, int maxit) {
   c.hacc.alloc(maxit + 1); c.htmp.alloc(maxit + 1);
   c.partial.alloc((size_t)(maxit + 2) * (size_t)(kCgsSubGrid > kCgsDotGrid ? kCgsSubGrid : kCgsDotGrid));
   c.kcap = maxit;
+  c.kn = n;
+  c.kprec = c.opt.precision;
 }
 
 // Classical Gram-Schmidt applied twice against V_0..V_{m-1}:

@@ -386,3 +386,22 @@ def test_iterations_roughly_flat_in_mesh_size(fs):
         ctx.close()
     for variant, v in its.items():
         assert max(v) <= 1.5 * min(v), (variant, v)
+
+
+def test_context_reused_for_other_sizes(fs):
+    """One context, fc_setup on a small, a larger and again the small system:
+    the Krylov workspace follows the vector length (and the iteration cap)."""
+    ctx = fs.Context(fs.default_options(coarse_max=50, coarse_max_p=30))
+    for preset, over in (("tiny8", {}), ("rects128", dict(N=16)), ("tiny8", {})):
+        P = fracgen.generate(preset, **over)
+        ctx.setup(fs.device_blocks(P), P.n_node, P.n_face)
+        J = osp.jacobian(P)
+        for maxit in (60, 400):
+            b = cuda(P.b)
+            x = torch.zeros_like(b)
+            rc, it, rr = ctx.solve("tup", b, x, 1e-8, maxit, allow_fail=True)
+            true = np.linalg.norm(P.b - J @ x.cpu().numpy()) / np.linalg.norm(P.b)
+            assert abs(true - rr) <= 1e-3 * rr
+            if maxit == 400:
+                assert rr <= 1e-8
+    ctx.close()
