@@ -210,6 +210,24 @@ def reference(args, rank):
     }))
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(value: float, dist, device: str = "cuda") -> float:
+    """The largest value over the ranks (the slowest replica's step time);
+    the value itself on one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_env() -> tuple[int, int, int]:
+    """RANK, WORLD_SIZE, LOCAL_RANK of a torchrun launch (0, 1, 0 without)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
 # ------------------------------------------------------------------ our arm
 def ours(args, rank, world, local_rank):
     import numpy as np
@@ -304,11 +322,7 @@ def ours(args, rank, world, local_rank):
     x_mixed = x.cpu().numpy().copy()
 
     # max over ranks
-    step_ms = total_ms / args.steps
-    if dist is not None:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(total_ms / args.steps, dist)
 
     # FP64 form on the same workload for the FP32-vs-FP64 comparison
     fp64 = None
@@ -526,9 +540,7 @@ def main():
     if args.mode == "vcycle":
         vcycle_case(args)
         return
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local_rank = rank_env()
     if args.impl == "reference":
         reference(args, rank)
     else:
