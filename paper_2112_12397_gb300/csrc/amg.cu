@@ -323,32 +323,37 @@ __global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, c
         if (lane == 0) cnt[i] = nu;
         continue;
       }
-      if (first) {
-        // blocks of this aggregate in row order (ascending lanes of the match)
-        double acc[BS];
+      // the B x B entries of the row's nu blocks of P, spread over the lanes
+      // (unit k: aggregate number k / BS in lane order, entry k % BS); each
+      // entry sums its aggregate's blocks in row order, as a whole block would
+      const int o = rpP[i];
+      const double *Di = Dinv + i * BS;
+      const int ai = agg[i];
+      for (int k0 = 0; k0 < nu * BS; k0 += 32) {
+        const int k = k0 + lane;
+        const int fi = min(k / BS, nu - 1), e = k - (k / BS) * BS;
+        // lane holding the fi-th first entry
+        unsigned m = firsts;
+        for (int t = 0; t < fi; t++) m &= m - 1;
+        const int fl = __ffs(m) - 1;
+        const int fa = __shfl_sync(0xffffffffu, a, fl);
+        const unsigned fsame = __shfl_sync(0xffffffffu, same, fl);
+        const int fr = __shfl_sync(0xffffffffu, r, fl);
+        if (k < nu * BS) {
+          const int rr = e / B, cc = e - rr * B;
+          const double isz = 1.0 / sqrt((double)asize[fa]);
+          double mm = 0.0;
 #pragma unroll
-        for (int q = 0; q < BS; q++) acc[q] = 0.0;
-        for (unsigned m = same; m; m &= m - 1) {
-          const double *v = S.val + (int64_t)(s0 + __ffs(m) - 1) * BS;
-#pragma unroll
-          for (int q = 0; q < BS; q++) acc[q] += v[q];
-        }
-        const int o = rpP[i];
-        const double *Di = Dinv + i * BS;
-        const int ai = agg[i];
-        const double isz = 1.0 / sqrt((double)asize[a]);
-        double *out = valP + (int64_t)(o + r) * BS;
-#pragma unroll
-        for (int rr = 0; rr < B; rr++)
-#pragma unroll
-          for (int cc = 0; cc < B; cc++) {
-            double mm = 0.0;
-#pragma unroll
-            for (int q = 0; q < B; q++) mm += Di[rr * B + q] * (acc[q * B + cc] * isz);
-            const double pt = (ai == a && rr == cc) ? isz : 0.0;
-            out[rr * B + cc] = pt - omega * mm;
+          for (int q = 0; q < B; q++) {
+            double acc = 0.0;
+            for (unsigned mu = fsame; mu; mu &= mu - 1)
+              acc += S.val[(int64_t)(s0 + __ffs(mu) - 1) * BS + q * B + cc];
+            mm += Di[rr * B + q] * (acc * isz);
           }
-        ciP[o + r] = a;
+          const double pt = (ai == fa && rr == cc) ? isz : 0.0;
+          valP[(int64_t)(o + fr) * BS + e] = pt - omega * mm;
+          if (e == 0) ciP[o + fr] = fa;
+        }
       }
       continue;
     }
