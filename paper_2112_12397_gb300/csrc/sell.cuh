@@ -42,10 +42,6 @@ struct Sell {
     v.sp = sp.p; v.ci = ci.p; v.val = val.p;
     return v;
   }
-  // bytes a product streams from the matrix (values, indices, slot offsets)
-  double stream_bytes() const {
-    return (double)slots * kSellH * (br * bc * sizeof(T) + 4) + (double)(nslice + 1) * 8;
-  }
 };
 
 // Convert a double BSR matrix (sorted rows) into sliced ELL of value type T.
