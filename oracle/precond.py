@@ -56,18 +56,18 @@ class BlockPreconditioner:
         b = blk or osp.blocks(P)
         self.b = b
         self.nu, self.nt, self.np_ = 3 * P.n_node, 3 * P.n_face, P.n_face
-        self.Hinv = schur.htilde_inv(P, b["H"])                      # Alg. 1/3 line 1
+        self.Hinv = schur.htilde_inv(P, b["H"])                      # H~^-1 (Alg. 1, Alg. 3)
         opt = opt or AmgOptions()
         opt_p = opt_p or opt
         if variant == "tpu":
             self.S1 = schur.s1(P, b)
-            self.Su = schur.s_tilde(P, b, self.S1)                    # Alg. 1 line 3
+            self.Su = schur.s_tilde(P, b, self.S1)                    # S~ (Alg. 1)
             self.u_inv = _solver(self.Su if u_matrix is None else u_matrix, 3, u_solver, opt, u_aggregates)
             self.p_inv = _solver(b["T"] if p_matrix is None else p_matrix, 1, p_solver, opt_p, p_aggregates)
         elif variant in ("tup", "tup_star"):
-            self.S1 = schur.s1(P, b)                                  # Alg. 3 line 2
+            self.S1 = schur.s1(P, b)                                  # S1 (Alg. 3)
             self.Su = self.S1
-            self.S2 = schur.s2_tilde(P, self.S1, b)                   # Alg. 3 line 3
+            self.S2 = schur.s2_tilde(P, self.S1, b)                   # S~2 = T - FS (Alg. 3)
             self.u_inv = _solver(self.S1 if u_matrix is None else u_matrix, 3, u_solver, opt, u_aggregates)
             self.p_inv = _solver(self.S2 if p_matrix is None else p_matrix, 1, p_solver, opt_p, p_aggregates)
         else:
@@ -76,52 +76,49 @@ class BlockPreconditioner:
     def split(self, w):
         return w[:self.nu], w[self.nu:self.nu + self.nt], w[self.nu + self.nt:]
 
+    # The applications are written factor by factor from the block LDU forms
+    # (Eq. P1 in the order (t, p, u), Eq. P2 in the order (t, u, p)); Alg. 2
+    # and Alg. 4 are the same products with every inner inverse applied once.
+
     def apply_tpu(self, w):
-        """Alg. 2, app_tpu."""
+        """M1^-1 w = U1^-1 D1^-1 L1^-1 w (Eq. P1), the operator of Alg. 2."""
         b = self.b
         w_u, w_t, w_p = self.split(w)
-        t_p = self.p_inv(w_p)                          # 1: t_p = T^-1 w_p
-        t_t = self.Hinv @ w_t                          # 2: t_t = H~^-1 w_t
-        t_u = w_u + b["C1"] @ t_t - b["Q1"] @ t_p      # 3
-        v_u = self.u_inv(t_u)                          # 4: AMG(S~, t_u)
-        s_p = b["Q2"] @ v_u                            # 5
-        s_t = b["C2"] @ v_u                            # 6
-        v_p = t_p - self.p_inv(s_p)                    # 7
-        v_t = -t_t + self.Hinv @ s_t                   # 8
-        return np.concatenate([v_u, v_t, v_p])
+        hw = self.Hinv @ w_t                                  # H~^-1 w_t
+        tw = self.p_inv(w_p)                                  # T^-1 w_p
+        # L1^-1 then D1^-1: t -> -H~^-1 w_t, p -> T^-1 w_p,
+        # u -> S~^-1 (w_u + C1 H~^-1 w_t - Q1 T^-1 w_p)
+        z_u = self.u_inv(w_u + b["C1"] @ hw - b["Q1"] @ tw)
+        # U1^-1: p -= T^-1 Q2 u, t += H~^-1 C2 u
+        v_p = tw - self.p_inv(b["Q2"] @ z_u)
+        v_t = -hw + self.Hinv @ (b["C2"] @ z_u)
+        return np.concatenate([z_u, v_t, v_p])
+
+    def _tup_lower_diag(self, w):
+        """D2^-1 L2^-1 w (Eq. LDU2): t -> -H~^-1 w_t, u -> S~1^-1 y_u with
+        y_u = w_u + C1 H~^-1 w_t, p -> S~2^-1 (w_p - Q2 S~1^-1 y_u); the
+        S~1^-1 y_u of both factors is one AMG application."""
+        b = self.b
+        w_u, w_t, w_p = self.split(w)
+        hw = self.Hinv @ w_t
+        z_u = self.u_inv(w_u + b["C1"] @ hw)
+        z_p = self.p_inv(w_p - b["Q2"] @ z_u)
+        return z_u, -hw, z_p
 
     def apply_tup(self, w):
-        """Alg. 4, app_tup."""
+        """M2^-1 w = U2^-1 (D2^-1 L2^-1 w) (Eq. P2), the operator of Alg. 4:
+        U2^-1 takes u -= S~1^-1 Q1 p, then t += H~^-1 C2 u."""
         b = self.b
-        w_u, w_t, w_p = self.split(w)
-        t_t = self.Hinv @ w_t                          # 1
-        t_u = w_u + b["C1"] @ t_t                      # 2
-        s_u = self.u_inv(t_u)                          # 3: AMG(S1, t_u)
-        t_p = w_p - b["Q2"] @ s_u                      # 4
-        v_p = self.p_inv(t_p)                          # 5: S~2^-1 t_p
-        t_u = b["Q1"] @ v_p                            # 6
-        v_u = self.u_inv(t_u)                          # 7: AMG(S1, t_u)
-        v_u = s_u - v_u                                # 8
-        s_t = b["C2"] @ v_u                            # 9
-        v_t = -t_t + self.Hinv @ s_t                   # 10
-        return np.concatenate([v_u, v_t, v_p])
+        z_u, z_t, z_p = self._tup_lower_diag(w)
+        v_u = z_u - self.u_inv(b["Q1"] @ z_p)
+        v_t = z_t + self.Hinv @ (b["C2"] @ v_u)
+        return np.concatenate([v_u, v_t, z_p])
 
     def apply_tup_star(self, w):
-        """M2*^-1 w = D2^-1 (L2^-1 w) with the factors of Eq. LDU2, in the
-        (t, u, p) order of Eq. Q2:
-          L2^-1: y_t = w_t, y_u = w_u + C1 H~^-1 w_t, y_p = w_p - Q2 S~1^-1 y_u
-          D2^-1: v_t = -H~^-1 y_t, v_u = S~1^-1 y_u, v_p = S~2^-1 y_p
-        S~1^-1 y_u appears in both factors; it is one AMG call."""
-        b = self.b
-        w_u, w_t, w_p = self.split(w)
-        t_t = self.Hinv @ w_t                          # H~^-1 w_t
-        y_u = w_u + b["C1"] @ t_t                      # L2^-1, u block
-        s_u = self.u_inv(y_u)                          # S~1^-1 y_u = AMG(S1, y_u)
-        y_p = w_p - b["Q2"] @ s_u                      # L2^-1, p block
-        v_p = self.p_inv(y_p)                          # D2^-1, p block
-        v_u = s_u                                      # D2^-1, u block
-        v_t = -t_t                                     # D2^-1, t block
-        return np.concatenate([v_u, v_t, v_p])
+        """M2*^-1 w = D2^-1 L2^-1 w: Eq. P2 without its first factor (the
+        incomplete form of the remark after Prop. 3.2)."""
+        z_u, z_t, z_p = self._tup_lower_diag(w)
+        return np.concatenate([z_u, z_t, z_p])
 
     def __call__(self, w):
         w = np.asarray(w, dtype=np.float64)

@@ -47,7 +47,7 @@ def htilde_inv(P, Hs=None) -> sp.csr_matrix:
 
 
 def s1(P, blk=None) -> sp.csr_matrix:
-    """S1 = A + C1 H~^-1 C2 (Eq. Schur1_2, Alg. 3 line 2)."""
+    """S1 = A + C1 H~^-1 C2 (Eq. Schur1_2, Alg. 3)."""
     b = blk or osp.blocks(P)
     return (b["A"] + b["C1"] @ htilde_inv(P, b["H"]) @ b["C2"]).tocsr()
 

@@ -38,6 +38,10 @@ inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
 
 // levels whose rows hold more blocks than this on average use the
 // lane-group BSR kernel instead of sliced ELL (coarse levels)
+// blocks of the cooperative Gauss-Jordan launch
+#ifndef FS_GJ_MAX_BLOCKS
+#define FS_GJ_MAX_BLOCKS 64
+#endif
 #ifndef FS_SELL_MAX_MEAN_ROW
 #define FS_SELL_MAX_MEAN_ROW 40.0
 #endif
@@ -496,17 +500,62 @@ __device__ inline void gj_elim_step(double *M, int n, int k, const double *colk)
 
 __global__ void k_gj_elim(double *M, int n, int k, const double *colk) { gj_elim_step(M, n, k, colk); }
 
-// All n steps in one cooperative launch (co-resident blocks, grid-wide
-// barriers between the pivot and elimination phases): the same arithmetic
-// as the two kernels per step, without 2 n launches.
-__global__ void __launch_bounds__(1024) k_gj_coop(double *M, int n, int *perm, double *colk, int *flag) {
+// All n steps in one cooperative launch (co-resident blocks, one grid-wide
+// barrier per step): step k reads matrix Mk and writes Mn (ping-pong), so
+// every block can take the pivot of column k itself (the same search, the
+// same row) and eliminate its entries without waiting for a pivot phase.
+// The arithmetic per entry is that of the two-kernel step: the pivot row
+// (swapped into row k) scaled by 1/piv, then a_ij - a_ik a~_kj with column k
+// becoming -a_ik / piv.  perm[k] = pivot row; the result ends in buf[n & 1].
+__global__ void __launch_bounds__(1024) k_gj_coop(double *buf0, double *buf1, int n, int *perm, int *flag) {
   __shared__ double sv[1024];
   __shared__ int si[1024];
   cg::grid_group grid = cg::this_grid();
   for (int k = 0; k < n; k++) {
-    if (blockIdx.x == 0) gj_pivot_step(M, n, k, perm, colk, flag, sv, si);
-    grid.sync();
-    gj_elim_step(M, n, k, colk);
+    const double *Mk = (k & 1) ? buf1 : buf0;
+    double *Mn = (k & 1) ? buf0 : buf1;
+    double best = -1.0;
+    int bi = n;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      double v = fabs(Mk[(int64_t)i * n + k]);
+      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        double v = sv[threadIdx.x + o];
+        int ii = si[threadIdx.x + o];
+        if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ii < si[threadIdx.x])) {
+          sv[threadIdx.x] = v;
+          si[threadIdx.x] = ii;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = si[0] < n ? si[0] : k;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      perm[k] = p;
+      if (!(sv[0] > 0.0)) atomicExch(flag, 1);
+    }
+    const double piv = Mk[(int64_t)p * n + k];
+    const double ip = piv != 0.0 ? 1.0 / piv : 0.0;
+    __syncthreads();
+    const int64_t total = (int64_t)n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+      const int i = (int)(t / n), j = (int)(t - (int64_t)i * n);
+      const double rkj = (j == k) ? ip : Mk[(int64_t)p * n + j] * ip;   // scaled pivot row
+      if (i == k) {
+        Mn[t] = rkj;
+      } else {
+        const int src = (i == p) ? k : i;                                  // rows k and p swap
+        const double aik = Mk[(int64_t)src * n + k];
+        const double base = (j == k) ? 0.0 : Mk[(int64_t)src * n + j];
+        Mn[t] = base - aik * rkj;
+      }
+    }
     grid.sync();
   }
 }
@@ -785,15 +834,20 @@ void invert_coarsest(Hierarchy &H, cudaStream_t s) {
   if (coop && per_sm > 0) {
     int nsm = 0;
     FS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int want = (int)std::min<int64_t>(((int64_t)n * n + 1023) / 1024, (int64_t)nsm * per_sm);
+    // few blocks: the grid-wide barrier per step costs more with every block
+    const int want = (int)std::min<int64_t>(std::min<int64_t>(((int64_t)n * n + 1023) / 1024, (int64_t)nsm * per_sm),
+                                            FS_GJ_MAX_BLOCKS);
     const int blocks = std::max(1, want);
-    double *Mp = H.cinv.p;
+    DBuf<double> other((size_t)n * n);
+    double *b0 = H.cinv.p, *b1 = other.p;
     int *pp = perm.p, *fp = flag.p;
-    double *cp = colk.p;
     int nn = n;
-    void *args[] = {&Mp, &nn, &pp, &cp, &fp};
+    void *args[] = {&b0, &b1, &nn, &pp, &fp};
     FS_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_coop, dim3(blocks), dim3(1024), args, 0, s));
     FS_LAUNCHED();
+    if (n & 1)
+      FS_CUDA(cudaMemcpyAsync(H.cinv.p, other.p, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, s));
+    FS_CUDA(cudaStreamSynchronize(s));
   } else {
     const int eg = blocks_for((int64_t)n * n, 256, kSMs * 8);
     for (int k = 0; k < n; k++) {

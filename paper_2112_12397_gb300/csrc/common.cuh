@@ -139,8 +139,6 @@ struct Profiler {
 // library diagnostics level (set from fc_options.verbose by fc_setup)
 extern int g_verbose;
 
-// Wall-clock phase timer for setup diagnostics (verbose only): synchronises
-// the stream at each mark.
 // NVTX range for the duration of a scope (visible in Nsight timelines; a
 // no-op unless a tool is attached)
 struct NvtxRange {
@@ -150,6 +148,8 @@ struct NvtxRange {
   NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+// Wall-clock phase timer for setup diagnostics (verbose only): synchronises
+// the stream at each mark.
 struct PhaseTimer {
   bool on;
   cudaStream_t s;

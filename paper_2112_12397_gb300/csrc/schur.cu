@@ -1,9 +1,9 @@
 // Setup of the approximate Schur complements (double precision).
 //
-//   H~ = Bdiag(H, 3) and its inverse           Alg. 1 line 1, Alg. 3 line 1
-//   S1 = A + C1 H~^-1 C2                       Eq. Schur1_2, Alg. 3 line 2
-//   S~ = S1 - Q1 T~^-1 Q2, T~ = diag(T)        Eq. appSchur_1, Alg. 1 line 3
-//   S~2 = T - S_K                              Eq. app_Schur2_2, Alg. 3 line 3
+//   H~ = Bdiag(H, 3) and its inverse           Alg. 1, Alg. 3
+//   S1 = A + C1 H~^-1 C2                       Eq. Schur1_2, Alg. 3
+//   S~ = S1 - Q1 T~^-1 Q2, T~ = diag(T)        Eq. appSchur_1, Alg. 1
+//   S~2 = T - S_K                              Eq. app_Schur2_2, Alg. 3
 //   [S_K]_k = Q2^(k)T (S1^(k))^-1 Q1^(k)       Eq. FS_algebraic (Remark rem:FS)
 // S_K: for every face k with a nonzero row of Q2, the scalar index set
 // K = nz(Q1 column k) U nz(Q2 row k) (entries that are exactly zero do not

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(kCgsT)
     double acc[kCgsQ];
 #pragma unroll
     for (int q = 0; q < kCgsQ; q++) acc[q] = 0.0;
+#pragma unroll 2
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + tid; e < n; e += stride) {
       const double we = __ldg(w + e);
 #pragma unroll
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kCgsT)
   double nn = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + tid; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     double sum = 0.0;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = 0; i < m; i++) sum += __ldg(V + (int64_t)i * n + e) * hs[i];
     const double we = w[e] - sum;
     w[e] = we;
@@ -353,34 +354,34 @@ void apply_prec(fc_ctx &c, PrecData<TP> &P, int variant, const TP *w, TP *z) {
     }
   } else if (variant == FC_TUP) {
     Hierarchy &Hu = c.hier[FC_H_TUP_U], &Hp = c.hier[FC_H_TUP_P];
-    if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }   // 1
-    sell_axpby<3, 3>(P.sC1.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                // 2
+    if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }   // t_t = H~^-1 w_t
+    sell_axpby<3, 3>(P.sC1.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                // t_u = w_u + C1 t_t
     c.prof.start(PK_VCYCLE, s);
-    amg_vcycle<TP>(Hu, P.tu.p, P.su.p, s);                                                            // 3
+    amg_vcycle<TP>(Hu, P.tu.p, P.su.p, s);                                                            // s_u = AMG(S1, t_u)
     c.prof.stop(PK_VCYCLE, s, 0.0);
-    sell_axpby<1, 3>(P.sQ2.view(), P.su.p, P.tp.p, -1.0, 1.0, w_p, s);                              // 4
+    sell_axpby<1, 3>(P.sQ2.view(), P.su.p, P.tp.p, -1.0, 1.0, w_p, s);                              // t_p = w_p - Q2 s_u
     c.prof.start(PK_VCYCLE_P, s);
-    if (nf) amg_vcycle<TP>(Hp, P.tp.p, z_p, s);                                                        // 5
+    if (nf) amg_vcycle<TP>(Hp, P.tp.p, z_p, s);                                                        // v_p = S~2^-1 t_p
     c.prof.stop(PK_VCYCLE_P, s, 0.0);
-    sell_axpby<3, 1>(P.sQ1.view(), z_p, P.tu.p, 1.0, 0.0, (const TP *)nullptr, s);                 // 6
-    amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // 7
-    axpbyz(z_u, P.su.p, z_u, 1.0, -1.0, nu, s);                                                       // 8
-    if (nf) {                                                                                         // 9-10
+    sell_axpby<3, 1>(P.sQ1.view(), z_p, P.tu.p, 1.0, 0.0, (const TP *)nullptr, s);                 // t_u = Q1 v_p
+    amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // v_u = AMG(S1, t_u)
+    axpbyz(z_u, P.su.p, z_u, 1.0, -1.0, nu, s);                                                       // v_u = s_u - v_u
+    if (nf) {                                                                                         // v_t = -t_t + H~^-1 C2 v_u
       EpiHinvUpdate<TP> e{z_t, P.tt.p, P.Hinv};
       sell_spmv<3, 3>(P.sC2.view(), z_u, e, s);
     }
   } else {
     Hierarchy &Hu = c.hier[FC_H_TPU_U], &Hp = c.hier[FC_H_TPU_P];
-    if (nf) amg_vcycle<TP>(Hp, w_p, P.tp.p, s);                                                        // 1
-    if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }    // 2
-    sell_axpby<3, 3>(P.sC1.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                // 3
+    if (nf) amg_vcycle<TP>(Hp, w_p, P.tp.p, s);                                                        // t_p = T^-1 w_p
+    if (nf) { k_face_hinv<TP><<<vgrid(nf), 256, 0, s>>>(nf, P.Hinv, w_t, P.tt.p); FS_LAUNCHED(); }    // t_t = H~^-1 w_t
+    sell_axpby<3, 3>(P.sC1.view(), P.tt.p, P.tu.p, 1.0, 1.0, w_u, s);                                // t_u = w_u + C1 t_t - Q1 t_p
     sell_axpby<3, 1>(P.sQ1.view(), P.tp.p, P.tu.p, -1.0, 1.0, P.tu.p, s);
-    amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // 4
+    amg_vcycle<TP>(Hu, P.tu.p, z_u, s);                                                               // v_u = AMG(S~, t_u)
     if (nf) {
-      sell_axpby<1, 3>(P.sQ2.view(), z_u, P.sp.p, 1.0, 0.0, (const TP *)nullptr, s);                // 5
-      amg_vcycle<TP>(Hp, P.sp.p, P.vp.p, s);                                                          // 7
+      sell_axpby<1, 3>(P.sQ2.view(), z_u, P.sp.p, 1.0, 0.0, (const TP *)nullptr, s);                // s_p = Q2 v_u
+      amg_vcycle<TP>(Hp, P.sp.p, P.vp.p, s);                                                          // v_p = t_p - T^-1 s_p
       axpbyz(z_p, P.tp.p, P.vp.p, 1.0, -1.0, nf, s);
-      EpiHinvUpdate<TP> e{z_t, P.tt.p, P.Hinv};                                                      // 6, 8
+      EpiHinvUpdate<TP> e{z_t, P.tt.p, P.Hinv};                                                      // v_t = -t_t + H~^-1 C2 v_u
       sell_spmv<3, 3>(P.sC2.view(), z_u, e, s);
     }
   }
@@ -920,19 +921,19 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     c->pf = PrecData<float>();
     c->pd = PrecData<double>();
     pt.mark("free old");
-    build_hinv(c->H.view(), c->Hinv64, s);                                        // Alg. 1/3 line 1
-    c->S1 = build_s1(c->A.view(), c->C1.view(), c->C2.view(), c->Hinv64.p, s);   // Alg. 3 line 2
+    build_hinv(c->H.view(), c->Hinv64, s);                                        // H~^-1 (Alg. 1, Alg. 3)
+    c->S1 = build_s1(c->A.view(), c->C1.view(), c->C2.view(), c->Hinv64.p, s);   // S1 (Alg. 3)
     pt.mark("S1");
     const int prec = c->opt.precision;
     c->have[FC_TPU] = (c->opt.variants >> FC_TPU) & 1;
     c->have[FC_TUP] = (c->opt.variants >> FC_TUP) & 1;
     if (c->have[FC_TPU]) {
-      c->St = build_stilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), s);   // Alg. 1 line 3
+      c->St = build_stilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), s);   // S~ (Alg. 1)
       amg_setup(c->hier[FC_H_TPU_U], copy_cast<double, double>(c->St.view(), s), 3, amg_params(c->opt, false), prec, s);
       if (nf) amg_setup(c->hier[FC_H_TPU_P], copy_cast<double, double>(c->T.view(), s), 1, amg_params(c->opt, true), prec, s);
     }
     if (c->have[FC_TUP]) {
-      c->S2t = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s, &c->geo);  // Alg. 3 line 3
+      c->S2t = build_s2tilde(c->S1.view(), c->Q1.view(), c->Q2.view(), c->T.view(), c->SK, s, &c->geo);  // S~2 = T - FS (Alg. 3)
       pt.mark("S2tilde (fixed stress)");
       amg_setup(c->hier[FC_H_TUP_U], copy_cast<double, double>(c->S1.view(), s), 3, amg_params(c->opt, false), prec, s);
       if (nf) amg_setup(c->hier[FC_H_TUP_P], copy_cast<double, double>(c->S2t.view(), s), 1, amg_params(c->opt, true), prec, s);

@@ -112,7 +112,7 @@ struct EpiCheb {
   }
 };
 
-// Alg. 2 line 8 / Alg. 4 line 10 fused with the C2 product:
+// The last step of Alg. 2 and Alg. 4 fused with the C2 product:
 //   v_t[row] = -t_t[row] + Hinv[row] * (C2 v_u)[row]
 template <typename TA>
 struct EpiHinvUpdate {
