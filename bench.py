@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rects128", choices=sorted(WORKLOADS))
+    ap.add_argument("--N", type=int, default=0,
+                    help="override the workload's grid size (cells per side; 0: the workload's own)")
     ap.add_argument("--variant", default="tup", choices=["tup", "tpu", "tup_star"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -242,7 +244,7 @@ def ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     fracgen.build()
-    P = fracgen.generate(args.workload, seed=rank)
+    P = fracgen.generate(args.workload, seed=rank, **({"N": args.N} if args.N else {}))
     blocks = fs.device_blocks(P)
     b = torch.from_numpy(P.b).cuda()
     x = torch.zeros_like(b)
@@ -496,6 +498,7 @@ def ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "unknowns": P.n,
+                   "grid": P.N,
                    "variant": args.variant, "precision": args.precision, "tol": args.tol,
                    "l2": "matrices of several GB, larger than L2; no flush"},
         "breakdown": {"setup_s": mean_setup, "solve_s": mean_solve, "iters": its[-1], "relres": rrs[-1],

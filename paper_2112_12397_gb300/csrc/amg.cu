@@ -99,11 +99,13 @@ __global__ void k_diag(BsrView<double> S, double *Dinv, double *dn, int *flag) {
 // Strong couplings of each row, in column order: ||S_ij||_F^2 > theta^2
 // ||S_ii||_F ||S_jj||_F (dn holds the diagonal-block norms), weight
 // ||S_ij||_F^2 / (||S_ii||_F ||S_jj||_F).  A group of G lanes takes a row and
-// G consecutive blocks at a time (coalesced block reads); a ballot keeps the
-// column order when pass 1 writes the strong entries.
+// G consecutive blocks at a time (coalesced block reads).  Pass 0 evaluates
+// every block once, keeps each entry's weight (-1: not strong) in wall and
+// counts; pass 1 compacts the strong entries from wall in column order (a
+// ballot keeps the order) without reading S's values again.
 template <int G>
 __global__ void k_strength(BsrView<double> S, const double *dn, double theta2, int pass, int *cnt,
-                           const int *rpG, int *ciG, double *wG) {
+                           double *wall, const int *rpG, int *ciG, double *wG) {
   const int bs = S.br * S.bc;
   const int lane = threadIdx.x & (G - 1);
   const int base = threadIdx.x & 31 & ~(G - 1);
@@ -112,26 +114,31 @@ __global__ void k_strength(BsrView<double> S, const double *dn, double theta2, i
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; i < S.nbr; i += ngroups) {
     int n = 0;
     const int o = pass ? rpG[i] : 0;
-    const double di = dn[i];
+    const double di = pass ? 0.0 : dn[i];
     const int e1 = S.rp[i + 1];
     for (int eb = S.rp[i]; eb < e1; eb += G) {
       const int e = eb + lane;
       bool strong = false;
-      int j = 0;
-      double w = 0.0;
+      double w = -1.0;
       if (e < e1) {
-        j = S.ci[e];
-        if (j != i) {
-          const double sv = frob2(S.val + (int64_t)e * bs, bs);
-          const double dd = __dmul_rn(di, dn[j]);
-          strong = sv > __dmul_rn(theta2, dd);
-          if (strong && pass) w = __ddiv_rn(sv, dd);
+        if (pass) {
+          w = wall[e];
+          strong = w >= 0.0;
+        } else {
+          const int j = S.ci[e];
+          if (j != i) {
+            const double sv = frob2(S.val + (int64_t)e * bs, bs);
+            const double dd = __dmul_rn(di, dn[j]);
+            strong = sv > __dmul_rn(theta2, dd);
+            if (strong) w = __ddiv_rn(sv, dd);
+          }
+          wall[e] = w;
         }
       }
       const unsigned m = __ballot_sync(gmask, strong) >> base;
       if (pass && strong) {
         const int pos = n + __popc(m & ((1u << lane) - 1u));
-        ciG[o + pos] = j;
+        ciG[o + pos] = S.ci[e];
         wG[o + pos] = w;
       }
       n += __popc(m);
@@ -630,13 +637,14 @@ Graph strength_graph(const BsrView<double> &S, const double *dn, double theta, c
   const double th2 = theta * theta;
   constexpr int SG = 8;   // lanes per row
   const int sgrid = blocks_for((int64_t)n * SG, kT, kSMs * 32);
-  k_strength<SG><<<sgrid, kT, 0, s>>>(S, dn, th2, 0, cnt.p, nullptr, nullptr, nullptr);
+  DBuf<double> wall(S.nnzb > 0 ? S.nnzb : 1);
+  k_strength<SG><<<sgrid, kT, 0, s>>>(S, dn, th2, 0, cnt.p, wall.p, nullptr, nullptr, nullptr);
   FS_LAUNCHED();
   Gd.nnz = exclusive_scan(cnt.p, Gd.rp.p, n, s);
   Gd.ci.alloc(Gd.nnz);
   Gd.w.alloc(Gd.nnz);
   if (Gd.nnz) {
-    k_strength<SG><<<sgrid, kT, 0, s>>>(S, dn, th2, 1, nullptr, Gd.rp.p, Gd.ci.p, Gd.w.p);
+    k_strength<SG><<<sgrid, kT, 0, s>>>(S, dn, th2, 1, nullptr, wall.p, Gd.rp.p, Gd.ci.p, Gd.w.p);
     FS_LAUNCHED();
   }
   // transpose of the directed strong pattern (weights as 1x1 blocks)
