@@ -130,9 +130,11 @@ int fc_create(fc_ctx **ctx, const fc_options *opt, void *cuda_stream);
  * (Eq. appSchur_1), S~2 = T - FS(Q2, S1, Q1) (Eq. app_Schur2_2,
  * Eq. FS_algebraic), and the AMG hierarchies of S~ and T (t-p-u) or S1 and
  * S~2 (t-u-p).  The blocks are deep-copied: the caller may free them when
- * this returns.  Calling it again replaces the operator.
- * Errors: FC_BAD_ARG (inconsistent sizes), FC_SINGULAR_BLOCK, FC_OOM,
- * FC_INTERNAL, FC_CUDA_ERROR. */
+ * this returns.  Calling it again replaces the operator.  Every block's
+ * structure is checked on the device before use (row pointers from 0 to
+ * nnzb, non-decreasing; columns in range and strictly increasing per row).
+ * Errors: FC_BAD_ARG (inconsistent sizes, row pointers or columns),
+ * FC_SINGULAR_BLOCK, FC_OOM, FC_INTERNAL, FC_CUDA_ERROR. */
 int fc_setup(fc_ctx *ctx, const fc_blocks *J);
 
 /* Replace the algebraic fixed stress of S~2 (Eq. FS_algebraic) by the
@@ -237,7 +239,12 @@ int fc_solve_adjoint(fc_ctx *ctx, int variant, const double *d_g, double *d_lamb
  * dJ/da arrives as entries sorted by face, DEVICE arrays: face_ptr (n_face+1,
  * int64) delimits the entries of each face; entry e is d J[row, col]/d a_f =
  * val with block[e] = 0 for T (row, col faces; comp unused) or 1 for Q2 (row a
- * face, (col, comp) = (node copy, component)).  Deterministic. */
+ * face, (col, comp) = (node copy, component)).  The entry arrays hold
+ * face_ptr[n_face] elements, owned by the caller.  Deterministic.
+ * Errors: FC_NOT_SETUP before fc_setup; FC_BAD_ARG for NULL arrays, a face_ptr
+ * that does not start at 0 or decreases, or an entry whose row, column, block
+ * or component lies outside the system (checked on the device; d_grad is then
+ * unspecified). */
 int fc_aperture_gradient(fc_ctx *ctx, const int64_t *d_face_ptr, const int8_t *d_block,
                          const int32_t *d_row, const int32_t *d_col, const int8_t *d_comp,
                          const double *d_val, const double *d_x, const double *d_lambda, double *d_grad);

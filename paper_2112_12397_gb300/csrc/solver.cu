@@ -292,10 +292,18 @@ AmgParams amg_params(const fc_options &o, bool pressure) {
   return p;
 }
 
-void check_bsr(const fc_bsr &m, int nbr, int nbc, int br, int bc, const char *name) {
+void check_bsr(const fc_bsr &m, int nbr, int nbc, int br, int bc, const char *name, cudaStream_t s) {
   bool ok = m.n_brows == nbr && m.n_bcols == nbc && m.br == br && m.bc == bc && m.nnzb >= 0 &&
             (m.nnzb == 0 || (m.d_col_idx && m.d_val)) && m.d_row_ptr;
   FS_REQUIRE(ok, FC_BAD_ARG, std::string("block ") + name + " has inconsistent sizes or null pointers");
+  BsrView<double> v;
+  v.nbr = m.n_brows; v.nbc = m.n_bcols; v.br = m.br; v.bc = m.bc; v.nnzb = m.nnzb;
+  v.rp = m.d_row_ptr; v.ci = m.d_col_idx; v.val = m.d_val;
+  const int bad = check_structure(v, s);
+  FS_REQUIRE(!(bad & 1), FC_BAD_ARG,
+             std::string("block ") + name + ": row pointers must run from 0 to nnzb without decreasing");
+  FS_REQUIRE(!(bad & 2), FC_BAD_ARG,
+             std::string("block ") + name + ": columns must lie in [0, n_bcols) and increase within each row");
 }
 
 template <typename TP>
@@ -891,13 +899,13 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     c->ready = false;
     const int nn = J->n_node, nf = J->n_face;
     FS_REQUIRE(nn > 0 && nf >= 0, FC_BAD_ARG, "n_node must be positive");
-    check_bsr(J->A, nn, nn, 3, 3, "A");
-    check_bsr(J->C1, nn, nf, 3, 3, "C1");
-    check_bsr(J->Q1, nn, nf, 3, 1, "Q1");
-    check_bsr(J->C2, nf, nn, 3, 3, "C2");
-    check_bsr(J->H, nf, nf, 3, 3, "H");
-    check_bsr(J->Q2, nf, nn, 1, 3, "Q2");
-    check_bsr(J->T, nf, nf, 1, 1, "T");
+    check_bsr(J->A, nn, nn, 3, 3, "A", c->s);
+    check_bsr(J->C1, nn, nf, 3, 3, "C1", c->s);
+    check_bsr(J->Q1, nn, nf, 3, 1, "Q1", c->s);
+    check_bsr(J->C2, nf, nn, 3, 3, "C2", c->s);
+    check_bsr(J->H, nf, nf, 3, 3, "H", c->s);
+    check_bsr(J->Q2, nf, nn, 1, 3, "Q2", c->s);
+    check_bsr(J->T, nf, nf, 1, 1, "T", c->s);
     NvtxRange nvtx("fc_setup");
     cudaStream_t s = c->s;
     FS_REQUIRE(!c->geo.omega || c->geo_n == nf, FC_BAD_ARG,
@@ -957,13 +965,13 @@ int fc_update(fc_ctx *c, const fc_blocks *J) {
     FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_update needs a completed fc_setup");
     const int nn = c->nn, nf = c->nf;
     FS_REQUIRE(J->n_node == nn && J->n_face == nf, FC_BAD_ARG, "fc_update: sizes differ from the last fc_setup");
-    check_bsr(J->A, nn, nn, 3, 3, "A");
-    check_bsr(J->C1, nn, nf, 3, 3, "C1");
-    check_bsr(J->Q1, nn, nf, 3, 1, "Q1");
-    check_bsr(J->C2, nf, nn, 3, 3, "C2");
-    check_bsr(J->H, nf, nf, 3, 3, "H");
-    check_bsr(J->Q2, nf, nn, 1, 3, "Q2");
-    check_bsr(J->T, nf, nf, 1, 1, "T");
+    check_bsr(J->A, nn, nn, 3, 3, "A", c->s);
+    check_bsr(J->C1, nn, nf, 3, 3, "C1", c->s);
+    check_bsr(J->Q1, nn, nf, 3, 1, "Q1", c->s);
+    check_bsr(J->C2, nf, nn, 3, 3, "C2", c->s);
+    check_bsr(J->H, nf, nf, 3, 3, "H", c->s);
+    check_bsr(J->Q2, nf, nn, 1, 3, "Q2", c->s);
+    check_bsr(J->T, nf, nf, 1, 1, "T", c->s);
     NvtxRange nvtx("fc_update");
     cudaStream_t s = c->s;
     fs::g_verbose = c->opt.verbose;
@@ -1190,16 +1198,31 @@ namespace {
 // grad[f] = - sum over the derivative entries e of face f of
 //   lambda_p[row_e] * val_e * x[col_e]   (x_p for T entries, x_u for Q2 entries)
 // one warp per face, lane-strided sums reduced in a fixed tree
-__global__ void k_aperture_gradient(int nf, const int64_t *fptr, const int8_t *block, const int *row,
+__global__ void k_check_face_ptr(int nf, const int64_t *fptr, int *flag) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    if ((f == 0 && fptr[0] != 0) || fptr[f + 1] < fptr[f]) atomicOr(flag, 1);
+  }
+}
+
+// entries whose indices fall outside the system are skipped and flagged
+__global__ void k_aperture_gradient(int nf, int nn, const int64_t *fptr, const int8_t *block, const int *row,
                                     const int *col, const int8_t *comp, const double *val, const double *x_u,
-                                    const double *x_p, const double *lam_p, double *grad) {
+                                    const double *x_p, const double *lam_p, double *grad, int *flag) {
   const int lane = threadIdx.x & 31;
   for (int64_t f = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; f < nf;
        f += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     double s = 0.0;
     for (int64_t e = fptr[f] + lane; e < fptr[f + 1]; e += 32) {
-      const double xv = block[e] == 0 ? x_p[col[e]] : x_u[3 * (int64_t)col[e] + comp[e]];
-      s += lam_p[row[e]] * val[e] * xv;
+      const int b = block[e], r = row[e], cl = col[e], cp = comp[e];
+      const bool ok = r >= 0 && r < nf &&
+                      ((b == 0 && cl >= 0 && cl < nf) || (b == 1 && cl >= 0 && cl < nn && cp >= 0 && cp < 3));
+      if (!ok) {
+        atomicOr(flag, 2);
+        continue;
+      }
+      const double xv = b == 0 ? x_p[cl] : x_u[3 * (int64_t)cl + cp];
+      s += lam_p[r] * val[e] * xv;
     }
     s = warp_sum(s);
     if (lane == 0) grad[f] = -s;
@@ -1214,11 +1237,22 @@ int fc_aperture_gradient(fc_ctx *c, const int64_t *face_ptr, const int8_t *block
   return run(c, [&]() {
     FS_REQUIRE(c->ready, FC_NOT_SETUP, "fc_setup has not completed");
     if (c->nf == 0) return FC_OK;
+    FS_REQUIRE(block && row && col && comp && val, FC_BAD_ARG, "aperture gradient: null entry arrays");
     const double *x_u = x, *x_p = x + c->nu + c->nt, *lam_p = lambda + c->nu + c->nt;
-    k_aperture_gradient<<<blocks_for((int64_t)c->nf * 32, 256, kSMs * 16), 256, 0, c->s>>>(
-        c->nf, face_ptr, block, row, col, comp, val, x_u, x_p, lam_p, grad);
+    DBuf<int> flag(1);
+    FS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), c->s));
+    k_check_face_ptr<<<blocks_for(c->nf, 256, kSMs * 8), 256, 0, c->s>>>(c->nf, face_ptr, flag.p);
     FS_LAUNCHED();
+    int h = 0;
+    FS_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     FS_CUDA(cudaStreamSynchronize(c->s));
+    FS_REQUIRE(!h, FC_BAD_ARG, "aperture gradient: face_ptr must start at 0 and not decrease");
+    k_aperture_gradient<<<blocks_for((int64_t)c->nf * 32, 256, kSMs * 16), 256, 0, c->s>>>(
+        c->nf, c->nn, face_ptr, block, row, col, comp, val, x_u, x_p, lam_p, grad, flag.p);
+    FS_LAUNCHED();
+    FS_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    FS_REQUIRE(!h, FC_BAD_ARG, "aperture gradient: an entry's row, column or component is out of range");
     return FC_OK;
   });
 }

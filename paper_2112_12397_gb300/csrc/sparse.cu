@@ -634,6 +634,55 @@ __global__ void k_diff_bits(const unsigned long long *a, const unsigned long lon
 }
 }  // namespace
 
+namespace {
+// row pointers: rp[0] = 0, non-decreasing, rp[nbr] = nnzb (flag bit 1)
+__global__ void k_check_rp(const int *rp, int nbr, int64_t nnzb, int *flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nbr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int v = rp[i];
+    bool ok = v >= 0 && (int64_t)v <= nnzb;
+    if (i == 0) ok = ok && v == 0;
+    if (i == nbr) ok = ok && (int64_t)v == nnzb;
+    if (i < nbr) ok = ok && rp[i + 1] >= v;
+    if (!ok) atomicOr(flag, 1);
+  }
+}
+// columns within [0, nbc), strictly increasing in each row (flag bit 2);
+// only run once the row pointers passed
+__global__ void k_check_ci(const int *rp, const int *ci, int nbr, int nbc, int *flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int prev = -1;
+    for (int e = rp[i]; e < rp[i + 1]; e++) {
+      const int c = ci[e];
+      if (c <= prev || c >= nbc) {
+        atomicOr(flag, 2);
+        break;
+      }
+      prev = c;
+    }
+  }
+}
+}  // namespace
+
+int check_structure(const BsrView<double> &A, cudaStream_t s) {
+  DBuf<int> f(1);
+  FS_CUDA(cudaMemsetAsync(f.p, 0, sizeof(int), s));
+  k_check_rp<<<blocks_for((int64_t)A.nbr + 1, 256, kSMs * 8), 256, 0, s>>>(A.rp, A.nbr, A.nnzb, f.p);
+  FS_LAUNCHED();
+  int h = 0;
+  FS_CUDA(cudaMemcpyAsync(&h, f.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  if (h) return 1;
+  if (A.nbr > 0 && A.nnzb > 0) {
+    k_check_ci<<<blocks_for(A.nbr, 128, kSMs * 16), 128, 0, s>>>(A.rp, A.ci, A.nbr, A.nbc, f.p);
+    FS_LAUNCHED();
+    FS_CUDA(cudaMemcpyAsync(&h, f.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+  }
+  return h;
+}
+
 bool same_values(const double *a, const double *b, int64_t n, cudaStream_t s) {
   if (n <= 0) return true;
   DBuf<int> d(1);

@@ -34,6 +34,12 @@ void spgemm_numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<doub
 // True when the n doubles at a and b are bitwise identical (device arrays).
 bool same_values(const double *a, const double *b, int64_t n, cudaStream_t s);
 
+// Validates a caller's block structure on the device before any kernel
+// indexes through it: 0 = valid; bit 1 = row pointers not 0 .. nnzb
+// non-decreasing; bit 2 = a column outside [0, nbc) or not strictly
+// increasing within its row (checked only when the row pointers are valid).
+int check_structure(const BsrView<double> &A, cudaStream_t s);
+
 // True when A and B have identical row pointers and column indices.
 bool same_pattern(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s);
 

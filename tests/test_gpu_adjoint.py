@@ -164,6 +164,34 @@ def test_aperture_gradient_kernel(fs):
     ctx.close()
 
 
+def test_aperture_gradient_rejects_malformed_entries(fs):
+    """Out-of-range rows, columns or components and a decreasing face_ptr
+    are reported as FC_BAD_ARG instead of being read."""
+    P = fracgen.generate("planes64", N=8, p_stick=0.4, p_slip=0.3, seed=5)
+    ctx = fs.context_for(P, fs.default_options(coarse_max=32, coarse_max_p=16))
+    rs = np.random.default_rng(1)
+    x, lam = cuda(rs.standard_normal(P.n)), cuda(rs.standard_normal(P.n))
+    grad = torch.zeros(P.n_face, dtype=torch.float64, device="cuda")
+    good = fs.device_dk(P)
+    q2 = int(torch.nonzero(good["block"] == 1)[0])
+    t = int(torch.nonzero(good["block"] == 0)[0])
+    cases = []
+    for key, e, v in (("row", t, P.n_face), ("col", t, -1), ("col", q2, P.n_node), ("comp", q2, 3)):
+        d = {k: a.clone() for k, a in good.items()}
+        d[key][e] = v
+        cases.append(d)
+    d = {k: a.clone() for k, a in good.items()}
+    d["face_ptr"][2], d["face_ptr"][3] = good["face_ptr"][3], good["face_ptr"][2] - 1
+    cases.append(d)
+    for d in cases:
+        with pytest.raises(fs.FcError):
+            ctx.aperture_gradient(d, x, lam, grad)
+    ctx.aperture_gradient(good, x, lam, grad)
+    ref = adjoint.aperture_gradient(P, x.cpu().numpy(), lam.cpu().numpy())
+    assert rel(grad.cpu().numpy(), ref) <= 1e-13
+    ctx.close()
+
+
 def test_aperture_gradient_matches_dense_adjoint_8cubed(fs):
     """8^3 case: forward and adjoint solved on the GPU, gradient against the
     oracle's dense adjoint gradient."""

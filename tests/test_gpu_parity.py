@@ -405,3 +405,34 @@ def test_context_reused_for_other_sizes(fs):
             if maxit == 400:
                 assert rr <= 1e-8
     ctx.close()
+
+
+def test_malformed_block_structure_is_rejected(fs):
+    """fc_setup checks the caller's row pointers and columns on the device
+    before any kernel indexes through them: an out-of-range column and a row
+    pointer array that does not end at nnzb are refused with FC_BAD_ARG, and
+    the context still takes a valid system afterwards."""
+    P = fracgen.generate("tiny8")
+    ctx = fs.Context(fs.default_options())
+    good = fs.device_blocks(P)
+    bad_col = dict(good)
+    rp, ci, val = good["A"][:3]
+    ci2 = ci.clone()
+    ci2[5] = P.n_node                                   # one column out of range
+    bad_col["A"] = (rp, ci2, val) + tuple(good["A"][3:])
+    with pytest.raises(fs.FcError) as e:
+        ctx.setup(bad_col, P.n_node, P.n_face)
+    assert e.value.code == fs.FC_BAD_ARG and "columns" in str(e.value)
+    bad_rp = dict(good)
+    rp2 = rp.clone()
+    rp2[-1] = rp2[-1] - 1                               # does not end at nnzb
+    bad_rp["A"] = (rp2, ci, val) + tuple(good["A"][3:])
+    with pytest.raises(fs.FcError) as e:
+        ctx.setup(bad_rp, P.n_node, P.n_face)
+    assert e.value.code == fs.FC_BAD_ARG and "row pointers" in str(e.value)
+    ctx.setup(good, P.n_node, P.n_face)
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    rc, it, rr = ctx.solve("tup", b, x, 1e-8, 200)
+    assert rr <= 1e-8
+    ctx.close()
