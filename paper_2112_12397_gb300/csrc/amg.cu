@@ -304,6 +304,7 @@ __global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, c
                           int cap, int *flag) {
   constexpr int BS = B * B;
   extern __shared__ int sh_agg[];
+  __shared__ double sh_sum[8][32 * BS];        // short rows: block sums per aggregate (at most 8 warps)
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   int *al = sh_agg + (size_t)wid * 3 * cap;   // aggregate of entry t (-1: none)
   int *fl = al + cap;                          // 1 if entry t is the first with its aggregate
@@ -335,37 +336,47 @@ __global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, c
         continue;
       }
       // the B x B entries of the row's nu blocks of P, spread over the lanes
-      // (unit k: aggregate number k / BS in lane order, entry k % BS); each
-      // entry sums its aggregate's blocks in row order, as a whole block would
+      // (unit k: aggregate number k / BS in lane order, entry k % BS).  First
+      // each entry of an aggregate's block sum, in row order, as a whole
+      // block would; then D_i^-1 times the scaled sums
       const int o = rpP[i];
       const double *Di = Dinv + i * BS;
       const int ai = agg[i];
+      const double isz_first = first ? 1.0 / sqrt((double)asize[a]) : 0.0;
+      double *sums = sh_sum[wid];
       for (int k0 = 0; k0 < nu * BS; k0 += 32) {
         const int k = k0 + lane;
         const int fi = min(k / BS, nu - 1), e = k - (k / BS) * BS;
-        // lane holding the fi-th first entry
+        unsigned m = firsts;   // lane holding the fi-th first entry
+        for (int t = 0; t < fi; t++) m &= m - 1;
+        const unsigned fsame = __shfl_sync(0xffffffffu, same, __ffs(m) - 1);
+        if (k < nu * BS) {
+          double acc = 0.0;
+          for (unsigned mu = fsame; mu; mu &= mu - 1) acc += S.val[(int64_t)(s0 + __ffs(mu) - 1) * BS + e];
+          sums[k] = acc;
+        }
+      }
+      __syncwarp();
+      for (int k0 = 0; k0 < nu * BS; k0 += 32) {
+        const int k = k0 + lane;
+        const int fi = min(k / BS, nu - 1), e = k - (k / BS) * BS;
         unsigned m = firsts;
         for (int t = 0; t < fi; t++) m &= m - 1;
         const int fl = __ffs(m) - 1;
         const int fa = __shfl_sync(0xffffffffu, a, fl);
-        const unsigned fsame = __shfl_sync(0xffffffffu, same, fl);
         const int fr = __shfl_sync(0xffffffffu, r, fl);
+        const double isz = __shfl_sync(0xffffffffu, isz_first, fl);
         if (k < nu * BS) {
           const int rr = e / B, cc = e - rr * B;
-          const double isz = 1.0 / sqrt((double)asize[fa]);
           double mm = 0.0;
 #pragma unroll
-          for (int q = 0; q < B; q++) {
-            double acc = 0.0;
-            for (unsigned mu = fsame; mu; mu &= mu - 1)
-              acc += S.val[(int64_t)(s0 + __ffs(mu) - 1) * BS + q * B + cc];
-            mm += Di[rr * B + q] * (acc * isz);
-          }
+          for (int q = 0; q < B; q++) mm += Di[rr * B + q] * (sums[fi * BS + q * B + cc] * isz);
           const double pt = (ai == fa && rr == cc) ? isz : 0.0;
           valP[(int64_t)(o + fr) * BS + e] = pt - omega * mm;
           if (e == 0) ciP[o + fr] = fa;
         }
       }
+      __syncwarp();
       continue;
     }
     for (int t = lane; t < len; t += 32) al[t] = agg[S.ci[s0 + t]];

@@ -142,18 +142,24 @@ struct WarpHash {
   int *keys;   // kHashCap
   int *list;   // kListCap
   int *count;  // 1
+  int mask;    // slots in use - 1 (a power of two minus one)
 };
 
-__device__ inline void hash_clear(WarpHash &h, int lane) {
-  for (int k = lane; k < kHashCap; k += 32) h.keys[k] = -1;
+// use the smallest power-of-two table of at least 2 n slots (n keys at most;
+// 32 at least, kHashCap at most) and empty it
+__device__ inline void hash_clear(WarpHash &h, int lane, int n) {
+  int cap = 32;
+  while (cap < 2 * n && cap < kHashCap) cap <<= 1;
+  h.mask = cap - 1;
+  for (int k = lane; k < cap; k += 32) h.keys[k] = -1;
   if (lane == 0) *h.count = 0;
   __syncwarp();
 }
 
 // returns false on overflow
 __device__ inline bool hash_insert(WarpHash &h, int key) {
-  unsigned slot = ((unsigned)key * 2654435761u) & (kHashCap - 1);
-  for (int probe = 0; probe < kHashCap; probe++) {
+  unsigned slot = ((unsigned)key * 2654435761u) & h.mask;
+  for (int probe = 0; probe <= h.mask; probe++) {
     int old = atomicCAS(h.keys + slot, -1, key);
     if (old == -1) {
       int pos = atomicAdd(h.count, 1);
@@ -162,7 +168,7 @@ __device__ inline bool hash_insert(WarpHash &h, int key) {
       return true;
     }
     if (old == key) return true;
-    slot = (slot + 1) & (kHashCap - 1);
+    slot = (slot + 1) & h.mask;
   }
   return false;
 }
@@ -216,23 +222,37 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   __shared__ int s_keys[kWarpsPerBlock][kHashCap];
   __shared__ int s_list[kWarpsPerBlock][kListCap];
   __shared__ int s_pre[kWarpsPerBlock][kSymPre + 1];
+  __shared__ int s_kb[kWarpsPerBlock][kSymPre];
   __shared__ int s_cnt[kWarpsPerBlock];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpHash h{s_keys[wid], s_list[wid], &s_cnt[wid]};
-  int *pre = s_pre[wid];
+  WarpHash h{s_keys[wid], s_list[wid], &s_cnt[wid], kHashCap - 1};
+  int *pre = s_pre[wid], *kb = s_kb[wid];
   const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerBlock;
   for (int64_t i = blockIdx.x * (int64_t)kWarpsPerBlock + wid; i < A.nbr; i += nwarps) {
-    hash_clear(h, lane);
     bool ok = true;
     const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
     if (na <= kSymPre) {
       const int T = row_product_prefix(A, B, a0, na, pre, lane);
-      for (int t = lane; t < T; t += 32) {
-        const int x = product_entry(pre, na, t);
-        const int k = A.ci[a0 + x];
-        ok &= hash_insert(h, B.ci[B.rp[k] + (t - pre[x])]);
+      for (int x = lane; x < na; x += 32) kb[x] = B.rp[A.ci[a0 + x]];
+      hash_clear(h, lane, T);
+      // four products per lane at a time: their column loads issue together
+      for (int t0 = 0; t0 < T; t0 += 128) {
+        int cv[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int t = t0 + u * 32 + lane;
+          cv[u] = -1;
+          if (t < T) {
+            const int x = product_entry(pre, na, t);
+            cv[u] = B.ci[kb[x] + (t - pre[x])];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (cv[u] >= 0) ok &= hash_insert(h, cv[u]);
       }
     } else {
+      hash_clear(h, lane, kHashCap);
       for (int e = a0; e < a0 + na; e++) {
         int k = A.ci[e];
         for (int f = B.rp[k] + lane; f < B.rp[k + 1]; f += 32) ok &= hash_insert(h, B.ci[f]);
@@ -261,64 +281,55 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
-// Numeric pass with the products of a row sorted by output slot.  A group
-// of W warps takes one row of C; warp w of the group owns the slots
-// [w ceil(cn / W), (w + 1) ceil(cn / W)) and, in it, lane l the units
-// u = l + 32 k (k < KU), unit = (slot p, block row r), summed in registers.
-// The products (e, f) of the row (entries of A's row, then of B's matching
-// row) are taken in their fixed enumeration order, in segments of capT:
-// each product gets its slot (the position of B's column among C's sorted
-// columns), products outside the warp's slots are dropped, a stable counting
-// sort groups the rest by slot, and each lane adds the segment's products of
-// its units in order.  Every entry of C is the same ordered sum on every run
-// (no atomics on values), all lanes work even when B's rows hold a handful
-// of blocks, and the shared memory per warp does not grow with the row's
-// product count.  W > 1 splits long rows of C over a whole block (one group
-// per block).  Rows with more slots than W warps hold or longer A rows than
-// capA stay pending for the chunked kernel.
-template <int BR, int BK, int BC, int KU, int W>
+// Numeric pass with the products of a row sorted by output slot and split
+// evenly over the lanes.  One warp per row of C (the rows of a length class,
+// from a list); the row's slot sums live in shared memory.  The row's
+// products (e, f) (entries of A's row, then of B's matching row) are taken
+// in their fixed enumeration order in segments of capT; each gets its slot
+// (the position of B's column among C's sorted columns) and a stable
+// counting sort groups the segment by slot.  The sorted list is then cut
+// into 32 equal runs, one per lane: a lane adds its run's products in order
+// into a register block, starting from the slot's sum so far when the slot
+// begins in its run (the lane then owns it) and from zero when the slot
+// continues from the lane before; the owner then adds those continuations
+// in lane order.  Every FP64 instruction thus runs on a full warp (the FP64
+// pipe executes a warp instruction whole, active lanes or not), and every
+// entry of C is the same ordered sum on every run, with no value atomics.
+constexpr int kSegT = 192;   // products per segment of the numeric pass
+
+template <int BR, int BK, int BC, bool GS>
 __global__ void __launch_bounds__(256)
-    k_spgemm_numeric_seg(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC, double *valC,
-                         int *pending, int capA, int capT, int *bad) {
-  constexpr int BS = BR * BC;
-  constexpr int capC = (32 * KU) / BR;      // slots per warp
-  constexpr int capR = capC * W;            // slots per row
-  extern __shared__ int ismem[];
+    k_spgemm_numeric_mp(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC, double *valC,
+                        const int *rows, const int *nrows, int capA, int capC, int *bad) {
+  constexpr int BS = BR * BC, AS = BR * BK, BB = BK * BC, capT = kSegT, kPL = kSegT / 32;
+  extern __shared__ double dsm[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  const int G = wpb / W;                    // row groups per block (1 when W > 1)
-  const int g = wid / W, wr = wid - g * W;
-  // per group: cols (capR), pre (capA + 1); per warp: start, off, products
-  const int per_group = capR + capA + 1;
-  const int per_warp = 2 * capC + 1 + 4 * capT;
-  int *cols = ismem + (size_t)g * per_group;
-  int *pre = cols + capR;
-  int *start = ismem + (size_t)G * per_group + (size_t)wid * per_warp;   // capC + 1
-  int *off = start + capC + 1;    // capC
-  int *pl = off + capC;           // capT: local slot of a kept segment product
-  int *ee = pl + capT;            // capT: its A entry
-  int *ff = ee + capT;            // capT: its B entry
-  int *srt = ff + capT;           // capT: kept products sorted by slot
+  const int dw = (GS ? 0 : capC) + 32;                   // doubles per warp, in blocks
+  double *carry = dsm + (size_t)wid * dw * BS;            // 32 continuation sums
+  int *cols = reinterpret_cast<int *>(dsm + (size_t)wpb * dw * BS) +
+              (size_t)wid * (3 * capC + 2 * capA + 2 + 4 * capT);
+  int *pre = cols + capC;          // capA + 1
+  int *kb = pre + capA + 1;        // capA: start of B's row for each A entry
+  int *start = kb + capA;          // capC + 1
+  int *off = start + capC + 1;     // capC
+  int *pl = off + capC;            // capT: slot of a segment product
+  int *ee = pl + capT;             // capT: its A entry
+  int *ff = ee + capT;             // capT: its B entry
+  int *srt = ff + capT;            // capT: the products sorted by slot
   const unsigned lt = (1u << lane) - 1u;
-  auto sync = [&]() {
-    if constexpr (W == 1) __syncwarp();
-    else __syncthreads();
-  };
-  for (int64_t i = blockIdx.x * (int64_t)G + g; i < A.nbr; i += (int64_t)gridDim.x * G) {
-    if (!pending[i]) continue;
-    const int cs = rpC[i], cn = rpC[i + 1] - cs;
+  const int n = *nrows;
+  for (int w = blockIdx.x * wpb + wid; w < n; w += gridDim.x * wpb) {
+    const int i = rows[w];
+    const int cs = rpC[i], p_n = rpC[i + 1] - cs;
     const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
-    const int chunk = (cn + W - 1) / W;
-    if (chunk > capC || na > capA) continue;
-    if (wr == 0) row_product_prefix(A, B, a0, na, pre, lane);
-    for (int t = wr * 32 + lane; t < cn; t += 32 * W) cols[t] = ciC[cs + t];
-    sync();
+    // the slot sums: in shared memory, or (long rows) the row of C itself
+    double *sums = GS ? valC + (int64_t)cs * BS : carry + 32 * BS;
+    row_product_prefix(A, B, a0, na, pre, lane);
+    for (int x = lane; x < na; x += 32) kb[x] = B.rp[A.ci[a0 + x]];
+    for (int t = lane; t < p_n; t += 32) cols[t] = ciC[cs + t];
+    __syncwarp();
     const int T = pre[na];
-    const int p_lo = wr * chunk, p_n = max(0, min(cn, p_lo + chunk) - p_lo);
-    double acc[KU][BC];
-#pragma unroll
-    for (int k = 0; k < KU; k++)
-#pragma unroll
-      for (int cc = 0; cc < BC; cc++) acc[k][cc] = 0.0;
+    for (int x = lane; x < p_n * BS; x += 32) sums[x] = 0.0;
     bool okp = true;
     for (int t0 = 0; t0 < T; t0 += capT) {
       const int tn = min(capT, T - t0);
@@ -327,32 +338,38 @@ __global__ void __launch_bounds__(256)
         off[t] = 0;
       }
       __syncwarp();
-      // slots of the segment's products; the warp keeps those in its range,
-      // in enumeration order (ballot + prefix count)
-      int kept = 0;
-      for (int c0 = 0; c0 < tn; c0 += 32) {
-        const int tl = c0 + lane;
-        int e = 0, f = 0, p = -1;
+      // the segment's products, kPL per lane, their loads issued together
+      int ev[kPL], fv[kPL], cv[kPL];
+#pragma unroll
+      for (int u = 0; u < kPL; u++) {
+        const int tl = u * 32 + lane;
+        ev[u] = 0;
+        fv[u] = 0;
         if (tl < tn) {
           const int t = t0 + tl;
           const int x = product_entry(pre, na, t);
-          e = a0 + x;
-          f = B.rp[A.ci[e]] + (t - pre[x]);
-          p = find_sorted(cols, cn, B.ci[f]);
-          if (p < 0 && tl < tn) okp = false;   // cannot happen: the symbolic pass saw every column
-          p -= p_lo;
+          ev[u] = a0 + x;
+          fv[u] = kb[x] + (t - pre[x]);
         }
-        const bool keep = tl < tn && p >= 0 && p < p_n;
-        const unsigned km = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          const int pos = kept + __popc(km & lt);
-          ee[pos] = e;
-          ff[pos] = f;
-          pl[pos] = p;
+      }
+#pragma unroll
+      for (int u = 0; u < kPL; u++) cv[u] = u * 32 + lane < tn ? B.ci[fv[u]] : 0;
+#pragma unroll
+      for (int u = 0; u < kPL; u++) {
+        const int tl = u * 32 + lane;
+        if (tl < tn) {
+          int p = find_sorted(cols, p_n, cv[u]);
+          if (p < 0) {   // cannot happen: the symbolic pass saw every column
+            okp = false;
+            p = 0;
+          }
+          ee[tl] = ev[u];
+          ff[tl] = fv[u];
+          pl[tl] = p;
           atomicAdd(&start[p], 1);
         }
-        kept += __popc(km);
       }
+      const int kept = tn;
       __syncwarp();
       int run = 0;
       for (int x0 = 0; x0 < p_n; x0 += 32) {
@@ -385,25 +402,79 @@ __global__ void __launch_bounds__(256)
         if (act && (m & lt) == 0) off[p] = o + __popc(m);
         __syncwarp();
       }
+      // this lane's run of the sorted products
+      const int q_lo = (lane * kept) >> 5, q_hi = ((lane + 1) * kept) >> 5;
+      int cur = -1;
+      bool own = false;
+      if (q_lo < q_hi) {
+        double acc[BS], av[AS], bv[BB], an[AS], bn[BB];
+        int tl = srt[q_lo];
+        cur = pl[tl];
+        own = start[cur] == q_lo;
 #pragma unroll
-      for (int k = 0; k < KU; k++) {
-        const int u = lane + 32 * k;
-        if (u < p_n * BR) {
-          const int p = u / BR, r = u - p * BR;
-          const int q1 = start[p + 1];
-#pragma unroll 2
-          for (int q = start[p]; q < q1; q++) {
-            const int tl = srt[q];
-            const double *a = A.val + (int64_t)ee[tl] * BR * BK + r * BK;
-            const double *b = B.val + (int64_t)ff[tl] * BK * BC;
-            double av[BK];
+        for (int x = 0; x < BS; x++) acc[x] = own ? sums[cur * BS + x] : 0.0;
+        {
+          const double *a = A.val + (int64_t)ee[tl] * AS, *b = B.val + (int64_t)ff[tl] * BB;
 #pragma unroll
-            for (int tt = 0; tt < BK; tt++) av[tt] = a[tt];
-            // straight FMA accumulation: the FP64 pipe bounds this kernel
+          for (int x = 0; x < AS; x++) av[x] = a[x];
 #pragma unroll
-            for (int cc = 0; cc < BC; cc++)
+          for (int x = 0; x < BB; x++) bv[x] = b[x];
+        }
+        for (int q = q_lo; q < q_hi; q++) {
+          int tn2 = 0;
+          if (q + 1 < q_hi) {   // fetch the next product's blocks while this one is summed
+            tn2 = srt[q + 1];
+            const double *a = A.val + (int64_t)ee[tn2] * AS, *b = B.val + (int64_t)ff[tn2] * BB;
 #pragma unroll
-              for (int tt = 0; tt < BK; tt++) acc[k][cc] = fma(av[tt], b[tt * BC + cc], acc[k][cc]);
+            for (int x = 0; x < AS; x++) an[x] = a[x];
+#pragma unroll
+            for (int x = 0; x < BB; x++) bn[x] = b[x];
+          }
+          const int p = pl[tl];
+          if (p != cur) {   // a new slot begins here: this lane owns it
+            if (own) {
+#pragma unroll
+              for (int x = 0; x < BS; x++) sums[cur * BS + x] = acc[x];
+            } else {
+#pragma unroll
+              for (int x = 0; x < BS; x++) carry[lane * BS + x] = acc[x];
+            }
+            cur = p;
+            own = true;
+#pragma unroll
+            for (int x = 0; x < BS; x++) acc[x] = sums[cur * BS + x];
+          }
+#pragma unroll
+          for (int r = 0; r < BR; r++)
+#pragma unroll
+            for (int k = 0; k < BK; k++)
+#pragma unroll
+              for (int c = 0; c < BC; c++) acc[r * BC + c] = fma(av[r * BK + k], bv[k * BC + c], acc[r * BC + c]);
+          tl = tn2;
+#pragma unroll
+          for (int x = 0; x < AS; x++) av[x] = an[x];
+#pragma unroll
+          for (int x = 0; x < BB; x++) bv[x] = bn[x];
+        }
+        if (own) {
+#pragma unroll
+          for (int x = 0; x < BS; x++) sums[cur * BS + x] = acc[x];
+        } else {
+#pragma unroll
+          for (int x = 0; x < BS; x++) carry[lane * BS + x] = acc[x];
+        }
+      }
+      __syncwarp();
+      // the owner of the run's last slot adds the continuations of the
+      // following lanes, in lane order
+      if (own) {
+        const int end = start[cur + 1];
+        for (int l = lane + 1; l < 32; l++) {
+          const int lo = (l * kept) >> 5;
+          if (lo >= end) break;
+          if (((l + 1) * kept) >> 5 > lo) {
+#pragma unroll
+            for (int x = 0; x < BS; x++) sums[cur * BS + x] += carry[l * BS + x];
           }
         }
       }
@@ -411,19 +482,35 @@ __global__ void __launch_bounds__(256)
     }
     if (!__all_sync(0xffffffffu, okp)) {
       if (lane == 0) atomicExch(bad, 1);
-    } else {
-#pragma unroll
-      for (int k = 0; k < KU; k++) {
-        const int u = lane + 32 * k;
-        if (u < p_n * BR) {
-          const int p = u / BR, r = u - p * BR;
-#pragma unroll
-          for (int cc = 0; cc < BC; cc++) valC[(int64_t)(cs + p_lo + p) * BS + r * BC + cc] = acc[k][cc];
-        }
-      }
+    } else if (!GS) {
+      for (int x = lane; x < p_n * BS; x += 32) valC[(int64_t)cs * BS + x] = sums[x];
     }
-    sync();
-    if (wr == 0 && lane == 0) pending[i] = 0;
+    __syncwarp();
+  }
+}
+
+// Length classes of the rows of C for the numeric pass: class c takes rows
+// with at most caps[c] columns and an A row of at most capa[c] entries;
+// rows beyond the last class stay pending for the chunked kernel.
+struct RowClasses {
+  int n;
+  int caps[3], capa[3];
+};
+
+__global__ void k_classify_rows(const int *rpA, const int *rpC, int nbr, RowClasses rc, int *lists, int *counts,
+                                int *pending) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int cn = rpC[i + 1] - rpC[i], na = rpA[i + 1] - rpA[i];
+    int c = 0;
+    while (c < rc.n && (cn > rc.caps[c] || na > rc.capa[c])) c++;
+    if (c < rc.n) {
+      const int pos = atomicAdd(counts + c, 1);
+      lists[(int64_t)c * nbr + pos] = (int)i;
+      pending[i] = 0;
+    } else {
+      pending[i] = 1;
+    }
   }
 }
 
@@ -540,19 +627,17 @@ __global__ void k_max_pending_len(const int *rp, int n, const int *pending, int 
   atomicMax(out, m);
 }
 
-template <int BR, int BK, int BC, int KU, int W>
-void launch_seg(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, int *pending, int *flags,
-                cudaStream_t s) {
-  // a block per row (W > 1) also takes long rows of A (coarse restrictions)
-  const int capA = W == 1 ? 512 : 4096, capT = 192;
-  const int wpb = W == 1 ? 8 : W;
-  const int G = wpb / W;
-  constexpr int capC = (32 * KU) / BR;
-  const size_t ints = (size_t)G * (capC * W + capA + 1) + (size_t)wpb * (2 * capC + 1 + 4 * capT);
-  const size_t shm = ints * sizeof(int);
-  auto kern = k_spgemm_numeric_seg<BR, BK, BC, KU, W>;
+template <int BR, int BK, int BC, bool GS>
+void launch_mp(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, const int *rows,
+               const int *nrows, int capC, int capA, int *flags, cudaStream_t s) {
+  const int wpb = 8;
+  const size_t dbl = (size_t)wpb * ((GS ? 0 : capC) + 32) * BR * BC;
+  const size_t ints = (size_t)wpb * (3 * capC + 2 * capA + 2 + 4 * kSegT);
+  const size_t shm = dbl * sizeof(double) + ints * sizeof(int);
+  const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(225 * 1024) / shm));
+  auto kern = k_spgemm_numeric_mp<BR, BK, BC, GS>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  kern<<<kSMs * (W == 1 ? 8 : 2), wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, pending, capA, capT, flags);
+  kern<<<kSMs * per_sm, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, rows, nrows, capA, capC, flags);
   FS_LAUNCHED();
 }
 
@@ -560,16 +645,20 @@ template <int BR, int BK, int BC>
 void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s) {
   constexpr int BS = BR * BC;
   if (C.nbr == 0) return;
-  DBuf<int> pending(C.nbr), flags(2);
-  FS_CUDA(cudaMemsetAsync(pending.p, 1, sizeof(int) * C.nbr, s));   // nonzero = pending
+  // three length classes of C rows (columns, A-row entries): short rows sum
+  // in shared memory at two blocks per SM; medium and long rows sum in the
+  // row of C itself, which keeps eight or more warps per SM
+  const RowClasses rc{3, {64, 160, 768}, {256, 512, 1024}};
+  DBuf<int> pending(C.nbr), flags(2), lists((size_t)rc.n * C.nbr), counts(rc.n);
   FS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
-  // segmented sorted-product kernel in tiers of units per lane (KU = 4 keeps
-  // the register accumulators small for the common short rows; KU = 9 takes
-  // C rows up to 96 block columns per warp; eight warps per row take rows up
-  // to 768 block columns): A-row entries capA, products per segment capT
-  launch_seg<BR, BK, BC, 4, 1>(A, B, C, pending.p, flags.p, s);
-  launch_seg<BR, BK, BC, 9, 1>(A, B, C, pending.p, flags.p, s);
-  launch_seg<BR, BK, BC, 9, 8>(A, B, C, pending.p, flags.p, s);   // long rows: a block per row
+  FS_CUDA(cudaMemsetAsync(counts.p, 0, rc.n * sizeof(int), s));
+  k_classify_rows<<<blocks_for(C.nbr, 256, kSMs * 8), 256, 0, s>>>(A.rp, C.rp.p, C.nbr, rc, lists.p, counts.p,
+                                                                    pending.p);
+  FS_LAUNCHED();
+  launch_mp<BR, BK, BC, false>(A, B, C, lists.p, counts.p, rc.caps[0], rc.capa[0], flags.p, s);
+  for (int c = 1; c < rc.n; c++)
+    launch_mp<BR, BK, BC, true>(A, B, C, lists.p + (size_t)c * C.nbr, counts.p + c, rc.caps[c], rc.capa[c],
+                                flags.p, s);
   // rows beyond the tiers (very long rows of A or many products): longest C row among them
   k_max_pending_len<<<blocks_for(C.nbr, 256, kSMs * 4), 256, 0, s>>>(C.rp.p, C.nbr, pending.p, flags.p + 1);
   FS_LAUNCHED();
