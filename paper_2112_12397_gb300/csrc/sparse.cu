@@ -499,16 +499,27 @@ struct RowClasses {
 
 __global__ void k_classify_rows(const int *rpA, const int *rpC, int nbr, RowClasses rc, int *lists, int *counts,
                                 int *pending) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbr;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int cn = rpC[i + 1] - rpC[i], na = rpA[i + 1] - rpA[i];
-    int c = 0;
-    while (c < rc.n && (cn > rc.caps[c] || na > rc.capa[c])) c++;
+  const int lane = threadIdx.x & 31;
+  // whole warps iterate (the grid stride is a multiple of 32); the lanes of
+  // one class take their list positions with one atomic
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < nbr;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    int c = rc.n + 1;   // no row
+    if (i < nbr) {
+      const int cn = rpC[i + 1] - rpC[i], na = rpA[i + 1] - rpA[i];
+      c = 0;
+      while (c < rc.n && (cn > rc.caps[c] || na > rc.capa[c])) c++;
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (c < rc.n && lane == leader) base = atomicAdd(counts + c, __popc(same));
+    base = __shfl_sync(0xffffffffu, base, leader);
     if (c < rc.n) {
-      const int pos = atomicAdd(counts + c, 1);
-      lists[(int64_t)c * nbr + pos] = (int)i;
+      lists[(int64_t)c * nbr + base + __popc(same & ((1u << lane) - 1u))] = (int)i;
       pending[i] = 0;
-    } else {
+    } else if (i < nbr) {
       pending[i] = 1;
     }
   }
@@ -847,33 +858,125 @@ Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStrea
 
 // ============================================================ sparse add
 namespace {
-__global__ void k_spadd(BsrView<double> A, BsrView<double> B, double alpha, double beta, int pass,
-                        int *cnt, const int *rpC, int *ciC, double *valC) {
+// number of sorted columns ci[lo..hi) below c, and whether c is among them
+__device__ inline int rank_below(const int *ci, int lo, int hi, int c, bool &found) {
+  int a = lo, b = hi;
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (ci[m] < c) a = m + 1;
+    else b = m;
+  }
+  found = a < hi && ci[a] == c;
+  return a - lo;
+}
+
+// C = alpha A + beta B on the union pattern, one warp per block row.  With
+// m(k) = the entries of B before entry k whose column A lacks, entry t of
+// A's row lands at t + m(rank of its column in B's row), and an entry k of B
+// whose column A lacks at (rank of its column in A's row) + m(k).  A row of
+// B that is empty (most rows: B is the fracture coupling) is a straight copy;
+// rows of B longer than kAddB entries are merged by one lane.  Each value is
+// (0 + alpha a) + beta b, with absent terms skipped.
+constexpr int kAddB = 64;
+
+__global__ void __launch_bounds__(256)
+    k_spadd(BsrView<double> A, BsrView<double> B, double alpha, double beta, int pass, int *cnt,
+            const int *rpC, int *ciC, double *valC) {
+  __shared__ int s_m[8][kAddB + 1];
   const int bs = A.br * A.bc;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.nbr;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int a = A.rp[i], ae = A.rp[i + 1], b = B.rp[i], be = B.rp[i + 1];
-    int n = 0;
-    int o = pass ? rpC[i] : 0;
-    while (a < ae || b < be) {
-      int ca = a < ae ? A.ci[a] : INT32_MAX;
-      int cb = b < be ? B.ci[b] : INT32_MAX;
-      int c = ca < cb ? ca : cb;
-      if (pass) {
-        ciC[o + n] = c;
-        double *dst = valC + (int64_t)(o + n) * bs;
-        for (int q = 0; q < bs; q++) {
-          double v = 0.0;
-          if (ca == c) v += alpha * A.val[(int64_t)a * bs + q];
-          if (cb == c) v += beta * B.val[(int64_t)b * bs + q];
-          dst[q] = v;
-        }
+  const int lane = threadIdx.x & 31;
+  int *m = s_m[threadIdx.x >> 5];
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < A.nbr; i += nw) {
+    const int a0 = A.rp[i], na = A.rp[i + 1] - a0, b0 = B.rp[i], nb = B.rp[i + 1] - b0;
+    const int o = pass ? rpC[i] : 0;
+    if (nb == 0) {
+      if (!pass) {
+        if (lane == 0) cnt[i] = na;
+        continue;
       }
-      if (ca == c) a++;
-      if (cb == c) b++;
-      n++;
+      for (int t = lane; t < na; t += 32) ciC[o + t] = A.ci[a0 + t];
+      for (int64_t q = lane; q < (int64_t)na * bs; q += 32)
+        valC[(int64_t)o * bs + q] = 0.0 + alpha * A.val[(int64_t)a0 * bs + q];
+      continue;
     }
-    if (!pass) cnt[i] = n;
+    if (nb > kAddB) {   // long rows of B: a sequential merge
+      if (lane == 0) {
+        int a = a0, ae = a0 + na, b = b0, be = b0 + nb, n = 0;
+        while (a < ae || b < be) {
+          const int ca = a < ae ? A.ci[a] : INT32_MAX, cb = b < be ? B.ci[b] : INT32_MAX;
+          const int c = ca < cb ? ca : cb;
+          if (pass) {
+            ciC[o + n] = c;
+            for (int q = 0; q < bs; q++) {
+              double v = 0.0;
+              if (ca == c) v += alpha * A.val[(int64_t)a * bs + q];
+              if (cb == c) v += beta * B.val[(int64_t)b * bs + q];
+              valC[(int64_t)(o + n) * bs + q] = v;
+            }
+          }
+          if (ca == c) a++;
+          if (cb == c) b++;
+          n++;
+        }
+        if (!pass) cnt[i] = n;
+      }
+      __syncwarp();
+      continue;
+    }
+    // m: exclusive prefix over B's row of "column absent from A"
+    int carry = 0;
+    for (int k0 = 0; k0 < nb; k0 += 32) {
+      const int k = k0 + lane;
+      int absent = 0;
+      if (k < nb) {
+        bool f;
+        rank_below(A.ci, a0, a0 + na, B.ci[b0 + k], f);
+        absent = !f;
+      }
+      int inc = absent;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+      }
+      if (k < nb) m[k] = carry + inc - absent;
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) m[nb] = carry;
+    __syncwarp();
+    if (!pass) {
+      if (lane == 0) cnt[i] = na + m[nb];
+      __syncwarp();
+      continue;
+    }
+    for (int t = lane; t < na; t += 32) {
+      const int c = A.ci[a0 + t];
+      bool f;
+      const int r = rank_below(B.ci, b0, b0 + nb, c, f);
+      const int pos = o + t + m[r];
+      ciC[pos] = c;
+      for (int q = 0; q < bs; q++) {
+        double v = 0.0;
+        v += alpha * A.val[(int64_t)(a0 + t) * bs + q];
+        if (f) v += beta * B.val[(int64_t)(b0 + r) * bs + q];
+        valC[(int64_t)pos * bs + q] = v;
+      }
+    }
+    for (int k = lane; k < nb; k += 32) {
+      const int c = B.ci[b0 + k];
+      bool f;
+      const int r = rank_below(A.ci, a0, a0 + na, c, f);
+      if (f) continue;
+      const int pos = o + r + m[k];
+      ciC[pos] = c;
+      for (int q = 0; q < bs; q++) {
+        double v = 0.0;
+        v += beta * B.val[(int64_t)(b0 + k) * bs + q];
+        valC[(int64_t)pos * bs + q] = v;
+      }
+    }
+    __syncwarp();
   }
 }
 }  // namespace
@@ -886,9 +989,9 @@ Bsr<double> spadd(const BsrView<double> &A, const BsrView<double> &B, double alp
   C.shape(A.nbr, A.nbc, A.br, A.bc);
   C.rp.alloc(A.nbr + 1);
   DBuf<int> cnt(A.nbr + 1);
-  const int grid = blocks_for(A.nbr, 128, kSMs * 8);
+  const int grid = blocks_for((int64_t)A.nbr * 32, 256, kSMs * 16);
   if (A.nbr > 0) {
-    k_spadd<<<grid, 128, 0, s>>>(A, B, alpha, beta, 0, cnt.p, nullptr, nullptr, nullptr);
+    k_spadd<<<grid, 256, 0, s>>>(A, B, alpha, beta, 0, cnt.p, nullptr, nullptr, nullptr);
     FS_LAUNCHED();
   }
   int64_t nnz = exclusive_scan(cnt.p, C.rp.p, A.nbr, s);
@@ -896,7 +999,7 @@ Bsr<double> spadd(const BsrView<double> &A, const BsrView<double> &B, double alp
   C.ci.alloc(nnz);
   C.val.alloc(nnz * C.br * C.bc);
   if (nnz) {
-    k_spadd<<<grid, 128, 0, s>>>(A, B, alpha, beta, 1, nullptr, C.rp.p, C.ci.p, C.val.p);
+    k_spadd<<<grid, 256, 0, s>>>(A, B, alpha, beta, 1, nullptr, C.rp.p, C.ci.p, C.val.p);
     FS_LAUNCHED();
   }
   FS_CUDA(cudaStreamSynchronize(s));

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(BsrView<TA> A, const TX *__res
   if (valid) {
     const int s = __ldg(A.rp + row), e = __ldg(A.rp + row + 1);
     // each lane takes whole blocks: no index arithmetic per scalar entry
-#pragma unroll 2
+#pragma unroll 4
     for (int b = s + lane; b < e; b += G) {
       const int col = __ldg(A.ci + b);
       TA a[BS];
