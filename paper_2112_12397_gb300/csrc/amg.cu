@@ -736,10 +736,20 @@ __global__ void k_power_scale(TP *v, const TP *w, int64_t n, const double *ww, c
     v[k] = (TP)(a * (double)w[k]);
 }
 
-// lambda of D^-1 S by normalised power steps on the cycle-precision operator;
-// norms in double on the device, one host read at the end
-template <int B, typename TP>
-double power_lambda(const SellView<TP> &S, const TP *Dinv, uint64_t seed, int level, int steps, cudaStream_t s) {
+template <int B, typename TP, typename Epi>
+void op_apply(const SellView<TP> &S, const TP *v, const Epi &e, cudaStream_t s) {
+  sell_spmv<B, B>(S, v, e, s);
+}
+template <int B, typename TP, typename Epi>
+void op_apply(const BsrView<TP> &S, const TP *v, const Epi &e, cudaStream_t s) {
+  spmv<B, B>(S, v, e, s);
+}
+
+// lambda of D^-1 S by normalised power steps on the cycle-precision operator
+// (in the layout the cycle uses for it); norms in double on the device, one
+// host read at the end
+template <int B, typename TP, typename M>
+double power_lambda(const M &S, const TP *Dinv, uint64_t seed, int level, int steps, cudaStream_t s) {
   const int64_t n = (int64_t)S.nbr * B;
   DBuf<double> v0(n), scal(2 + steps), part(kRedBlocks + 1);
   DBuf<TP> v(n), w(n);
@@ -748,7 +758,7 @@ double power_lambda(const SellView<TP> &S, const TP *Dinv, uint64_t seed, int le
   cast(v.p, v0.p, n, s);
   for (int it = 0; it < steps; it++) {
     EpiBlockDiag<B, TP> e{w.p, Dinv};
-    sell_spmv<B, B>(S, v.p, e, s);
+    op_apply<B, TP>(S, v.p, e, s);
     nrm2sq_dev(w.p, n, scal.p, s, part.p);
     nrm2sq_dev(v.p, n, scal.p + 1, s, part.p);
     k_power_scale<TP><<<grid_rows(n), kT, 0, s>>>(v.p, w.p, n, scal.p, scal.p + 1, scal.p + 2 + it);
@@ -910,14 +920,21 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
         }
         c.Dinv = c.Dinv_own.p;
       }
-      if (sell) c.Ss = L.Ssf.nbr == L.nb && L.Ssf.sp.p ? std::move(L.Ssf) : to_sell<TP>(L.S.view(), s);
-      else {
-        c.S_own = copy_cast<TP, double>(L.S.view(), s);
+      if (sell) {
+        c.Ss = L.Ssf.nbr == L.nb && L.Ssf.sp.p ? std::move(L.Ssf) : to_sell<TP>(L.S.view(), s);
+      } else {
+        if constexpr (std::is_same<TP, float>::value) {
+          if (L.Sbf.nbr == L.nb && L.Sbf.val.p) c.S_own = std::move(L.Sbf);
+          else c.S_own = copy_cast<TP, double>(L.S.view(), s);
+        } else {
+          c.S_own = copy_cast<TP, double>(L.S.view(), s);
+        }
         c.S = c.S_own.view();
       }
     }
     L.Ssf = Sell<float>();
     L.Ssd = Sell<double>();
+    L.Sbf = Bsr<float>();
     c.op.sell = sell;
     c.op.sv = c.Ss.view();
     c.op.bv = c.S;
@@ -961,14 +978,22 @@ void level_diag(LevelSetup &L, int l, DBuf<double> &dn, cudaStream_t s) {
 template <int B>
 void level_lambda(LevelSetup &L, const AmgParams &p, int l, int precision, cudaStream_t s) {
   const int nb = L.nb;
+  const bool sell = nb == 0 || (double)L.S.nnzb / nb <= kSellMaxMeanRow;
   if (precision == FC_MIXED) {
-    L.Ssf = to_sell<float>(L.S.view(), s);
     L.Dinvf.alloc((size_t)nb * B * B);
     cast(L.Dinvf.p, L.Dinv.p, (int64_t)nb * B * B, s);
-    L.lam = power_lambda<B, float>(L.Ssf.view(), L.Dinvf.p, p.seed, l, p.power_steps, s);
-  } else {
+    if (sell) {
+      L.Ssf = to_sell<float>(L.S.view(), s);
+      L.lam = power_lambda<B, float>(L.Ssf.view(), L.Dinvf.p, p.seed, l, p.power_steps, s);
+    } else {
+      L.Sbf = copy_cast<float, double>(L.S.view(), s);
+      L.lam = power_lambda<B, float>(L.Sbf.view(), L.Dinvf.p, p.seed, l, p.power_steps, s);
+    }
+  } else if (sell) {
     L.Ssd = to_sell<double>(L.S.view(), s);
     L.lam = power_lambda<B, double>(L.Ssd.view(), L.Dinv.p, p.seed, l, p.power_steps, s);
+  } else {
+    L.lam = power_lambda<B, double>(L.S.view(), L.Dinv.p, p.seed, l, p.power_steps, s);
   }
 }
 

@@ -37,6 +37,7 @@ struct LevelSetup {
   // (the power iteration runs on them) and handed to the cycle
   Sell<float> Ssf;
   Sell<double> Ssd;
+  Bsr<float> Sbf;                // float BSR copy of a long-row level (power steps, then the cycle)
   DBuf<float> Dinvf;
 };
 

@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // evenly over the lanes.  One warp per row of C (the rows of a length class,
 // from a list); the row's slot sums live in shared memory.  The row's
 // products (e, f) (entries of A's row, then of B's matching row) are taken
-// in their fixed enumeration order in segments of capT; each gets its slot
+// in their fixed enumeration order in segments of capT (a multiple of
+// kSegT, by row class); each gets its slot
 // (the position of B's column among C's sorted columns) and a stable
 // counting sort groups the segment by slot.  The sorted list is then cut
 // into 32 equal runs, one per lane: a lane adds its run's products in order
@@ -297,11 +298,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // entry of C is the same ordered sum on every run, with no value atomics.
 constexpr int kSegT = 192;   // products per segment of the numeric pass
 
+// A share of one row's products, [t_lo, t_hi) in enumeration order, summed
+// into scratch + soff (soff >= 0: a row split over several warps) or into
+// the row of C itself (soff < 0).
+struct SpgemmTask {
+  int row, t_lo, t_hi;
+  int64_t soff;
+};
+
 template <int BR, int BK, int BC, bool GS>
 __global__ void __launch_bounds__(256)
     k_spgemm_numeric_mp(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC, double *valC,
-                        const int *rows, const int *nrows, int capA, int capC, int *bad) {
-  constexpr int BS = BR * BC, AS = BR * BK, BB = BK * BC, capT = kSegT, kPL = kSegT / 32;
+                        const int *rows, const int *nrows, const SpgemmTask *tasks, double *scratch, int capA,
+                        int capC, int capT, int *bad) {
+  constexpr int BS = BR * BC, AS = BR * BK, BB = BK * BC, kPL = kSegT / 32;
   extern __shared__ double dsm[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   const int dw = (GS ? 0 : capC) + 32;                   // doubles per warp, in blocks
@@ -319,54 +329,59 @@ __global__ void __launch_bounds__(256)
   const unsigned lt = (1u << lane) - 1u;
   const int n = *nrows;
   for (int w = blockIdx.x * wpb + wid; w < n; w += gridDim.x * wpb) {
-    const int i = rows[w];
+    const SpgemmTask tk = tasks ? tasks[w] : SpgemmTask{rows[w], 0, INT32_MAX, -1};
+    const int i = tk.row;
     const int cs = rpC[i], p_n = rpC[i + 1] - cs;
     const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
-    // the slot sums: in shared memory, or (long rows) the row of C itself
-    double *sums = GS ? valC + (int64_t)cs * BS : carry + 32 * BS;
+    // the slot sums: in shared memory, or (long rows) the row of C itself or
+    // this task's share of the scratch
+    double *sums = !GS ? carry + 32 * BS : tk.soff >= 0 ? scratch + tk.soff : valC + (int64_t)cs * BS;
     row_product_prefix(A, B, a0, na, pre, lane);
     for (int x = lane; x < na; x += 32) kb[x] = B.rp[A.ci[a0 + x]];
     for (int t = lane; t < p_n; t += 32) cols[t] = ciC[cs + t];
     __syncwarp();
-    const int T = pre[na];
+    const int T = min(pre[na], tk.t_hi);
     for (int x = lane; x < p_n * BS; x += 32) sums[x] = 0.0;
     bool okp = true;
-    for (int t0 = 0; t0 < T; t0 += capT) {
+    for (int t0 = tk.t_lo; t0 < T; t0 += capT) {
       const int tn = min(capT, T - t0);
       for (int t = lane; t < p_n; t += 32) {
         start[t] = 0;
         off[t] = 0;
       }
       __syncwarp();
-      // the segment's products, kPL per lane, their loads issued together
-      int ev[kPL], fv[kPL], cv[kPL];
+      // the segment's products, kSegT at a time: kPL per lane, their loads
+      // issued together
+      for (int c0 = 0; c0 < tn; c0 += kSegT) {
+        int ev[kPL], fv[kPL], cv[kPL];
 #pragma unroll
-      for (int u = 0; u < kPL; u++) {
-        const int tl = u * 32 + lane;
-        ev[u] = 0;
-        fv[u] = 0;
-        if (tl < tn) {
-          const int t = t0 + tl;
-          const int x = product_entry(pre, na, t);
-          ev[u] = a0 + x;
-          fv[u] = kb[x] + (t - pre[x]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kPL; u++) cv[u] = u * 32 + lane < tn ? B.ci[fv[u]] : 0;
-#pragma unroll
-      for (int u = 0; u < kPL; u++) {
-        const int tl = u * 32 + lane;
-        if (tl < tn) {
-          int p = find_sorted(cols, p_n, cv[u]);
-          if (p < 0) {   // cannot happen: the symbolic pass saw every column
-            okp = false;
-            p = 0;
+        for (int u = 0; u < kPL; u++) {
+          const int tl = c0 + u * 32 + lane;
+          ev[u] = 0;
+          fv[u] = 0;
+          if (tl < tn) {
+            const int t = t0 + tl;
+            const int x = product_entry(pre, na, t);
+            ev[u] = a0 + x;
+            fv[u] = kb[x] + (t - pre[x]);
           }
-          ee[tl] = ev[u];
-          ff[tl] = fv[u];
-          pl[tl] = p;
-          atomicAdd(&start[p], 1);
+        }
+#pragma unroll
+        for (int u = 0; u < kPL; u++) cv[u] = c0 + u * 32 + lane < tn ? B.ci[fv[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < kPL; u++) {
+          const int tl = c0 + u * 32 + lane;
+          if (tl < tn) {
+            int p = find_sorted(cols, p_n, cv[u]);
+            if (p < 0) {   // cannot happen: the symbolic pass saw every column
+              okp = false;
+              p = 0;
+            }
+            ee[tl] = ev[u];
+            ff[tl] = fv[u];
+            pl[tl] = p;
+            atomicAdd(&start[p], 1);
+          }
         }
       }
       const int kept = tn;
@@ -638,19 +653,68 @@ __global__ void k_max_pending_len(const int *rp, int n, const int *pending, int 
   atomicMax(out, m);
 }
 
+// products and columns of the listed rows of C = A B
+__global__ void k_row_info(BsrView<double> A, BsrView<double> B, const int *rpC, const int *rows, int n,
+                           int *T, int *pn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < n; w += nw) {
+    const int i = rows[w];
+    int t = 0;
+    for (int e = A.rp[i] + lane; e < A.rp[i + 1]; e += 32) {
+      const int k = A.ci[e];
+      t += B.rp[k + 1] - B.rp[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+      T[w] = t;
+      pn[w] = rpC[i + 1] - rpC[i];
+    }
+  }
+}
+
+struct SplitRow {
+  int row, nt, pn;
+  int64_t soff;
+};
+
+// a row split over nt tasks: its sums, added in task order
+__global__ void k_sum_split(const SplitRow *sr, int n, const int *rpC, const double *scratch, int bs,
+                            double *valC) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < n; w += nw) {
+    const SplitRow r = sr[w];
+    const int64_t len = (int64_t)r.pn * bs;
+    for (int64_t x = lane; x < len; x += 32) {
+      double v = scratch[r.soff + x];
+      for (int k = 1; k < r.nt; k++) v += scratch[r.soff + k * len + x];
+      valC[(int64_t)rpC[r.row] * bs + x] = v;
+    }
+  }
+}
+
 template <int BR, int BK, int BC, bool GS>
 void launch_mp(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, const int *rows,
-               const int *nrows, int capC, int capA, int *flags, cudaStream_t s) {
-  const int wpb = 8;
-  const size_t dbl = (size_t)wpb * ((GS ? 0 : capC) + 32) * BR * BC;
-  const size_t ints = (size_t)wpb * (3 * capC + 2 * capA + 2 + 4 * kSegT);
-  const size_t shm = dbl * sizeof(double) + ints * sizeof(int);
-  const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)(225 * 1024) / shm));
+               const int *nrows, const SpgemmTask *tasks, double *scratch, int capC, int capA, int capT,
+               int *flags, cudaStream_t s) {
+  // shared memory per warp; up to eight warps per block, as many blocks per SM as fit
+  const size_t per_warp = (size_t)((GS ? 0 : capC) + 32) * BR * BC * sizeof(double) +
+                          (size_t)(3 * capC + 2 * capA + 2 + 4 * capT) * sizeof(int);
+  const size_t budget = 225 * 1024;
+  FS_REQUIRE(per_warp <= budget, FC_INTERNAL, "spgemm: row class does not fit in shared memory");
+  const int wpb = (int)std::min<size_t>(8, budget / per_warp);
+  const size_t shm = per_warp * wpb;
+  const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, budget / shm));
   auto kern = k_spgemm_numeric_mp<BR, BK, BC, GS>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  kern<<<kSMs * per_sm, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, rows, nrows, capA, capC, flags);
+  kern<<<kSMs * per_sm, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, rows, nrows, tasks, scratch, capA, capC,
+                                            capT, flags);
   FS_LAUNCHED();
 }
+
+constexpr int kTaskT = 8 * kSegT;                  // products per task of a split row, at least
+constexpr size_t kSplitScratch = (size_t)512 << 20;   // bytes of partial sums, at most
 
 template <int BR, int BK, int BC>
 void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s) {
@@ -658,7 +722,9 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   if (C.nbr == 0) return;
   // three length classes of C rows (columns, A-row entries): short rows sum
   // in shared memory at two blocks per SM; medium and long rows sum in the
-  // row of C itself, which keeps eight or more warps per SM
+  // row of C itself, which keeps eight or more warps per SM.  Long rows with
+  // many products are split into tasks of kTaskT or more products, summed
+  // apart and added in task order.
   const RowClasses rc{3, {64, 160, 768}, {256, 512, 1024}};
   DBuf<int> pending(C.nbr), flags(2), lists((size_t)rc.n * C.nbr), counts(rc.n);
   FS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
@@ -666,10 +732,80 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   k_classify_rows<<<blocks_for(C.nbr, 256, kSMs * 8), 256, 0, s>>>(A.rp, C.rp.p, C.nbr, rc, lists.p, counts.p,
                                                                     pending.p);
   FS_LAUNCHED();
-  launch_mp<BR, BK, BC, false>(A, B, C, lists.p, counts.p, rc.caps[0], rc.capa[0], flags.p, s);
-  for (int c = 1; c < rc.n; c++)
-    launch_mp<BR, BK, BC, true>(A, B, C, lists.p + (size_t)c * C.nbr, counts.p + c, rc.caps[c], rc.capa[c],
+  // segments of kSegT products in every class (longer segments for the
+  // longer rows, 768 and 1536 products, were slower at 128^3: fewer warps
+  // per SM)
+  launch_mp<BR, BK, BC, false>(A, B, C, lists.p, counts.p, nullptr, nullptr, rc.caps[0], rc.capa[0], kSegT,
+                               flags.p, s);
+  launch_mp<BR, BK, BC, true>(A, B, C, lists.p + C.nbr, counts.p + 1, nullptr, nullptr, rc.caps[1], rc.capa[1],
+                              kSegT, flags.p, s);
+  int hc[3] = {0, 0, 0};
+  FS_CUDA(cudaMemcpyAsync(hc, counts.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  const int n2 = hc[2];
+  DBuf<SpgemmTask> dtasks;
+  DBuf<SplitRow> dsplit;
+  DBuf<double> scratch;
+  DBuf<int> ntask;
+  int nsplit = 0;
+  if (n2 > 0) {
+    const int *rows2 = lists.p + (size_t)2 * C.nbr;
+    DBuf<int> T2(n2), P2(n2);
+    k_row_info<<<blocks_for((int64_t)n2 * 32, 256, kSMs * 8), 256, 0, s>>>(A, B, C.rp.p, rows2, n2, T2.p, P2.p);
+    FS_LAUNCHED();
+    std::vector<int> hr(n2), ht(n2), hp(n2);
+    FS_CUDA(cudaMemcpyAsync(hr.data(), rows2, sizeof(int) * n2, cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaMemcpyAsync(ht.data(), T2.p, sizeof(int) * n2, cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaMemcpyAsync(hp.data(), P2.p, sizeof(int) * n2, cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+    // the task size: kTaskT products, doubled until the partial sums fit the scratch bound
+    int64_t chunk = kTaskT;
+    for (;;) {
+      size_t bytes = 0;
+      for (int w = 0; w < n2; w++) {
+        const int64_t nt = std::max<int64_t>(1, (ht[w] + chunk - 1) / chunk);
+        if (nt > 1) bytes += (size_t)nt * hp[w] * BS * sizeof(double);
+      }
+      if (bytes <= kSplitScratch) break;
+      chunk *= 2;
+    }
+    std::vector<SpgemmTask> tasks;
+    std::vector<SplitRow> split;
+    int64_t soff = 0;
+    for (int w = 0; w < n2; w++) {
+      const int T = ht[w];
+      const int nt = (int)std::max<int64_t>(1, (T + chunk - 1) / chunk);
+      if (nt == 1) {
+        tasks.push_back({hr[w], 0, T, -1});
+        continue;
+      }
+      for (int k = 0; k < nt; k++)
+        tasks.push_back({hr[w], (int)((int64_t)T * k / nt), (int)((int64_t)T * (k + 1) / nt),
+                         soff + (int64_t)k * hp[w] * BS});
+      split.push_back({hr[w], nt, hp[w], soff});
+      soff += (int64_t)nt * hp[w] * BS;
+    }
+    nsplit = (int)split.size();
+    dtasks.alloc(tasks.size());
+    ntask.alloc(1);
+    const int nt_all = (int)tasks.size();
+    FS_CUDA(cudaMemcpyAsync(dtasks.p, tasks.data(), sizeof(SpgemmTask) * tasks.size(), cudaMemcpyHostToDevice, s));
+    FS_CUDA(cudaMemcpyAsync(ntask.p, &nt_all, sizeof(int), cudaMemcpyHostToDevice, s));
+    if (nsplit) {
+      dsplit.alloc(nsplit);
+      scratch.alloc((size_t)soff);
+      FS_CUDA(cudaMemcpyAsync(dsplit.p, split.data(), sizeof(SplitRow) * nsplit, cudaMemcpyHostToDevice, s));
+    }
+    launch_mp<BR, BK, BC, true>(A, B, C, nullptr, ntask.p, dtasks.p, scratch.p, rc.caps[2], rc.capa[2], kSegT,
                                 flags.p, s);
+    if (nsplit) {
+      k_sum_split<<<blocks_for((int64_t)nsplit * 32, 256, kSMs * 8), 256, 0, s>>>(dsplit.p, nsplit, C.rp.p,
+                                                                                  scratch.p, BS, C.val.p);
+      FS_LAUNCHED();
+    }
+    // the host vectors above go out of scope only after the copies that read them
+    FS_CUDA(cudaStreamSynchronize(s));
+  }
   // rows beyond the tiers (very long rows of A or many products): longest C row among them
   k_max_pending_len<<<blocks_for(C.nbr, 256, kSMs * 4), 256, 0, s>>>(C.rp.p, C.nbr, pending.p, flags.p + 1);
   FS_LAUNCHED();
