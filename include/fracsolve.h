@@ -115,7 +115,7 @@ typedef struct {
 typedef struct fc_ctx fc_ctx;
 
 /* Fill *opt with the defaults (FP64, both variants, theta0 0.08, decay 0.5,
- * coarse_max 1000, coarse_max_p 1000, 12 levels, ratio 0.8, 15 power
+ * coarse_max 200, coarse_max_p 200, 12 levels, ratio 0.8, 15 power
  * steps, omega_num 4/3, Chebyshev degree 2 on [0.11, 1.1] * lambda,
  * 3 restarts, coarse_graphs 1). */
 void fc_default_options(fc_options *opt);

@@ -47,7 +47,7 @@ from . import rng
 class AmgOptions:
     theta0: float = 0.08
     theta_decay: float = 0.5
-    coarse_max: int = 1000        # block rows
+    coarse_max: int = 200         # block rows
     max_levels: int = 12
     max_ratio: float = 0.8
     power_steps: int = 15

@@ -851,8 +851,8 @@ void fc_default_options(fc_options *o) {
   o->variants = (1 << FC_TPU) | (1 << FC_TUP);
   o->theta0 = 0.08;
   o->theta_decay = 0.5;
-  o->coarse_max = 1000;
-  o->coarse_max_p = 1000;
+  o->coarse_max = 200;
+  o->coarse_max_p = 200;
   o->max_levels = 12;
   o->max_ratio = 0.8;
   o->power_steps = 15;

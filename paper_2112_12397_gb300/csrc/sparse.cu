@@ -1,4 +1,6 @@
 // Setup-phase sparse kernels: transpose, block SpGEMM, sparse add.
+#include <cstdlib>
+
 #include "sparse.cuh"
 #include "sell.cuh"
 
@@ -725,7 +727,18 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   // row of C itself, which keeps eight or more warps per SM.  Long rows with
   // many products are split into tasks of kTaskT or more products, summed
   // apart and added in task order.
-  const RowClasses rc{3, {64, 160, 768}, {256, 512, 1024}};
+  RowClasses rc{3, {64, 160, 768}, {256, 512, 1024}};
+  // test hook: FS_SPGEMM_FORCE_LONG=<products> sends every row that fits the
+  // long class there and splits rows into tasks of that many products, so
+  // that small problems exercise the paths large ones take
+  int64_t task_min = kTaskT;
+  if (const char *ev = std::getenv("FS_SPGEMM_FORCE_LONG")) {
+    const long v = std::strtol(ev, nullptr, 10);
+    if (v > 0) {
+      rc.caps[0] = rc.caps[1] = -1;
+      task_min = v;
+    }
+  }
   DBuf<int> pending(C.nbr), flags(2), lists((size_t)rc.n * C.nbr), counts(rc.n);
   FS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
   FS_CUDA(cudaMemsetAsync(counts.p, 0, rc.n * sizeof(int), s));
@@ -759,7 +772,7 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
     FS_CUDA(cudaMemcpyAsync(hp.data(), P2.p, sizeof(int) * n2, cudaMemcpyDeviceToHost, s));
     FS_CUDA(cudaStreamSynchronize(s));
     // the task size: kTaskT products, doubled until the partial sums fit the scratch bound
-    int64_t chunk = kTaskT;
+    int64_t chunk = task_min;
     for (;;) {
       size_t bytes = 0;
       for (int w = 0; w < n2; w++) {

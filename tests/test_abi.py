@@ -44,7 +44,7 @@ def test_host_only_entry_points(lib):
     import paper_2112_12397_gb300 as fs
     fs.load()
     o = fs.default_options()
-    assert o.precision == fs.FC_FP64 and o.cheb_degree == 2 and o.coarse_max == 1000
+    assert o.precision == fs.FC_FP64 and o.cheb_degree == 2 and o.coarse_max == 200
     assert abs(o.omega_num - 4.0 / 3.0) < 1e-15
     assert fs.load().fc_strerror(fs.FC_SINGULAR_BLOCK) == b"singular block"
 
