@@ -729,14 +729,17 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   // apart and added in task order.
   RowClasses rc{3, {64, 160, 768}, {256, 512, 1024}};
   // test hook: FS_SPGEMM_FORCE_LONG=<products> sends every row that fits the
-  // long class there and splits rows into tasks of that many products, so
-  // that small problems exercise the paths large ones take
+  // long class there and splits rows into tasks of that many products; -1
+  // leaves every row to the chunked kernel that takes rows beyond the
+  // classes.  Small problems then exercise the paths large ones take.
   int64_t task_min = kTaskT;
   if (const char *ev = std::getenv("FS_SPGEMM_FORCE_LONG")) {
     const long v = std::strtol(ev, nullptr, 10);
     if (v > 0) {
       rc.caps[0] = rc.caps[1] = -1;
       task_min = v;
+    } else if (v == -1) {
+      rc.caps[0] = rc.caps[1] = rc.caps[2] = -1;
     }
   }
   DBuf<int> pending(C.nbr), flags(2), lists((size_t)rc.n * C.nbr), counts(rc.n);

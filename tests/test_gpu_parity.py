@@ -438,11 +438,12 @@ def test_malformed_block_structure_is_rejected(fs):
     ctx.close()
 
 
-@pytest.mark.parametrize("task", [200, 100000])
+@pytest.mark.parametrize("task", [200, 100000, -1])
 def test_galerkin_products_in_the_long_row_class(fs, task, monkeypatch):
     """Every Galerkin and Schur product sent through the long-row class of
     the numeric SpGEMM (row sums in the output row), with rows split into
-    tasks of about `task` products summed apart (200) or kept whole: the
+    tasks of about `task` products summed apart (200) or kept whole, or
+    (-1) through the chunked kernel that takes rows beyond every class: the
     operators and V-cycles match the oracle as in the default classes."""
     monkeypatch.setenv("FS_SPGEMM_FORCE_LONG", str(task))
     preset, over, cm, cmp = CASES["rects16"]
