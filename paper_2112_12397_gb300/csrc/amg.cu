@@ -293,13 +293,19 @@ __global__ void k_power_start(int64_t n, uint64_t seed, int level, double *v) {
 }
 
 // ------------------------------------------------------------ 6. prolongator
+// 1 / sqrt|a| of every aggregate (the scale of its tentative block), once
+__global__ void k_inv_sqrt_size(const int *asize, int nc, double *isz) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nc; a += (int64_t)gridDim.x * blockDim.x)
+    isz[a] = 1.0 / sqrt((double)asize[a]);
+}
+
 // One warp per row i of S.  The aggregates a(j) of the row's columns are
 // staged in shared memory; the distinct ones, ranked in increasing order, are
 // the row's columns in P.  For each distinct a, the blocks S_ij with
 // a(j) = a are added in row order, then
 //   P_ia = [a(i) = a] I / sqrt|a| - omega D_i^-1 (sum_j S_ij) / sqrt|a|.
 template <int B>
-__global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, const double *Dinv,
+__global__ void k_prolong(BsrView<double> S, const int *agg, const double *isz_agg, const double *Dinv,
                           double omega, int pass, int *cnt, const int *rpP, int *ciP, double *valP,
                           int cap, int *flag) {
   constexpr int BS = B * B;
@@ -342,7 +348,7 @@ __global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, c
       const int o = rpP[i];
       const double *Di = Dinv + i * BS;
       const int ai = agg[i];
-      const double isz_first = first ? 1.0 / sqrt((double)asize[a]) : 0.0;
+      const double isz_first = first ? isz_agg[a] : 0.0;
       double *sums = sh_sum[wid];
       for (int k0 = 0; k0 < nu * BS; k0 += 32) {
         const int k = k0 + lane;
@@ -420,7 +426,7 @@ __global__ void k_prolong(BsrView<double> S, const int *agg, const int *asize, c
         const double *v = S.val + (int64_t)(s0 + u) * BS;
         for (int q = 0; q < BS; q++) acc[q] += v[q];
       }
-      const double isz = 1.0 / sqrt((double)asize[a]);
+      const double isz = isz_agg[a];
       double *out = valP + (int64_t)(o + r) * BS;
       for (int rr = 0; rr < B; rr++)
         for (int cc = 0; cc < B; cc++) {
@@ -799,14 +805,19 @@ void build_prolongator(LevelSetup &L, const DBuf<int> &asize, int nc, double ome
   const size_t shm = (size_t)wpb * 3 * cap * sizeof(int);
   FS_CUDA(cudaFuncSetAttribute(k_prolong<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   const int grid = kSMs * 8;
-  k_prolong<B><<<grid, wpb * 32, shm, s>>>(S, L.agg.p, asize.p, L.Dinv.p, omega, 0, cnt.p, nullptr, nullptr,
+  DBuf<double> isz(nc > 0 ? nc : 1);
+  if (nc > 0) {
+    k_inv_sqrt_size<<<blocks_for(nc, 256, kSMs * 4), 256, 0, s>>>(asize.p, nc, isz.p);
+    FS_LAUNCHED();
+  }
+  k_prolong<B><<<grid, wpb * 32, shm, s>>>(S, L.agg.p, isz.p, L.Dinv.p, omega, 0, cnt.p, nullptr, nullptr,
                                             nullptr, cap, flag.p);
   FS_LAUNCHED();
   P.nnzb = exclusive_scan(cnt.p, P.rp.p, L.nb, s);
   P.ci.alloc(P.nnzb);
   P.val.alloc(P.nnzb * B * B);
   if (P.nnzb) {
-    k_prolong<B><<<grid, wpb * 32, shm, s>>>(S, L.agg.p, asize.p, L.Dinv.p, omega, 1, nullptr, P.rp.p, P.ci.p,
+    k_prolong<B><<<grid, wpb * 32, shm, s>>>(S, L.agg.p, isz.p, L.Dinv.p, omega, 1, nullptr, P.rp.p, P.ci.p,
                                               P.val.p, cap, flag.p);
     FS_LAUNCHED();
   }
@@ -834,8 +845,13 @@ void prolongator_values(LevelSetup &L, double omega, cudaStream_t s) {
   while (wpb > 1 && (size_t)wpb * 3 * cap * sizeof(int) > 96 * 1024) wpb >>= 1;
   const size_t shm = (size_t)wpb * 3 * cap * sizeof(int);
   FS_CUDA(cudaFuncSetAttribute(k_prolong<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  DBuf<double> isz(L.nc > 0 ? L.nc : 1);
+  if (L.nc > 0) {
+    k_inv_sqrt_size<<<blocks_for(L.nc, 256, kSMs * 4), 256, 0, s>>>(L.asize.p, L.nc, isz.p);
+    FS_LAUNCHED();
+  }
   if (P.nnzb) {
-    k_prolong<B><<<kSMs * 8, wpb * 32, shm, s>>>(S, L.agg.p, L.asize.p, L.Dinv.p, omega, 1, nullptr, P.rp.p,
+    k_prolong<B><<<kSMs * 8, wpb * 32, shm, s>>>(S, L.agg.p, isz.p, L.Dinv.p, omega, 1, nullptr, P.rp.p,
                                                  P.ci.p, P.val.p, cap, flag.p);
     FS_LAUNCHED();
   }
