@@ -323,3 +323,30 @@ def test_geometric_fixed_stress():
     assert 0.1 < np.median(ratio) < 10.0
     S2 = schur.s2_tilde(P, S1, sk=geo)
     assert np.abs(S2 - S2.T).max() <= 1e-14 * np.abs(S2).max()
+
+
+@pytest.mark.parametrize("variant", ["tpu", "tup"])
+def test_block_preconditioners_agree_with_block_jacobi_gmres(tiny, variant):
+    """Both preconditioned solves reach the solution that GMRES with the plain
+    block-Jacobi preconditioner of J reaches (3x3 node blocks of A, 3x3 face
+    blocks of -H, the diagonal of T), in a small fraction of its iterations."""
+    J = osp.jacobian(tiny)
+    Jd = J.toarray()
+    nu, nt = 3 * tiny.n_node, 3 * tiny.n_face
+    groups = [np.arange(i, i + 3) for i in range(0, nu + nt, 3)]
+    groups += [np.array([k]) for k in range(nu + nt, J.shape[0])]
+    inv = [np.linalg.inv(Jd[np.ix_(g, g)]) for g in groups]
+
+    def jacobi(v):
+        out = np.empty_like(v)
+        for g, Bi in zip(groups, inv):
+            out[g] = Bi @ v[g]
+        return out
+
+    rj = fgmres(lambda v: J @ v, jacobi, tiny.b, tol=1e-12, maxit=1500)
+    M = BlockPreconditioner(tiny, variant, opt=AmgOptions(coarse_max=64))
+    rp = fgmres(lambda v: J @ v, M, tiny.b, tol=1e-12, maxit=300)
+    xs = dense.solve(tiny)
+    assert rj.relres <= 1e-9 and rp.relres <= 1e-9
+    assert np.linalg.norm(rj.x - rp.x) <= 1e-10 * np.linalg.norm(xs)
+    assert 4 * rp.iters < rj.iters
