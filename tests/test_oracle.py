@@ -350,3 +350,32 @@ def test_block_preconditioners_agree_with_block_jacobi_gmres(tiny, variant):
     assert rj.relres <= 1e-9 and rp.relres <= 1e-9
     assert np.linalg.norm(rj.x - rp.x) <= 1e-10 * np.linalg.norm(xs)
     assert 4 * rp.iters < rj.iters
+
+
+def test_smoothed_prolongator_lowers_energy_and_keeps_translations():
+    """One damped-Jacobi smoothing step of P_tent (omega in (0, 2/lambda))
+    lowers the energy trace(P^T S P) of every column of the SPD elasticity
+    Schur complement, and keeps the rigid translations exactly on nodes whose
+    rows of S annihilate them (interior nodes, all neighbours aggregated)."""
+    P = fracgen.generate("planes64", N=6)
+    S = schur.s1(P)
+    amg = AMG(S, 3, AmgOptions(coarse_max=10))
+    L = amg.levels[0]
+    Pt = oamg.tentative(L.agg, L.nc, 3)
+    e_t = np.einsum("ij,ij->j", Pt.toarray(), (S @ Pt).toarray())
+    e_s = np.einsum("ij,ij->j", L.P.toarray(), (S @ L.P).toarray())
+    assert np.all(e_s < e_t)
+    size = np.bincount(L.agg[L.agg >= 0], minlength=L.nc).astype(float)
+    for comp in range(3):
+        c = np.zeros(3 * L.nc)
+        c[comp::3] = np.sqrt(size)
+        t = np.zeros(S.shape[0])
+        t[comp::3] = 1.0
+        St = S @ t
+        rows = np.nonzero(np.abs(St) <= 1e-12 * abs(S).max())[0]
+        rows = rows[np.repeat(L.agg >= 0, 3)[rows]]
+        Sa = S[rows]
+        keep = [r for k, r in enumerate(rows)
+                if np.all(np.repeat(L.agg >= 0, 3)[Sa.indices[Sa.indptr[k]:Sa.indptr[k + 1]]])]
+        assert len(keep) > 0
+        assert np.allclose((L.P @ c)[keep], t[keep], atol=1e-12)
