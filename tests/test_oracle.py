@@ -400,3 +400,37 @@ def test_power_estimate_of_the_jacobi_spectrum():
     M = sp.block_diag(list(Dinv), format="csr") @ S1
     rho = np.abs(np.linalg.eigvals(M.toarray())).max()
     assert 0.9 * rho <= est <= rho * (1 + 1e-10)
+
+
+def test_strength_graph_classic_cases():
+    """Strength of connection, scalar case: the 1D Laplacian couples every
+    neighbour with weight 1/4; the anisotropic 2D Laplacian -u_xx - eps u_yy
+    keeps the y couplings only while eps^2 / (2 + 2 eps)^2 exceeds theta^2
+    (theta0 = 0.08: eps = 0.1 weak, eps = 0.5 strong); the graph does not
+    change under a symmetric positive diagonal scaling D S D."""
+    n = 12
+    L1 = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    W = oamg.strength_graph(L1, 1, 0, AmgOptions())
+    assert W.nnz == 2 * (n - 1)
+    assert np.allclose(W.data, 0.25)
+    m = 6
+    I = sp.identity(m)
+    T1 = sp.diags([-np.ones(m - 1), 2 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+    for eps, strong_y in ((0.1, False), (0.5, True)):
+        # -u_xx - eps u_yy on an m x m grid, x fastest; diagonal 2 + 2 eps
+        Ax = sp.kron(I, T1)
+        Ay = sp.kron(T1, I)
+        A = (Ax + eps * Ay).tocsr()
+        W = oamg.strength_graph(A, 1, 0, AmgOptions()).tocoo()
+        dx = np.abs(W.row - W.col)
+        assert np.all((dx == 1) | (dx == m))
+        assert (dx == 1).sum() == 2 * m * (m - 1)
+        assert ((dx == m).sum() > 0) == strong_y
+    rs = np.random.default_rng(4)
+    P = fracgen.generate("planes64", N=4, seed=2)
+    S = schur.s1(P)
+    d = np.repeat(rs.uniform(0.5, 2.0, S.shape[0] // 3), 3)
+    Ds = sp.diags(d)
+    W1 = oamg.strength_graph(S, 3, 0, AmgOptions())
+    W2 = oamg.strength_graph((Ds @ S @ Ds).tocsr(), 3, 0, AmgOptions())
+    assert (W1 != 0).toarray().tolist() == (W2 != 0).toarray().tolist()
