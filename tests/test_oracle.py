@@ -434,3 +434,27 @@ def test_strength_graph_classic_cases():
     W1 = oamg.strength_graph(S, 3, 0, AmgOptions())
     W2 = oamg.strength_graph((Ds @ S @ Ds).tocsr(), 3, 0, AmgOptions())
     assert (W1 != 0).toarray().tolist() == (W2 != 0).toarray().tolist()
+
+
+def test_aggregates_are_rooted_balls_of_radius_two():
+    """MIS-2 aggregation: every aggregate holds exactly one root, and each of
+    its nodes is the root, a strong neighbour of it, or a strong neighbour of
+    such a neighbour within the same aggregate (radius <= 2, connected)."""
+    P = fracgen.generate("planes64", N=6)
+    S = schur.s1(P)
+    W = oamg.strength_graph(S, 3, 0, AmgOptions())
+    root = oamg.mis2_greedy(W, oamg.priority_keys(W.shape[0], 0, 0))
+    agg, nc = oamg.aggregate(W, root)
+    roots = np.nonzero(root)[0]
+    assert np.array_equal(np.sort(agg[roots]), np.arange(nc))
+    for a in range(nc):
+        members = np.nonzero(agg == a)[0]
+        r = roots[agg[roots] == a]
+        assert len(r) == 1
+        r = r[0]
+        nb1 = set(W.indices[W.indptr[r]:W.indptr[r + 1]]) & set(members)
+        for i in members:
+            if i == r or i in nb1:
+                continue
+            ni = set(W.indices[W.indptr[i]:W.indptr[i + 1]])
+            assert ni & nb1, (a, i)
