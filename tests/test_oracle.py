@@ -458,3 +458,22 @@ def test_aggregates_are_rooted_balls_of_radius_two():
                 continue
             ni = set(W.indices[W.indptr[i]:W.indptr[i + 1]])
             assert ni & nb1, (a, i)
+
+
+def test_stick_jacobian_is_a_symmetric_saddle_point(tiny):
+    """All faces in stick: the (u, t) part [A C1; C2 -H] of the assembled J is
+    symmetric (C2 = C1^T) with exactly n_u positive and n_t negative
+    eigenvalues (Sylvester: A is SPD once the constrained dofs are removed, and
+    the Schur complement -(H + C1^T A^-1 C1) is negative definite), which a
+    wrong sign of H or a misplaced block would break."""
+    assert np.all(tiny.state == 0)
+    J = osp.jacobian(tiny)
+    nu, nt = 3 * tiny.n_node, 3 * tiny.n_face
+    K = J[:nu + nt, :nu + nt].toarray()
+    assert np.abs(K - K.T).max() <= 1e-12 * np.abs(K).max()
+    # inertia is kept by the congruence |diag K|^-1/2 K |diag K|^-1/2, which
+    # brings the traction rows (~1e7 times the displacement scale) to O(1)
+    d = 1.0 / np.sqrt(np.abs(np.diag(K)))
+    ev = np.linalg.eigvalsh(K * d[:, None] * d[None, :])
+    assert np.abs(ev).min() > 1e-3
+    assert (ev > 0).sum() == nu and (ev < 0).sum() == nt
