@@ -184,9 +184,11 @@ int fc_residual(fc_ctx *ctx, const double *d_b, const double *d_x, double *d_r, 
  * device arrays of the library (8 MiB + 4 KiB, held on every GPU that loads it
  * until the process exits).  Limit: n <= 1048576, else FC_BAD_ARG.  The first
  * call on a device looks up the arrays' device addresses (set-up, once per
- * device), so make that first call before any stream capture.  Every call
- * reuses the same arrays and overwrites them; calls that overlap on the GPU
- * (other streams, other contexts of the same device) race on them. */
+ * device), so make that first call before any stream capture.  J x is formed
+ * by the same product as fc_spmv.  The call synchronises the context's stream
+ * before it returns (the norm is read on the host).  Every call reuses the
+ * same arrays and overwrites them; calls that overlap on the GPU (other
+ * streams, other contexts of the same device) race on them. */
 int fc_residual_noalloc(fc_ctx *ctx, const double *d_b, const double *d_x, double *relres);
 
 /* d_v = M^-1 d_w: app_tpu (Alg. 2) for FC_TPU, app_tup (Alg. 4) for FC_TUP,

@@ -60,21 +60,37 @@ class fc_blocks(C.Structure):
                 ("Q2", fc_bsr), ("T", fc_bsr), ("n_node", C.c_int32), ("n_face", C.c_int32)]
 
 
+LIB_HOOKS_PATH = os.path.join(_HERE, "lib", "libfracsolve_testhooks.so")
+
 _lib = None
+_lib_hooks = None
 
 
 def load(build_if_missing: bool = False):
     """Load the shared library (optionally building it first)."""
     global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
+    if _lib is None:
+        _lib = _open(LIB_PATH, build_if_missing)
+    return _lib
+
+
+def load_test_hooks():
+    """The test build of the library (same entry points; its block SpGEMM
+    honours the FS_SPGEMM_FORCE_LONG test variable).  Only tests use it."""
+    global _lib_hooks
+    if _lib_hooks is None:
+        _lib_hooks = _open(LIB_HOOKS_PATH, False)
+    return _lib_hooks
+
+
+def _open(path: str, build_if_missing: bool):
+    if not os.path.exists(path):
         if build_if_missing:
             from . import build as _b
             _b.build()
         else:
-            raise FileNotFoundError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
-    lib = C.CDLL(LIB_PATH)
+            raise FileNotFoundError(f"{path} is missing: run __graft_entry__.build() first")
+    lib = C.CDLL(path)
     vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     pi32, pi64, pd, pint = C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int)
     sig = {
@@ -110,7 +126,6 @@ def load(build_if_missing: bool = False):
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
     return lib
 
 
@@ -138,11 +153,11 @@ def _ptr(t) -> int:
 class Context:
     """One fc_ctx bound to the current CUDA device and a CUDA stream."""
 
-    def __init__(self, options: fc_options | None = None, stream=None):
+    def __init__(self, options: fc_options | None = None, stream=None, lib=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("fracsolve needs a CUDA device; no CPU path exists")
-        self.lib = load()
+        self.lib = lib or load()
         self.opt = options or default_options()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
@@ -337,8 +352,8 @@ def device_dk(problem, device="cuda"):
                for k in ("block", "row", "col", "comp", "val")}}
 
 
-def context_for(problem, options: fc_options | None = None, stream=None) -> Context:
-    ctx = Context(options, stream)
+def context_for(problem, options: fc_options | None = None, stream=None, lib=None) -> Context:
+    ctx = Context(options, stream, lib)
     blocks = device_blocks(problem)
     ctx.setup(blocks, problem.n_node, problem.n_face)
     return ctx

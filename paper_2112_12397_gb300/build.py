@@ -3,6 +3,12 @@
 Each translation unit under csrc/ is compiled in parallel into an object
 file under _build/, then linked into lib/libfracsolve.so.  Rebuilds only
 when a source or header is newer than the library.
+
+A second library, lib/libfracsolve_testhooks.so, links the same objects
+except the block SpGEMM, which is compiled once more with FS_TEST_HOOKS: in
+that build an environment variable can force the SpGEMM's long-row and
+chunked paths on small problems, so that a GPU test covers them.  Only that
+test loads it; the product library reads no environment variable.
 """
 from __future__ import annotations
 
@@ -16,6 +22,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libfracsolve.so")
+LIB_HOOKS = os.path.join(LIBDIR, "libfracsolve_testhooks.so")
+HOOKED = "sparse.cu"          # the translation unit with the test hook
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -38,9 +46,9 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(LIB_HOOKS)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_HOOKS))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -52,9 +60,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     cc = nvcc()
     extra = extra or []
 
-    def one(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    def one(job):
+        src, hooks = job
+        base = os.path.basename(src).replace(".cu", "_hooks.o" if hooks else ".o")
+        obj = os.path.join(BUILD, base)
+        cmd = [cc, *ARCH, *FLAGS, *extra, *(["-DFS_TEST_HOOKS"] if hooks else []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -63,14 +73,18 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return obj
 
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(s, False) for s in srcs] + [(s, True) for s in srcs if os.path.basename(s) == HOOKED]
+    with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(one, jobs))
+    plain = objs[:len(srcs)]
+    hooked = [o for o, (s, _) in zip(plain, jobs) if os.path.basename(s) != HOOKED] + objs[len(srcs):]
+    for out, parts in ((LIB, plain), (LIB_HOOKS, hooked)):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *parts, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out)
     return LIB
 
 

@@ -1378,17 +1378,9 @@ int fc_residual_noalloc(fc_ctx *c, const double *b, const double *x, double *rel
     const int rc = noalloc_scratch(c->device, &sc);
     FS_REQUIRE(rc == FC_OK, rc, "cudaGetSymbolAddress of the residual scratch failed");
     cudaStream_t s = c->s;
-    double *y_u = sc.r, *y_t = sc.r + c->nu, *y_p = sc.r + c->nu + c->nt;
-    const double *z_u = x, *z_t = x + c->nu, *z_p = x + c->nu + c->nt;
-    spmv_axpby<3, 3>(c->A.view(), z_u, y_u, 1.0, 0.0, (const double *)nullptr, s);
-    if (c->nf) {
-      spmv_axpby<3, 3>(c->C1.view(), z_t, y_u, 1.0, 1.0, y_u, s);
-      spmv_axpby<3, 1>(c->Q1.view(), z_p, y_u, 1.0, 1.0, y_u, s);
-      spmv_axpby<3, 3>(c->C2.view(), z_u, y_t, 1.0, 0.0, (const double *)nullptr, s);
-      spmv_axpby<3, 3>(c->H.view(), z_t, y_t, -1.0, 1.0, y_t, s);
-      spmv_axpby<1, 3>(c->Q2.view(), z_u, y_p, 1.0, 0.0, (const double *)nullptr, s);
-      spmv_axpby<1, 1>(c->T.view(), z_p, y_p, 1.0, 1.0, y_p, s);
-    }
+    // J x into the scratch by the solver's own product (a double direction
+    // needs no widening buffer, so nothing is allocated)
+    jac_spmv<double>(*c, x, sc.r);
     k_noalloc_resid<<<kNoAllocParts, 256, 0, s>>>(b, sc.r, c->n, sc.part);
     FS_LAUNCHED();
     k_noalloc_final<<<1, 32, 0, s>>>(sc.part);

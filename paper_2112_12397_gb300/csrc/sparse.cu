@@ -728,11 +728,14 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   // many products are split into tasks of kTaskT or more products, summed
   // apart and added in task order.
   RowClasses rc{3, {64, 160, 768}, {256, 512, 1024}};
-  // test hook: FS_SPGEMM_FORCE_LONG=<products> sends every row that fits the
-  // long class there and splits rows into tasks of that many products; -1
-  // leaves every row to the chunked kernel that takes rows beyond the
-  // classes.  Small problems then exercise the paths large ones take.
+  // test hook, compiled only into the test build (FS_TEST_HOOKS):
+  // FS_SPGEMM_FORCE_LONG=<products> sends every row that fits the long class
+  // there and splits rows into tasks of that many products; -1 leaves every
+  // row to the chunked kernel that takes rows beyond the classes.  Small
+  // problems then exercise the paths large ones take.  The product library
+  // reads no environment variable.
   int64_t task_min = kTaskT;
+#ifdef FS_TEST_HOOKS
   if (const char *ev = std::getenv("FS_SPGEMM_FORCE_LONG")) {
     const long v = std::strtol(ev, nullptr, 10);
     if (v > 0) {
@@ -742,6 +745,7 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
       rc.caps[0] = rc.caps[1] = rc.caps[2] = -1;
     }
   }
+#endif
   DBuf<int> pending(C.nbr), flags(2), lists((size_t)rc.n * C.nbr), counts(rc.n);
   FS_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
   FS_CUDA(cudaMemsetAsync(counts.p, 0, rc.n * sizeof(int), s));

@@ -11,6 +11,8 @@ from oracle import sparse as osp
 from oracle.amg import AMG, AmgOptions
 from oracle.precond import BlockPreconditioner
 
+from fields import assert_fields
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +57,7 @@ def test_transposed_products(fs, name):
     x = np.random.default_rng(0).standard_normal(P.n)
     y = torch.zeros(P.n, dtype=torch.float64, device="cuda")
     ctx.spmv_adjoint(cuda(x), y)
-    assert rel(y.cpu().numpy(), JT @ x) <= 1e-14
+    assert np.all(np.abs(y.cpu().numpy() - JT @ x) <= 2e-14 * (abs(JT) @ np.abs(x)))
     S1 = schur.s1(P)
     for hier, M in ((fs.FC_H_TUP_U, S1), (fs.FC_H_TPU_U, schur.s_tilde(P, S1=S1))):
         ref = AMG(M, 3, opt)
@@ -74,7 +76,7 @@ def test_adjoint_preconditioner_and_solve(fs, name, variant):
     w = np.random.default_rng(9).standard_normal(P.n)
     v = torch.zeros(P.n, dtype=torch.float64, device="cuda")
     ctx.apply_prec_adjoint(variant, cuda(w), v)
-    assert rel(v.cpu().numpy(), Mt(w)) <= 1e-10
+    assert_fields(P, v.cpu().numpy(), Mt(w), 1e-10, f"{name} {variant} M^-T w")
     g = np.zeros(P.n)
     g[-P.n_face:] = np.random.default_rng(4).standard_normal(P.n_face)
     lam = torch.zeros(P.n, dtype=torch.float64, device="cuda")
@@ -84,7 +86,7 @@ def test_adjoint_preconditioner_and_solve(fs, name, variant):
     rc, it, rr = ctx.solve_adjoint(variant, cuda(g), lam, 1e-8, 400, allow_fail=star)
     ref = adjoint.solve_adjoint(P, M, g, 1e-8, 400)
     assert abs(it - ref.iters) <= 1
-    assert rel(lam.cpu().numpy(), ref.x) <= 1e-8
+    assert_fields(P, lam.cpu().numpy(), ref.x, 1e-8, f"{name} {variant} lambda")
     JT = osp.jacobian(P).T.tocsr()
     assert np.linalg.norm(g - JT @ lam.cpu().numpy()) / np.linalg.norm(g) <= (3e-8 if star else 1e-8)
 
@@ -97,7 +99,7 @@ def test_adjoint_matches_dense_on_8cubed(fs):
     for variant in ("tpu", "tup"):
         lam = torch.zeros(P.n, dtype=torch.float64, device="cuda")
         ctx.solve_adjoint(variant, cuda(g), lam, 1e-12, 400, allow_fail=True)
-        assert rel(lam.cpu().numpy(), lam_d) <= 1e-8
+        assert_fields(P, lam.cpu().numpy(), lam_d, 1e-8, f"tiny8 {variant} lambda vs dense")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -128,26 +130,6 @@ def test_autograd_gradient_wrt_rhs(fs, precision):
             lm = float(loss_of(b - h * cuda(d)))
             fd = (lp - lm) / (2 * h)
             assert abs(fd - grad @ d) <= 1e-5 * abs(grad @ d)
-    ctx.close()
-
-
-def test_full_size_adjoint_planes64(fs):
-    """64^3 three-plane workload in FP64: forward solve, then the adjoint of
-    0.5 ||p - p_obs||^2; the adjoint residual checked by the oracle's J^T."""
-    P = fracgen.generate("planes64")
-    ctx = fs.context_for(P, fs.default_options(variants=2))
-    b = cuda(P.b)
-    x = torch.zeros_like(b)
-    ctx.solve("tup", b, x, 1e-8, 600)
-    p = x[-P.n_face:].cpu().numpy()
-    p_obs = p * (1 + 0.1 * np.random.default_rng(12).standard_normal(P.n_face))
-    g = np.zeros(P.n)
-    g[-P.n_face:] = p - p_obs
-    lam = torch.zeros_like(b)
-    rc, it, rr = ctx.solve_adjoint("tup", cuda(g), lam, 1e-8, 600)
-    JT = osp.jacobian(P).T.tocsr()
-    true = np.linalg.norm(g - JT @ lam.cpu().numpy()) / np.linalg.norm(g)
-    assert true <= 1e-8 and abs(true - rr) <= 1e-3 * true
     ctx.close()
 
 

@@ -11,6 +11,8 @@ from oracle.amg import AmgOptions
 from oracle.fgmres import fgmres
 from oracle.precond import BlockPreconditioner
 
+from fields import assert_fields
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -65,13 +67,14 @@ def test_geometric_fixed_stress_matches_oracle(fs, name, over):
     w = np.random.default_rng(6).standard_normal(P.n)
     v = torch.zeros(P.n, dtype=torch.float64, device="cuda")
     ctx.apply_prec("tup", torch.from_numpy(w).cuda(), v)
-    assert rel(v.cpu().numpy(), M(w)) <= 1e-10
+    assert_fields(P, v.cpu().numpy(), M(w), 1e-10, "geometric FS tup M^-1 w")
     J = osp.jacobian(P)
     b = torch.from_numpy(P.b).cuda()
     x = torch.zeros_like(b)
     rc, it, rr = ctx.solve("tup", b, x, 1e-8, 600, allow_fail=True)
     ref = fgmres(lambda q: J @ q, M, P.b, 1e-8, 600)
-    assert abs(it - ref.iters) <= 1 and rel(x.cpu().numpy(), ref.x) <= 1e-8
+    assert abs(it - ref.iters) <= 1
+    assert_fields(P, x.cpu().numpy(), ref.x, 1e-8, "geometric FS tup x")
     # back to the algebraic form
     ctx.set_geometric_fs(None)
     ctx.setup(fs.device_blocks(P), P.n_node, P.n_face)
