@@ -83,14 +83,37 @@ def test_A_symmetric_and_rigid_modes_of_each_piece(name, kw):
     free = np.repeat(~touched, 3)
     R = A @ Z
     assert np.abs(R[free]).max() <= 1e-11 * abs(A).max()
-    # piecewise rigid: translate every copy on the + side of one fracture face
-    # set independently -- A stays blind to it (no cells shared across)
-    if P.n_face:
+
+def test_A_blind_to_a_rigid_motion_of_one_side_of_a_full_plane():
+    """The node split of S3: one fracture plane through the whole cube cuts
+    it in two pieces that share no cell, so a translation of the + piece
+    alone (every copy of a cell beyond the plane, the + copies on it) is a
+    rigid motion of each piece and A sees no force in any row that no
+    roller touches.  A copy shared across the plane (a wrong split) would
+    couple the pieces and fail this."""
+    P = fracgen.generate("tiny8")
+    A = osp.csr(P.A)
+    N1 = P.N + 1
+    ix = P.node_grid % N1
+    m = P.N // 2
+    assert np.all(P.face_geom[:, 0] == 0) and np.all(P.face_geom[:, 1] == m)
+    plus = (ix > m) | np.isin(np.arange(P.n_node), P.face_copies[:, 1, :])
+    assert not np.any(np.isin(P.face_copies[:, 0, :], np.nonzero(plus)[0]))
+    node_dir = P.dirichlet.reshape(-1, 3).any(axis=1)
+    rp, ci = P.A.row_ptr, P.A.col_idx
+    touched = np.array([node_dir[ci[rp[i]:rp[i + 1]]].any() for i in range(P.n_node)])
+    free = np.repeat(~touched, 3)
+    assert free.sum() > 0
+    for d in range(3):
         v = np.zeros(A.shape[0])
-        plus = np.unique(P.face_copies[:, 1, :])
-        minus = np.unique(P.face_copies[:, 0, :])
-        only_plus = np.setdiff1d(plus, minus)
-        assert only_plus.size > 0
+        v[3 * np.nonzero(plus)[0] + d] = 1.0
+        r = A @ v
+        assert np.abs(r[free]).max() <= 1e-12 * abs(A).max()
+        # and it is not blind to the same motion of a piece that crosses
+        # the plane (the pin has teeth)
+        w = np.zeros(A.shape[0])
+        w[3 * np.nonzero(ix >= m - 1)[0] + d] = 1.0
+        assert np.abs((A @ w)[free]).max() > 1e-3 * abs(A).max()
 
 
 def test_A_patch_test_linear_field():
@@ -269,3 +292,182 @@ def test_Q2_equals_storage_term_plus_complex_step_flux_derivative():
         g = P.aperture.astype(complex) + np.where(open_, jump, 0.0)
         d = _flux_residual_rows(P, g).imag / hstep
         assert np.allclose(Fu @ du, d, rtol=1e-10, atol=1e-12 * np.abs(d).max())
+
+
+# ---------------------------------------------------------------- slip and open faces
+def _normal(seed: int, stream: int, i: int) -> float:
+    """Standard normal by Box-Muller from the counter draws 2i and 2i+1."""
+    u1 = 1.0 - fracgen.uniform(seed, stream, 2 * i)
+    u2 = fracgen.uniform(seed, stream, 2 * i + 1)
+    return float(np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2))
+
+
+def _slip_data(P, f):
+    """Seeded slip data of face f: t_N = -(5 + 10 U) MPa (stream 3), slip
+    direction at angle 2 pi U (stream 4), |Delta g_T| = 1e-4 exp(0.5 Z) m
+    (stream 5)."""
+    s = P.cfg.seed
+    tN = -(5.0 + 10.0 * fracgen.uniform(s, 3, f))
+    phi = 2.0 * np.pi * fracgen.uniform(s, 4, f)
+    dg = 1e-4 * np.exp(0.5 * _normal(s, 5, f))
+    return tN, np.array([np.cos(phi), np.sin(phi)]), dg
+
+
+TAN_THETA = np.tan(np.deg2rad(30.0))   # friction angle 30 degrees, cohesion 0
+
+
+def _friction_law(dgT, tN):
+    """t_T* = tau_max(t_N) Delta g_T / ||Delta g_T|| with the static Coulomb
+    limit tau_max = c - t_N tan(theta) (Sec. 2.1); written with sqrt(x.x)
+    so that a complex step differentiates it."""
+    tau = 0.0 - tN * TAN_THETA
+    return tau * dgT / np.sqrt(dgT[0] * dgT[0] + dgT[1] * dgT[1])
+
+
+def _frame(a):
+    R = np.zeros((3, 3))
+    R[0, a] = R[1, (a + 1) % 3] = R[2, (a + 2) % 3] = 1.0
+    return R
+
+
+def _k(P, f):
+    # k = Ebar_f / (8 h): the generator's reading of the paper's k
+    return P.Ebar_face[f] / (8.0 * P.h)
+
+
+def test_C2_slip_rows_are_the_friction_law_derivative():
+    """Eq. C2def on a slip face: the normal row is (mu_N, [[eta_N]]) as for
+    stick; the tangential rows are -(1/k)(mu_T, dt_T*/dDelta g_T .
+    [[eta_T]]).  The derivative is taken here by complex step of the
+    friction law itself at the seeded slip data, and the face integral of
+    the jump of a nodal basis function is +-h^2/4 (+ copy, - copy), so C2's
+    (face, copy) block is fixed entry by entry.  A flipped sign of the
+    derivative, a missing tangential projection (I - g g^T), k for 1/k or
+    swapped sides all fail it."""
+    P = fracgen.generate("planes64", N=6, p_stick=0.2, p_slip=0.7, seed=5)
+    C2 = osp.csr(P.C2).toarray()
+    dirichlet = P.dirichlet.reshape(-1, 3)
+    w = P.h ** 2 / 4.0
+    slip = np.nonzero(P.state == 1)[0]
+    assert slip.size > 10
+    checked = 0
+    for f in slip:
+        tN, ghat, dg = _slip_data(P, f)
+        D = np.zeros((2, 2))
+        for j in range(2):
+            e = np.zeros(2, dtype=complex)
+            e[j] = 1e-30j
+            D[:, j] = _friction_law(dg * ghat + e, tN).imag / 1e-30
+        R = _frame(P.face_geom[f, 0])
+        cm, cp = P.face_copies[f]
+        for side, sg in ((0, -1.0), (1, 1.0)):
+            for k in range(4):
+                c = (cm, cp)[side][k]
+                got = C2[3 * f:3 * f + 3, 3 * c:3 * c + 3]
+                if cm[k] == cp[k]:
+                    # a fracture tip: one copy, zero jump
+                    assert np.all(got == 0.0)
+                    continue
+                jump = sg * w * R                 # d/du_c of the face integral of [[u]] in (n, t1, t2)
+                exp = np.vstack([jump[0], -(1.0 / _k(P, f)) * D @ jump[1:]])
+                exp[:, dirichlet[c]] = 0.0
+                assert np.allclose(got, exp, rtol=1e-12, atol=1e-14 * np.abs(exp).max())
+                checked += 1
+    assert checked > 40
+
+
+def test_H_slip_and_open_blocks_follow_the_linearisation():
+    """Eq. Hdef.  An open face's row and column of H hold only its diagonal
+    block -(1/k)(mu, mu) = -(h^2/k) I (no j_t on open faces, Sec. 2.2 item
+    3).  A slip face's diagonal block is its stick block (the j_t part, set
+    by geometry and material alone) plus -(h^2/k) on the tangential diagonal
+    and (h^2/k) dt_T*/dt_N in the tangential rows of the normal column, the
+    derivative by complex step of t_T* in t_N.  Compared with the same
+    instance in all-stick state.  A flipped friction term, h^2 k for h^2/k
+    or j_t kept on open faces fail it."""
+    over = dict(N=6, seed=5)
+    P = fracgen.generate("planes64", p_stick=0.2, p_slip=0.5, **over)
+    P0 = fracgen.generate("planes64", p_stick=1.0, p_slip=0.0, **over)
+    assert np.array_equal(P.face_geom, P0.face_geom) and np.array_equal(P.E_cell, P0.E_cell)
+    H = osp.csr(P.H).toarray()
+    H0 = osp.csr(P0.H).toarray()
+    kinds = {0: 0, 1: 0, 2: 0}
+    for f in range(P.n_face):
+        blk = H[3 * f:3 * f + 3, 3 * f:3 * f + 3]
+        hk = P.h ** 2 / _k(P, f)
+        st = int(P.state[f])
+        kinds[st] += 1
+        if st == 0:
+            assert np.array_equal(blk, H0[3 * f:3 * f + 3, 3 * f:3 * f + 3])
+        elif st == 2:
+            assert np.allclose(blk, -hk * np.eye(3), rtol=1e-14, atol=0)
+            row = H[3 * f:3 * f + 3].copy()
+            row[:, 3 * f:3 * f + 3] = 0.0
+            col = H[:, 3 * f:3 * f + 3].copy()
+            col[3 * f:3 * f + 3] = 0.0
+            assert not row.any() and not col.any()
+        else:
+            tN, ghat, dg = _slip_data(P, f)
+            dtdn = _friction_law(dg * ghat + 0j, tN + 1e-30j).imag / 1e-30
+            exp = np.zeros((3, 3))
+            exp[1, 1] = exp[2, 2] = -hk
+            exp[1:, 0] = hk * dtdn
+            diff = blk - H0[3 * f:3 * f + 3, 3 * f:3 * f + 3]
+            assert np.allclose(diff, exp, rtol=1e-12, atol=1e-14 * hk)
+    assert min(kinds.values()) > 5
+
+
+def _edge_pairs(P):
+    """Pairs of faces sharing a grid edge (the TPFA connections of every
+    fracture, intersections included), with a coplanarity flag."""
+    N1 = P.N + 1
+    edges = {}
+    for f in range(P.n_face):
+        a, m, p, q = P.face_geom[f]
+        t1, t2 = (a + 1) % 3, (a + 2) % 3
+        for e in range(4):
+            g = [0, 0, 0]
+            g[a] = m
+            if e < 2:
+                g[t1], g[t2], d = p, q + e, t1
+            else:
+                g[t1], g[t2], d = p + e - 2, q, t2
+            edges.setdefault((g[0] + N1 * (g[1] + N1 * g[2])) * 3 + d, []).append(f)
+    out = {}
+    for fs in edges.values():
+        for i in range(len(fs)):
+            for j in range(i + 1, len(fs)):
+                K, L = fs[i], fs[j]
+                cop = (P.face_geom[K, 0] == P.face_geom[L, 0]) and (P.face_geom[K, 1] == P.face_geom[L, 1])
+                out[(min(K, L), max(K, L))] = bool(cop)
+    return out
+
+
+def test_T_is_tpfa_plus_normal_projection_of_jt_over_dt():
+    """Eq. Tdef: T = d[chi, p]_F/dp + (1/dt) j_p with j_p the normal
+    projection of j_t on every pair of coplanar faces, in every state
+    (Sec. 2.2).  Off the diagonal: T_KL = -Ups_K Ups_L / (Ups_K + Ups_L)
+    for every pair of faces sharing an edge (series TPFA, one-sided
+    2 C_f / mu, C_f = C_f0 + a^3 / 12, Eq. cond_def), plus H0_KL[N, N] / dt
+    for coplanar pairs, H0 the stabilisation of the same instance in
+    all-stick state (j_t then spans every coplanar edge); zero elsewhere.
+    Dropping the 1/dt, projecting on a tangential component, a harmonic
+    mean (twice the series value) or no flow across intersections fail it."""
+    over = dict(N=6, seed=2)
+    P = fracgen.generate("planes64", **over)
+    P0 = fracgen.generate("planes64", p_stick=1.0, p_slip=0.0, **over)
+    assert np.array_equal(P.aperture, P0.aperture)
+    T = osp.csr(P.T).toarray()
+    H0 = osp.csr(P0.H).toarray()
+    ups = 2.0 * (P.C_f0 + P.aperture ** 3 / 12.0) / P.mu
+    exp = np.zeros_like(T)
+    pairs = _edge_pairs(P)
+    assert any(pairs.values()) and not all(pairs.values())
+    for (K, L), cop in pairs.items():
+        v = -ups[K] * ups[L] / (ups[K] + ups[L])
+        if cop:
+            v += H0[3 * K, 3 * L] / P.dt
+            assert H0[3 * K, 3 * L] < 0
+        exp[K, L] = exp[L, K] = v
+    off = ~np.eye(P.n_face, dtype=bool)
+    assert np.allclose(T[off], exp[off], rtol=1e-13, atol=1e-15 * np.abs(T).max())

@@ -18,6 +18,8 @@ from oracle.amg import AMG, AmgOptions
 from oracle.fgmres import fgmres
 from oracle.precond import BlockPreconditioner
 
+from fields import assert_fields
+
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -44,7 +46,8 @@ def test_fgmres_matches_dense_solution(tiny, variant):
     # the true residual floors near eps * || |J| |x| || / ||b|| ~ 1e-10 here
     # (tractions are ~1e7 times the displacements); the solution is tighter
     assert r.relres <= 1e-9
-    assert np.linalg.norm(r.x - xs) <= 1e-11 * np.linalg.norm(xs)
+    # every field (u, t, p) on its own scale, not the t-dominated whole norm
+    assert_fields(tiny, r.x, xs, 1e-11, f"{variant} x vs dense")
 
 
 @pytest.mark.parametrize("variant", ["tpu", "tup", "tup_star"])
@@ -158,6 +161,48 @@ def test_fixed_stress_sign_and_bound():
     open_ = P.state == 2
     assert open_.any() and np.all(sk[open_] < 0) and np.all(sk[~open_] == 0)
     assert np.all(np.abs(sk[open_]) <= np.abs(exact[open_]) * (1 + 1e-12))
+
+
+def test_fixed_stress_index_set_is_the_union():
+    """Eq. FS_algebraic takes S1 on K = nz(Q1 column k) U nz(Q2 row k).
+    With p^l != 0 the flux derivative F_u puts neighbouring open faces'
+    copies into row k of Q2, so K2 = nz(Q2 row k) reaches beyond
+    K1 = nz(Q1 column k) and K1 beyond K2 (a stick face next to an open
+    one).  Zero every coupling of S1 between K and the rest: S1' is then
+    block diagonal on (K, rest), Q1 column k lives on K1 and Q2 row k on
+    K2, so (Q2 S1'^-1 Q1)_kk = Q2[k, K] S1[K, K]^-1 Q1[K, k] exactly, and
+    the oracle's local diagonal on S1' must equal that dense product.  With
+    K = K1 or K = K2 alone it does not."""
+    P = fracgen.generate("planes64", N=4, p_stick=0.5, p_slip=0.2, seed=3)
+    b = osp.blocks(P)
+    Q1c, Q2r = b["Q1"].tocsc(), b["Q2"].tocsr()
+    S1 = schur.s1(P, b).tolil()
+    d = dense.blocks_dense(P)
+    tested = 0
+    for k in range(P.n_face):
+        K1 = Q1c.indices[Q1c.indptr[k]:Q1c.indptr[k + 1]][Q1c.data[Q1c.indptr[k]:Q1c.indptr[k + 1]] != 0]
+        K2 = Q2r.indices[Q2r.indptr[k]:Q2r.indptr[k + 1]][Q2r.data[Q2r.indptr[k]:Q2r.indptr[k + 1]] != 0]
+        if np.setdiff1d(K1, K2).size == 0 or np.setdiff1d(K2, K1).size == 0:
+            continue
+        K = np.union1d(K1, K2)
+        rest = np.setdiff1d(np.arange(S1.shape[0]), K)
+        Sp = S1.tocsr().copy().tolil()
+        for i in K:
+            Sp[i, rest] = 0.0
+            Sp[rest, i] = 0.0
+        Sp = Sp.tocsr()
+        Sp.eliminate_zeros()
+        exact = d["Q2"][k] @ np.linalg.solve(Sp.toarray(), d["Q1"][:, k])
+        got = schur.fixed_stress(P, Sp, b)[k]
+        assert abs(got - exact) <= 1e-10 * abs(exact), (k, got, exact)
+        # the same product over K1 or K2 alone misses part of it
+        for part in (K1, K2):
+            alt = d["Q2"][k, part] @ np.linalg.solve(Sp[part][:, part].toarray(), d["Q1"][part, k])
+            assert abs(alt - exact) > 1e-6 * abs(exact)
+        tested += 1
+        if tested == 3:
+            break
+    assert tested == 3
 
 
 def test_fgmres_identity_preconditioner_distinct_eigenvalues():
