@@ -116,9 +116,11 @@ def test_planes64_adjoint_against_oracle(fs, oracle):
 
 
 # per-field bound of the mixed form's solution against the FP64 oracle
-# solution on the network: both stop at a true residual <= 1e-8, so their
-# difference is an error of that size mapped through J^-1
-MIXED_FIELD_BOUND = 1e-7
+# solution on the network (measured 1e-13 .. 5e-13): the FP32 preconditioner
+# changes the Krylov directions at ~1e-7 relative, which moves the
+# minimum-residual solution only to second order (times its ~1e-10 distance
+# from the exact solution)
+MIXED_FIELD_BOUND = 1e-9
 
 
 @pytest.mark.parametrize("variant", ["tpu", "tup"])

@@ -224,7 +224,10 @@ def test_mixed_precision_solve(fs, name, variant):
     e = field_errors(P, xm, ref.x)
     print(f"mixed {name} {variant}: iters {it} (fp64 {it64}) true {true:.2e} x vs fp64 oracle " +
           " ".join(f"{f} {v[0]:.1e}/{v[1]:.1e}" for f, v in e.items()))
-    assert_fields(P, xm, ref.x, 1e-6, f"mixed {name} {variant} x vs FP64 oracle")
+    # measured 1e-13 .. 6e-12 per field: the FP32 preconditioner perturbs
+    # the Krylov directions at 1e-7, and the solution's distance from the
+    # exact one (~1e-10 per field at 1e-8 residual) only to second order
+    assert_fields(P, xm, ref.x, 1e-9, f"mixed {name} {variant} x vs FP64 oracle")
     # mixed vector application: FP32 preconditioner within single-precision error
     w = np.random.default_rng(3).standard_normal(P.n)
     v32 = torch.zeros_like(b)
@@ -233,7 +236,9 @@ def test_mixed_precision_solve(fs, name, variant):
     ctx64.apply_prec(variant, cuda(w), v64)
     e = field_errors(P, v32.cpu().numpy(), v64.cpu().numpy())
     print(f"mixed {name} {variant}: M^-1 w vs fp64 " + " ".join(f"{f} {v[0]:.1e}/{v[1]:.1e}" for f, v in e.items()))
-    assert_fields(P, v32.cpu().numpy(), v64.cpu().numpy(), 1e-3, f"mixed {name} {variant} M^-1 w")
+    # FP32 storage and arithmetic of every inner operator: measured 4e-8 ..
+    # 8e-7 per field
+    assert_fields(P, v32.cpu().numpy(), v64.cpu().numpy(), 1e-5, f"mixed {name} {variant} M^-1 w")
     ctx.close()
 
 
@@ -352,7 +357,7 @@ def test_full_size_bench_configuration(fs):
     # the mixed form against the FP64 form (pinned to the oracle at 64^3),
     # field by field, and its iteration growth
     assert it <= 1.15 * it64
-    e = assert_fields(P, x.cpu().numpy(), x64, 1e-7, "rects128 mixed vs fp64 x")
+    e = assert_fields(P, x.cpu().numpy(), x64, 1e-9, "rects128 mixed vs fp64 x")
     print(f"rects128 tup: mixed iters {it}, fp64 {it64}; mixed vs fp64 " +
           " ".join(f"{f} {v[0]:.1e}/{v[1]:.1e}" for f, v in e.items()))
     # the incomplete t-u-p form on the same setup: mixed mode restarts from
