@@ -16,8 +16,12 @@ Workload (default): 128^3 unit-cube grid, ten seeded fracture rectangles,
 for the paper's private meshes.  Matrices are several GB, far above the
 129 MB L2, so no flush is needed between steps.
 
---impl reference times the CPU oracle (tests' reference implementation) on a
-bounded sample of the same workload family and scales it to the full size.
+--impl reference times the CPU oracle (the tests' reference implementation)
+on a bounded sample: the same workload family at --cpu-sample-n cells per
+side (32 by default, about 4 s per solve on one core), reported as measured,
+with the sample's own size in its config.  --cpu-full runs the oracle at the
+workload's full size instead (minutes per solve at 128^3; not part of the
+default run).
 """
 from __future__ import annotations
 
@@ -35,15 +39,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve s to rel-res 1e-8 (FP32-AMG vs FP64) at 1 GB300; V-cycle HBM GB/s % peak"
 WORKLOADS = {
-    "rects128": "128^3 grid, 10 seeded fracture rectangles, 60/30/10 stick/slip/open",
-    "planes64": "64^3 grid, three central fracture planes, 60/30/10 stick/slip/open",
-    "network96": "96^3 grid, fracture planes every 8 cells, 50/40/10 stick/slip/open",
-    "tiny8": "8^3 grid, one fracture plane, all stick",
+    "rects128": "unit cube, 10 seeded fracture rectangles (extents 0.2-0.8), 60/30/10 stick/slip/open",
+    "planes64": "unit cube, three central fracture planes, 60/30/10 stick/slip/open",
+    "network96": "unit cube, fracture planes every 8 cells, 50/40/10 stick/slip/open",
+    "tiny8": "unit cube, one fracture plane, all stick",
 }
-
-
-# unknowns of each full workload (seed 0), known from the generator
-FULL_UNKNOWNS = {"rects128": 6709355, "planes64": 911640, "network96": 4995648, "tiny8": 2686}
 
 
 def parse():
@@ -67,7 +67,10 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=1,
                     help="timed adjoint solves + aperture gradients after the timed region (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample-n", type=int, default=32)
+    ap.add_argument("--cpu-sample-n", type=int, default=32,
+                    help="grid size of the oracle's bounded sample (cells per side)")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="time the oracle at the workload's full size (long: minutes per solve)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--verbose", type=int, default=0, help="library diagnostics (setup phase times) to stderr")
     ap.add_argument("--mode", default="bench", choices=["bench", "vcycle"],
@@ -163,26 +166,40 @@ print(json.dumps(dict(n=P.n, setup=t1 - t0, solve=t2 - t1, iters=r.iters, relres
 """
 
 
-def run_oracle_sample(workload, n_cells, variant, tol, maxit):
+def run_oracle_sample(workload, n_cells, variant, tol, maxit, timeout=900):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     code = ORACLE_SNIPPET.format(root=ROOT, workload=workload, n=n_cells, variant=variant, tol=tol, maxit=maxit)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline(args, n_full):
-    s = run_oracle_sample(args.workload, args.cpu_sample_n, args.variant, args.tol, args.maxit)
+FULL_N = {"rects128": 128, "planes64": 64, "network96": 96, "tiny8": 8}
+
+
+def oracle_cells(args) -> int:
+    """Cells per side of the oracle's run: the bounded sample, or the full
+    workload with --cpu-full (or when the sample is not smaller)."""
+    full = args.N or FULL_N[args.workload]
+    return full if args.cpu_full else min(args.cpu_sample_n, full)
+
+
+def cpu_baseline(args):
+    n = oracle_cells(args)
+    s = run_oracle_sample(args.workload, n, args.variant, args.tol, args.maxit,
+                          timeout=7200 if args.cpu_full else 900)
     t = s["setup"] + s["solve"]
-    scale = n_full / s["n"]
-    return {"value": t * scale, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle {args.variant} setup+solve of the same workload family at "
-                       f"{args.cpu_sample_n}^3 ({s['n']} unknowns, {s['iters']} iters, "
-                       f"{t:.2f} s) scaled linearly by unknowns to {n_full}")}
+    full = n == (args.N or FULL_N[args.workload])
+    return {"value": t, "unit": "s", "cores": 1, "nproc": os.cpu_count(), "kind": "oracle",
+            "setup_s": s["setup"], "solve_s": s["solve"], "iters": s["iters"], "relres": s["relres"],
+            "unknowns": s["n"], "grid": n,
+            "sample": (f"oracle (FP64, one thread) {args.variant} setup+solve measured at {n}^3 "
+                       f"({s['n']} unknowns, {s['iters']} iterations)"
+                       + ("" if full else ", the bounded sample of the same workload family; not scaled"))}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -191,23 +208,30 @@ def reference(args, rank):
         return
     import fracgen
     fracgen.build()
-    n_full = FULL_UNKNOWNS[args.workload]
-    times = []
+    n = oracle_cells(args)
+    times, setups, solves = [], [], []
     last = None
     for k in range(args.warmup + args.steps):
-        s = run_oracle_sample(args.workload, args.cpu_sample_n, args.variant, args.tol, args.maxit)
+        s = run_oracle_sample(args.workload, n, args.variant, args.tol, args.maxit,
+                              timeout=7200 if args.cpu_full else 900)
         last = s
         if k >= args.warmup:
-            times.append((s["setup"] + s["solve"]) * n_full / s["n"])
+            times.append(s["setup"] + s["solve"])
+            setups.append(s["setup"])
+            solves.append(s["solve"])
     v = statistics.mean(times)
-    sample = (f"oracle {args.variant} setup+solve at {args.cpu_sample_n}^3 ({last['n']} unknowns, "
-              f"{last['iters']} iters) per step, scaled linearly by unknowns to {n_full}")
+    sample = (f"oracle (FP64, one thread) {args.variant} setup+solve measured at {n}^3 "
+              f"({last['n']} unknowns, {last['iters']} iterations) per step; not scaled")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "variant": args.variant},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": f"{args.workload} family at {n}^3", "description": WORKLOADS[args.workload],
+                   "grid": n, "unknowns": last["n"], "variant": args.variant, "tol": args.tol},
+        "breakdown": {"setup_s": statistics.mean(setups), "solve_s": statistics.mean(solves),
+                      "iters": last["iters"], "relres": last["relres"]},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "nproc": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -493,7 +517,7 @@ def ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(args, P.n)
+            cpu = cpu_baseline(args)
         except Exception as e:  # noqa: BLE001
             cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
 
