@@ -213,6 +213,72 @@ int fc_solve(fc_ctx *ctx, int variant, const double *d_b, double *d_x, double to
 int fc_solve_host(fc_ctx *ctx, int variant, const double *h_b, double *h_x, double tol,
                   int maxit, int *iters, double *relres);
 
+/* ---------------- seeded instances assembled on the device ---------------- */
+
+/* Fracture layouts of the synthetic unit-cube workloads (stand-ins for the
+ * paper's test meshes, Sec. 4): one x-plane through the centre; three central
+ * planes; n_rect seeded axis-aligned rectangles (extents 0.2-0.8 of the side);
+ * full planes every `spacing` cells on all three axes. */
+enum { FC_GEN_PLANE_X = 0, FC_GEN_PLANES_XYZ = 1, FC_GEN_RECTS = 2, FC_GEN_NETWORK = 3 };
+
+/* Generator parameters.  Contact state per face: stick with probability
+ * p_stick, slip with p_slip, open otherwise.  Young's modulus per cell
+ * E0 exp(sigma_E Z) (median 10 GPa); aperture per face 1e-3 exp(aperture_sigma Z)
+ * m unless d_aperture is given; current pressure p^l = pl_scale U MPa.
+ * beta scales the stabilisation tensor and k = Ebar / (k_scale h)
+ * (<= 0: the defaults 1/4 and 8). */
+typedef struct {
+  int32_t N;                 /* cells per side of the unit cube, [2, 1024] */
+  int32_t layout;            /* FC_GEN_* */
+  int32_t n_rect;            /* FC_GEN_RECTS: number of rectangles */
+  int32_t spacing;           /* FC_GEN_NETWORK: cells between planes */
+  double p_stick, p_slip;
+  double sigma_E, aperture_sigma, pl_scale;
+  double beta, k_scale;
+  const double *d_aperture;  /* optional DEVICE array of n_aperture apertures (m),
+                                one per fracture face in face order; NULL: drawn */
+  int32_t n_aperture;        /* must equal the layout's face count when d_aperture is set */
+} fc_gen_config;
+
+/* One assembled instance.  Every pointer is DEVICE memory owned by the
+ * instance (free it with fc_instance_free).  J feeds fc_setup directly. */
+typedef struct {
+  fc_blocks J;               /* the seven blocks of Eq. block_def */
+  const double *d_b;         /* right-hand side, U(-1, 1), 0 on roller dofs; length n */
+  int64_t n;                 /* 3 n_node + 4 n_face */
+  int32_t n_node, n_face, grid_n;
+  double h, dt, nu;          /* cell size, flow time step, Poisson ratio */
+  const int8_t *d_state;     /* n_face: 0 stick, 1 slip, 2 open */
+  const int8_t *d_dirichlet; /* 3 n_node: 1 on roller dofs */
+  const double *d_aperture;  /* n_face (m) */
+  const double *d_pl;        /* n_face: current pressures p^l (MPa) */
+  const double *d_ebar;      /* n_face: mean Young's modulus of the two cells (MPa) */
+  const int32_t *d_face_geom;   /* 4 n_face: normal axis, plane, in-plane cell p, q */
+  const int32_t *d_face_copies; /* 8 n_face: node copies of the minus side (corners 0-3), then plus */
+  const int32_t *d_node_grid;   /* n_node: grid node i + (N+1)(j + (N+1) k) of each copy */
+  void *owner;               /* library-internal */
+} fc_instance;
+
+/* Defaults of the four workload families for grid size N (the paper's state
+ * mix 60/30/10, sigma_E 1, lognormal apertures; one all-stick plane with
+ * sigma_E 0.5 and a = 1e-3 m; ten rectangles; planes every 8 cells with
+ * 50/40/10). */
+void fc_default_gen_config(fc_gen_config *cfg, int layout, int N);
+
+/* Assemble a seeded instance on the device, on `cuda_stream` (NULL: legacy
+ * default stream), synchronising it before returning: the unit cube of N^3
+ * trilinear hexahedra with rollers on its faces; fracture faces of the
+ * layout; grid nodes split across them (one copy per group of cells joined
+ * through unfractured faces, Sec. 2.2); the blocks A, C1, Q1, C2, H, Q2, T of
+ * Eq. block_def for the drawn contact states (Eq. C2def, Eq. Hdef, Eq. Q2def
+ * with Eq. Q2vsQ1, Eq. Tdef); b.  Counter-based draws: the result depends only
+ * on (cfg, seed).  *out receives the instance.  Errors: FC_BAD_ARG (sizes,
+ * layout, probabilities, n_aperture), FC_OOM, FC_CUDA_ERROR;
+ * fc_generate_error() describes the last failure of this thread. */
+int fc_generate(const fc_gen_config *cfg, uint64_t seed, void *cuda_stream, fc_instance **out);
+const char *fc_generate_error(void);
+void fc_instance_free(fc_instance *inst);
+
 /* ---------------- adjoint (transposed system) ---------------- */
 /* The adjoint data (transposed blocks, transposed preconditioner blocks and
  * transposed AMG cycles) is built on the first adjoint call after fc_setup. */

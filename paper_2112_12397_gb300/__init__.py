@@ -24,7 +24,8 @@ FC_M_LEVEL, FC_M_PROLONG, FC_M_S1, FC_M_STILDE, FC_M_S2TILDE = range(5)
 VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP, "tup_star": FC_TUP_STAR}
 
 # exported symbols declared by include/fracsolve.h
-SYMBOLS = ["fc_default_options", "fc_create", "fc_setup", "fc_update", "fc_set_geometric_fs", "fc_spmv", "fc_residual", "fc_residual_noalloc",
+SYMBOLS = ["fc_default_gen_config", "fc_generate", "fc_generate_error", "fc_instance_free",
+           "fc_default_options", "fc_create", "fc_setup", "fc_update", "fc_set_geometric_fs", "fc_spmv", "fc_residual", "fc_residual_noalloc",
            "fc_apply_prec", "fc_solve", "fc_spmv_adjoint", "fc_apply_prec_adjoint", "fc_solve_adjoint",
            "fc_vcycle_adjoint", "fc_aperture_gradient",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
@@ -62,6 +63,28 @@ class fc_blocks(C.Structure):
 
 LIB_HOOKS_PATH = os.path.join(_HERE, "lib", "libfracsolve_testhooks.so")
 
+FC_GEN_PLANE_X, FC_GEN_PLANES_XYZ, FC_GEN_RECTS, FC_GEN_NETWORK = range(4)
+# the four workload families by name: (layout, cells per side)
+GEN_PRESETS = {"tiny8": (FC_GEN_PLANE_X, 8), "planes64": (FC_GEN_PLANES_XYZ, 64),
+               "rects128": (FC_GEN_RECTS, 128), "network96": (FC_GEN_NETWORK, 96)}
+
+
+class fc_gen_config(C.Structure):
+    _fields_ = [("N", C.c_int32), ("layout", C.c_int32), ("n_rect", C.c_int32), ("spacing", C.c_int32),
+                ("p_stick", C.c_double), ("p_slip", C.c_double), ("sigma_E", C.c_double),
+                ("aperture_sigma", C.c_double), ("pl_scale", C.c_double), ("beta", C.c_double),
+                ("k_scale", C.c_double), ("d_aperture", C.c_void_p), ("n_aperture", C.c_int32)]
+
+
+class fc_instance(C.Structure):
+    _fields_ = [("J", fc_blocks), ("d_b", C.c_void_p), ("n", C.c_int64), ("n_node", C.c_int32),
+                ("n_face", C.c_int32), ("grid_n", C.c_int32), ("h", C.c_double), ("dt", C.c_double),
+                ("nu", C.c_double), ("d_state", C.c_void_p), ("d_dirichlet", C.c_void_p),
+                ("d_aperture", C.c_void_p), ("d_pl", C.c_void_p), ("d_ebar", C.c_void_p),
+                ("d_face_geom", C.c_void_p), ("d_face_copies", C.c_void_p), ("d_node_grid", C.c_void_p),
+                ("owner", C.c_void_p)]
+
+
 _lib = None
 _lib_hooks = None
 
@@ -94,6 +117,10 @@ def _open(path: str, build_if_missing: bool):
     vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     pi32, pi64, pd, pint = C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int)
     sig = {
+        "fc_default_gen_config": (None, [C.POINTER(fc_gen_config), C.c_int, C.c_int]),
+        "fc_generate": (C.c_int, [C.POINTER(fc_gen_config), C.c_uint64, vp, C.POINTER(C.POINTER(fc_instance))]),
+        "fc_generate_error": (C.c_char_p, []),
+        "fc_instance_free": (None, [C.POINTER(fc_instance)]),
         "fc_default_options": (None, [C.POINTER(fc_options)]),
         "fc_create": (C.c_int, [C.POINTER(vp), C.POINTER(fc_options), vp]),
         "fc_setup": (C.c_int, [vp, C.POINTER(fc_blocks)]),
@@ -357,3 +384,101 @@ def context_for(problem, options: fc_options | None = None, stream=None, lib=Non
     blocks = device_blocks(problem)
     ctx.setup(blocks, problem.n_node, problem.n_face)
     return ctx
+
+
+# ------------------------------------------------------------------ device generator
+class _DeviceArray:
+    """A view of library-owned device memory for torch.as_tensor (no copy)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3}
+
+
+_TYPESTR = {"i4": "<i4", "f8": "<f8", "i1": "|i1"}
+
+
+def gen_config(preset: str, **over) -> fc_gen_config:
+    """fc_gen_config of a workload family (tiny8, planes64, rects128,
+    network96) with field overrides (N, p_stick, p_slip, sigma_E,
+    aperture_sigma, pl_scale, n_rect, spacing, beta, k_scale)."""
+    layout, N = GEN_PRESETS[preset]
+    c = fc_gen_config()
+    load().fc_default_gen_config(C.byref(c), layout, int(over.pop("N", N)))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+class Instance:
+    """A seeded instance assembled on the device by fc_generate.  The blocks
+    and vectors are torch views of memory the library owns; they stay valid
+    until close()."""
+
+    def __init__(self, cfg: fc_gen_config, seed: int = 0, stream=None, aperture=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("fc_generate needs a CUDA device; no CPU path exists")
+        self.lib = load()
+        self._aper = None
+        if aperture is not None:
+            self._aper = aperture.to(device="cuda", dtype=torch.float64).contiguous()
+            cfg.d_aperture = self._aper.data_ptr()
+            cfg.n_aperture = self._aper.numel()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        p = C.POINTER(fc_instance)()
+        rc = self.lib.fc_generate(C.byref(cfg), int(seed), C.c_void_p(st.cuda_stream), C.byref(p))
+        if rc != FC_OK:
+            raise FcError(rc, self.lib.fc_strerror(rc).decode() + ": " + self.lib.fc_generate_error().decode())
+        self._p = p
+        self.inst = p.contents
+        self.n_node, self.n_face, self.n = self.inst.n_node, self.inst.n_face, self.inst.n
+        self.h, self.dt, self.nu = self.inst.h, self.inst.dt, self.inst.nu
+
+    def _view(self, ptr, n, t):
+        import torch
+        if n == 0:
+            dt = {"i4": torch.int32, "f8": torch.float64, "i1": torch.int8}[t]
+            return torch.zeros(0, dtype=dt, device="cuda")
+        return torch.as_tensor(_DeviceArray(ptr, n, _TYPESTR[t]), device="cuda")
+
+    def blocks(self) -> dict:
+        """name -> (row_ptr, col_idx, val, n_brows, n_bcols, br, bc), the
+        layout Context.setup takes."""
+        out = {}
+        for name in ("A", "C1", "Q1", "C2", "H", "Q2", "T"):
+            m = getattr(self.inst.J, name)
+            out[name] = (self._view(m.d_row_ptr, m.n_brows + 1, "i4"), self._view(m.d_col_idx, m.nnzb, "i4"),
+                         self._view(m.d_val, m.nnzb * m.br * m.bc, "f8"), m.n_brows, m.n_bcols, m.br, m.bc)
+        return out
+
+    @property
+    def b(self):
+        return self._view(self.inst.d_b, self.n, "f8")
+
+    def field(self, name: str):
+        """Per-face or per-copy arrays: state, dirichlet, aperture, pl, ebar,
+        face_geom (4 per face), face_copies (8 per face), node_grid."""
+        nf, nn = self.n_face, self.n_node
+        ptr, n, t = {"state": (self.inst.d_state, nf, "i1"), "dirichlet": (self.inst.d_dirichlet, 3 * nn, "i1"),
+                     "aperture": (self.inst.d_aperture, nf, "f8"), "pl": (self.inst.d_pl, nf, "f8"),
+                     "ebar": (self.inst.d_ebar, nf, "f8"), "face_geom": (self.inst.d_face_geom, 4 * nf, "i4"),
+                     "face_copies": (self.inst.d_face_copies, 8 * nf, "i4"),
+                     "node_grid": (self.inst.d_node_grid, nn, "i4")}[name]
+        return self._view(ptr, n, t)
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self.lib.fc_instance_free(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def generate(preset: str, seed: int = 0, stream=None, aperture=None, **over) -> Instance:
+    """fc_generate for a workload family with overrides (see gen_config)."""
+    return Instance(gen_config(preset, **over), seed, stream, aperture)
