@@ -485,7 +485,9 @@ def ours(args, rank, world, local_rank):
         adjoint = {"solve_s": statistics.mean(ts) / 1e3, "iters": it_a, "relres": rr_a,
                    "aperture_gradient_ms": statistics.mean(tg), "dk_entries": int(dk["val"].numel())}
 
-    # end to end through the C-ABI with host buffers
+    # end to end through the C-ABI with host buffers: fc_setup_host copies
+    # the seven blocks from pinned host memory, fc_solve_host copies b in and
+    # x out
     e2e = None
     if args.e2e_steps > 0:
         host = {}
@@ -496,23 +498,52 @@ def ours(args, rank, world, local_rank):
             h2d += sum(a.numel() * a.element_size() for a in (rp, ci, val))
         hb = torch.from_numpy(P.b).pin_memory()
         hx = torch.zeros_like(hb).pin_memory()
-        dev = {k: tuple(torch.empty_like(a, device="cuda") for a in v[:3]) + tuple(v[3:]) for k, v in host.items()}
         h2d += hb.numel() * 8
         d2h = hx.numel() * 8
         times = []
         for k in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            for name in host:
-                for dst, src in zip(dev[name][:3], host[name][:3]):
-                    dst.copy_(src, non_blocking=True)
-            ctx.setup(dev, P.n_node, P.n_face)
+            ctx.setup_host(host, P.n_node, P.n_face)
             rc, it, rr = ctx.solve_host(args.variant, hb, hx, args.tol, args.maxit, allow_fail=True)
             torch.cuda.synchronize()
             if k > 0:
                 times.append(time.perf_counter() - t0)
         e2e = {"value": statistics.mean(times), "unit": "s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+               "d2h_bytes_per_step": int(d2h), "api": "fc_setup_host + fc_solve_host"}
+        del host
+
+    # the instance assembled on the device by fc_generate (same seed and
+    # workload), and a step that starts from the seed: generate + setup +
+    # solve with x copied to the host
+    generator = None
+    if args.e2e_steps > 0 and not args.N:
+        gcfg = dict(seed=rank)
+        inst = fs.generate(args.workload, **gcfg)
+        inst.close()
+        gen_ms, seed_s = [], []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            inst = fs.generate(args.workload, **gcfg)
+            t1 = time.perf_counter()
+            ctx.setup(inst.blocks(), inst.n_node, inst.n_face)
+            xs = torch.zeros_like(inst.b)
+            rc, it_g, rr_g = ctx.solve(args.variant, inst.b, xs, args.tol, args.maxit, allow_fail=True)
+            hx.copy_(xs)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            if k > 0:
+                gen_ms.append((t1 - t0) * 1e3)
+                seed_s.append(t2 - t0)
+            bytes_out = sum(a.numel() * a.element_size() for v in inst.blocks().values() for a in v[:3])
+            same = all(torch.equal(a, b) for v, w in zip(inst.blocks().values(), blocks.values())
+                       for a, b in zip(v[:2], w[:2]))
+            inst.close()
+        generator = {"fc_generate_ms": statistics.mean(gen_ms), "bytes_of_blocks": int(bytes_out),
+                     "GBps_written": bytes_out / (statistics.mean(gen_ms) * 1e-3) / 1e9,
+                     "patterns_equal_host_generator": bool(same),
+                     "e2e_from_seed_s": statistics.mean(seed_s), "iters": it_g, "relres": rr_g}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -556,6 +587,7 @@ def ours(args, rank, world, local_rank):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "generator": generator,
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -133,9 +133,18 @@ int fc_create(fc_ctx **ctx, const fc_options *opt, void *cuda_stream);
  * this returns.  Calling it again replaces the operator.  Every block's
  * structure is checked on the device before use (row pointers from 0 to
  * nnzb, non-decreasing; columns in range and strictly increasing per row).
+ * The contact states take no argument of their own: they are carried by the
+ * blocks (the rows of C2 and Q2 and the blocks of H, Eq. block_def).
  * Errors: FC_BAD_ARG (inconsistent sizes, row pointers or columns),
  * FC_SINGULAR_BLOCK, FC_OOM, FC_INTERNAL, FC_CUDA_ERROR. */
 int fc_setup(fc_ctx *ctx, const fc_blocks *J);
+
+/* fc_setup with every array of J (row pointers, columns, values of the
+ * seven blocks) in HOST memory: the library copies them to the device on the
+ * context's stream (asynchronously from pinned memory) and keeps the copies
+ * as its own.  The caller guarantees that each host array holds the entries
+ * its sizes state.  Same checks, errors and results as fc_setup. */
+int fc_setup_host(fc_ctx *ctx, const fc_blocks *J);
 
 /* Replace the algebraic fixed stress of S~2 (Eq. FS_algebraic) by the
  * geometric one (Eq. FS, the cheaper form the paper starts from) at the next

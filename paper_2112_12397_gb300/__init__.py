@@ -25,7 +25,7 @@ VARIANTS = {"tpu": FC_TPU, "tup": FC_TUP, "tup_star": FC_TUP_STAR}
 
 # exported symbols declared by include/fracsolve.h
 SYMBOLS = ["fc_default_gen_config", "fc_generate", "fc_generate_error", "fc_instance_free",
-           "fc_default_options", "fc_create", "fc_setup", "fc_update", "fc_set_geometric_fs", "fc_spmv", "fc_residual", "fc_residual_noalloc",
+           "fc_default_options", "fc_create", "fc_setup", "fc_setup_host", "fc_update", "fc_set_geometric_fs", "fc_spmv", "fc_residual", "fc_residual_noalloc",
            "fc_apply_prec", "fc_solve", "fc_spmv_adjoint", "fc_apply_prec_adjoint", "fc_solve_adjoint",
            "fc_vcycle_adjoint", "fc_aperture_gradient",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
@@ -124,6 +124,7 @@ def _open(path: str, build_if_missing: bool):
         "fc_default_options": (None, [C.POINTER(fc_options)]),
         "fc_create": (C.c_int, [C.POINTER(vp), C.POINTER(fc_options), vp]),
         "fc_setup": (C.c_int, [vp, C.POINTER(fc_blocks)]),
+        "fc_setup_host": (C.c_int, [vp, C.POINTER(fc_blocks)]),
         "fc_update": (C.c_int, [vp, C.POINTER(fc_blocks)]),
         "fc_set_geometric_fs": (C.c_int, [vp, vp, vp, d]),
         "fc_spmv": (C.c_int, [vp, vp, vp]),
@@ -177,6 +178,15 @@ def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
 
+def _host_ptr(a) -> int:
+    """Address of a contiguous host array (numpy or CPU tensor)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return int(a.ctypes.data)
+    assert a.device.type == "cpu" and a.is_contiguous()
+    return int(a.data_ptr())
+
+
 class Context:
     """One fc_ctx bound to the current CUDA device and a CUDA stream."""
 
@@ -228,6 +238,22 @@ class Context:
         int32/int32/float64 CUDA tensors."""
         J = self._blocks(blocks, n_node, n_face)
         self._check(self.lib.fc_setup(self.h, C.byref(J)), self.h)
+        self.n = 3 * n_node + 4 * n_face
+        self.n_node, self.n_face = n_node, n_face
+
+    def setup_host(self, blocks: dict, n_node: int, n_face: int):
+        """fc_setup_host: the same blocks dict with int32/int32/float64 CPU
+        tensors or numpy arrays (pinned memory makes the copies
+        asynchronous)."""
+        J = fc_blocks()
+        for name in ("A", "C1", "Q1", "C2", "H", "Q2", "T"):
+            rp, ci, val, nbr, nbc, br, bc = blocks[name]
+            m = getattr(J, name)
+            m.n_brows, m.n_bcols, m.br, m.bc = nbr, nbc, br, bc
+            m.nnzb = int(ci.numel() if hasattr(ci, "numel") else ci.size)
+            m.d_row_ptr, m.d_col_idx, m.d_val = (_host_ptr(a) for a in (rp, ci, val))
+        J.n_node, J.n_face = n_node, n_face
+        self._check(self.lib.fc_setup_host(self.h, C.byref(J)), self.h)
         self.n = 3 * n_node + 4 * n_face
         self.n_node, self.n_face = n_node, n_face
 

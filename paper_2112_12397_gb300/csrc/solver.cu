@@ -893,9 +893,13 @@ int fc_create(fc_ctx **out, const fc_options *opt, void *stream) {
   return rc;
 }
 
-int fc_setup(fc_ctx *c, const fc_blocks *J) {
-  if (!c || !J) return FC_BAD_ARG;
-  return run(c, [&]() {
+}  // extern "C"
+
+namespace {
+// The setup of Alg. 1 / Alg. 3 on device blocks J.  `staged` (optional)
+// holds device copies of J's blocks that the context may keep as its own
+// instead of copying them once more.
+int setup_impl(fc_ctx *c, const fc_blocks *J, Bsr<double> *staged) {
     c->ready = false;
     const int nn = J->n_node, nf = J->n_face;
     FS_REQUIRE(nn > 0 && nf >= 0, FC_BAD_ARG, "n_node must be positive");
@@ -914,11 +918,12 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     c->nu = 3LL * nn; c->nt = 3LL * nf; c->n = c->nu + c->nt + nf;
     fs::g_verbose = c->opt.verbose;
     PhaseTimer pt(c->opt.verbose > 0, s, "setup");
-    auto up = [&](const fc_bsr &m) {
+    auto up = [&](const fc_bsr &m, int k) {
+      if (staged) return std::move(staged[k]);
       return upload_bsr(m.n_brows, m.n_bcols, m.br, m.bc, m.nnzb, m.d_row_ptr, m.d_col_idx, m.d_val, s);
     };
-    c->A = up(J->A); c->C1 = up(J->C1); c->Q1 = up(J->Q1); c->C2 = up(J->C2);
-    c->H = up(J->H); c->Q2 = up(J->Q2); c->T = up(J->T);
+    c->A = up(J->A, 0); c->C1 = up(J->C1, 1); c->Q1 = up(J->Q1, 2); c->C2 = up(J->C2, 3);
+    c->H = up(J->H, 4); c->Q2 = up(J->Q2, 5); c->T = up(J->T, 6);
     c->sA = to_sell<double>(c->A.view(), s); c->sC1 = to_sell<double>(c->C1.view(), s);
     c->sQ1 = to_sell<double>(c->Q1.view(), s); c->sC2 = to_sell<double>(c->C2.view(), s);
     c->sH = to_sell<double>(c->H.view(), s); c->sQ2 = to_sell<double>(c->Q2.view(), s);
@@ -956,6 +961,61 @@ int fc_setup(fc_ctx *c, const fc_blocks *J) {
     FS_CUDA(cudaStreamSynchronize(s));
     c->ready = true;
     return FC_OK;
+}
+
+// device copy of a block whose arrays are in host memory
+Bsr<double> stage_host_bsr(const fc_bsr &m, const char *name, cudaStream_t s) {
+  FS_REQUIRE(m.n_brows >= 0 && m.n_bcols >= 0 && m.br > 0 && m.bc > 0 && m.nnzb >= 0 && m.d_row_ptr &&
+                 (m.nnzb == 0 || (m.d_col_idx && m.d_val)),
+             FC_BAD_ARG, std::string("block ") + name + " has inconsistent sizes or null pointers");
+  Bsr<double> B;
+  B.shape(m.n_brows, m.n_bcols, m.br, m.bc);
+  B.nnzb = m.nnzb;
+  B.rp.alloc((size_t)m.n_brows + 1);
+  B.ci.alloc((size_t)std::max<int64_t>(m.nnzb, 1));
+  B.val.alloc((size_t)std::max<int64_t>(m.nnzb, 1) * m.br * m.bc);
+  FS_CUDA(cudaMemcpyAsync(B.rp.p, m.d_row_ptr, sizeof(int) * ((size_t)m.n_brows + 1), cudaMemcpyHostToDevice, s));
+  if (m.nnzb) {
+    FS_CUDA(cudaMemcpyAsync(B.ci.p, m.d_col_idx, sizeof(int) * (size_t)m.nnzb, cudaMemcpyHostToDevice, s));
+    FS_CUDA(cudaMemcpyAsync(B.val.p, m.d_val, sizeof(double) * (size_t)m.nnzb * m.br * m.bc,
+                            cudaMemcpyHostToDevice, s));
+  }
+  return B;
+}
+}  // namespace
+
+extern "C" {
+
+int fc_setup(fc_ctx *c, const fc_blocks *J) {
+  if (!c || !J) return FC_BAD_ARG;
+  return run(c, [&]() { return setup_impl(c, J, nullptr); });
+}
+
+int fc_setup_host(fc_ctx *c, const fc_blocks *J) {
+  if (!c || !J) return FC_BAD_ARG;
+  return run(c, [&]() {
+    const fc_bsr *in[7] = {&J->A, &J->C1, &J->Q1, &J->C2, &J->H, &J->Q2, &J->T};
+    const char *names[7] = {"A", "C1", "Q1", "C2", "H", "Q2", "T"};
+    // sizes first: nothing is read from the host arrays of a block whose
+    // dimensions do not fit the system
+    const int nn = J->n_node, nf = J->n_face;
+    FS_REQUIRE(nn > 0 && nf >= 0, FC_BAD_ARG, "n_node must be positive");
+    const int dims[7][4] = {{nn, nn, 3, 3}, {nn, nf, 3, 3}, {nn, nf, 3, 1}, {nf, nn, 3, 3},
+                            {nf, nf, 3, 3}, {nf, nn, 1, 3}, {nf, nf, 1, 1}};
+    for (int k = 0; k < 7; k++)
+      FS_REQUIRE(in[k]->n_brows == dims[k][0] && in[k]->n_bcols == dims[k][1] && in[k]->br == dims[k][2] &&
+                     in[k]->bc == dims[k][3],
+                 FC_BAD_ARG, std::string("block ") + names[k] + " has inconsistent sizes");
+    Bsr<double> st[7];
+    fc_blocks Jd = *J;
+    fc_bsr *out[7] = {&Jd.A, &Jd.C1, &Jd.Q1, &Jd.C2, &Jd.H, &Jd.Q2, &Jd.T};
+    for (int k = 0; k < 7; k++) {
+      st[k] = stage_host_bsr(*in[k], names[k], c->s);
+      out[k]->d_row_ptr = st[k].rp.p;
+      out[k]->d_col_idx = st[k].ci.p;
+      out[k]->d_val = st[k].val.p;
+    }
+    return setup_impl(c, &Jd, st);
   });
 }
 

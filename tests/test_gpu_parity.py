@@ -278,6 +278,39 @@ def test_solve_host_equals_device(fs):
     assert it == ith and np.array_equal(hx, x.cpu().numpy())
 
 
+def test_setup_from_host_blocks_equals_device_blocks(fs):
+    """fc_setup_host (blocks in host memory, numpy or pinned tensors) builds
+    the same operators as fc_setup: bitwise equal applications and solves."""
+    P = fracgen.generate("network96", N=16, spacing=4)
+    opt = fs.default_options(precision="mixed", coarse_max=60, coarse_max_p=40)
+    cd = fs.context_for(P, opt)
+    hb = {k: (B.row_ptr, B.col_idx, np.ascontiguousarray(B.val).reshape(-1), B.n_brows, B.n_bcols, B.br, B.bc)
+          for k, B in P.blocks().items()}
+    ch = fs.Context(opt)
+    ch.setup_host(hb, P.n_node, P.n_face)
+    pinned = {k: tuple(torch.from_numpy(a).pin_memory() for a in v[:3]) + v[3:] for k, v in hb.items()}
+    cp = fs.Context(opt)
+    cp.setup_host(pinned, P.n_node, P.n_face)
+    b = cuda(P.b)
+    for variant in ("tpu", "tup"):
+        out = []
+        for ctx in (cd, ch, cp):
+            v = torch.zeros_like(b)
+            ctx.apply_prec(variant, b, v)
+            x = torch.zeros_like(b)
+            _, it, _ = ctx.solve(variant, b, x, 1e-8, 400)
+            out.append((v.cpu().numpy(), x.cpu().numpy(), it))
+        for o in out[1:]:
+            assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1]) and o[2] == out[0][2]
+    bad = dict(hb)
+    bad["T"] = (hb["T"][0], hb["T"][1], hb["T"][2], hb["T"][3] + 1) + hb["T"][4:]
+    with pytest.raises(fs.FcError) as e:
+        ch.setup_host(bad, P.n_node, P.n_face)
+    assert e.value.code == fs.FC_BAD_ARG
+    for c in (cd, ch, cp):
+        c.close()
+
+
 # ------------------------------------------------------------------ edge cases
 def test_zero_rhs_nan_rhs_and_maxit(fs):
     P, ctx, _, _ = case("planes8", fs)
