@@ -64,6 +64,10 @@ def parse():
                     help="timed solves per preconditioner variant on one shared setup (0: skip)")
     ap.add_argument("--update-steps", type=int, default=1,
                     help="timed fc_update calls per update case (0: skip)")
+    ap.add_argument("--other-workloads", type=int, default=1,
+                    help="1: after the timed region, measure the other workloads (three planes 64^3 FP64, "
+                         "fracture network 96^3 mixed and FP64, the 64^3 adjoint, seeds 0-2 of the bench "
+                         "workload) on instances from fc_generate; 0: skip")
     ap.add_argument("--adjoint-steps", type=int, default=1,
                     help="timed adjoint solves + aperture gradients after the timed region (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -253,6 +257,105 @@ def field_diffs(a, ref, n_node: int, n_face: int) -> dict:
                   "relmax": float(np.abs(d).max() / max(np.abs(r).max(), 1e-300)),
                   "norm": float(np.linalg.norm(r))}
     return out
+
+
+# ------------------------------------------------------------------ other workloads
+def perturbed_apertures(aperture, seed: int, n_face: int, scale: float = 0.1, stream: int = 12):
+    """a exp(scale Z), Z standard normal by Box-Muller from the generator's
+    counter draws 2f, 2f + 1 of `stream` (the adjoint workload's p_obs run)."""
+    import numpy as np
+
+    import fracgen
+    u1 = np.array([fracgen.uniform(seed, stream, 2 * f) for f in range(n_face)])
+    u2 = np.array([fracgen.uniform(seed, stream, 2 * f + 1) for f in range(n_face)])
+    return aperture * np.exp(scale * np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2))
+
+
+def other_workloads(fs, args, stream):
+    """The workloads besides the bench's own, each assembled on the device by
+    fc_generate (seed 0 unless stated), timed with CUDA events on `stream`
+    outside the bench's timed region: setup and solve times, iterations, FP64
+    true residuals, and per-field differences of the mixed solution from the
+    FP64 one."""
+    import torch
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def run(inst, precision, variant, repeat=2):
+        ctx = fs.Context(fs.default_options(precision=precision, variants=fs.variant_bit(variant)))
+        out = None
+        for _ in range(repeat):
+            x = torch.zeros_like(inst.b)
+            e0, e1, e2 = ev(), ev(), ev()
+            e0.record(stream)
+            ctx.setup(inst.blocks(), inst.n_node, inst.n_face)
+            e1.record(stream)
+            rc, it, rr = ctx.solve(variant, inst.b, x, args.tol, args.maxit, allow_fail=True)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            out = {"setup_s": e0.elapsed_time(e1) / 1e3, "solve_s": e1.elapsed_time(e2) / 1e3, "iters": it,
+                   "relres": rr}
+        return ctx, out, x
+
+    res = {}
+    # three central planes, 64^3, FP64, both variants
+    inst = fs.generate("planes64")
+    res["planes64_fp64"] = {"unknowns": int(inst.n)}
+    for v in ("tpu", "tup"):
+        ctx, o, _ = run(inst, "fp64", v)
+        res["planes64_fp64"][v] = o
+        ctx.close()
+    # the adjoint workload on the same instance: p_obs from a forward solve
+    # with perturbed apertures, then J^T lambda = g, g = p - p_obs
+    ctx, o, x = run(inst, "fp64", "tup", repeat=1)
+    a = inst.field("aperture").cpu().numpy()
+    ia = fs.generate("planes64", aperture=torch.from_numpy(perturbed_apertures(a, 0, inst.n_face)))
+    cq, oq, xq = run(ia, "fp64", "tup", repeat=1)
+    nf = inst.n_face
+    g = torch.zeros_like(inst.b)
+    g[-nf:] = x[-nf:] - xq[-nf:]
+    lam = torch.zeros_like(inst.b)
+    ctx.solve_adjoint("tup", g, lam, args.tol, args.maxit, allow_fail=True)   # builds the J^T data
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    rc, ita, rra = ctx.solve_adjoint("tup", g, lam, args.tol, args.maxit, allow_fail=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res["adjoint64_fp64"] = {"forward": o, "p_obs_forward_iters": oq["iters"],
+                             "adjoint_solve_s": e0.elapsed_time(e1) / 1e3, "adjoint_iters": ita,
+                             "adjoint_relres": rra}
+    for c in (ctx, cq):
+        c.close()
+    ia.close()
+    inst.close()
+    # the fracture network, 96^3, mixed against FP64, both variants
+    inst = fs.generate("network96")
+    res["network96"] = {"unknowns": int(inst.n), "face_share": 4.0 * inst.n_face / inst.n}
+    for v in ("tpu", "tup"):
+        r = {}
+        xs = {}
+        for prec in ("mixed", "fp64"):
+            ctx, r[prec], xs[prec] = run(inst, prec, v)
+            ctx.close()
+        r["mixed_vs_fp64_per_field"] = field_diffs(xs["mixed"].cpu().numpy(), xs["fp64"].cpu().numpy(),
+                                                   inst.n_node, inst.n_face)
+        res["network96"][v] = r
+    inst.close()
+    # seeds 0, 1, 2 of the bench workload (mixed, the bench's variant)
+    steps = []
+    for seed in (0, 1, 2):
+        inst = fs.generate(args.workload, seed=seed)
+        ctx, o, _ = run(inst, "mixed", args.variant)
+        o["seed"], o["unknowns"] = seed, int(inst.n)
+        o["step_s"] = o["setup_s"] + o["solve_s"]
+        steps.append(o)
+        ctx.close()
+        inst.close()
+    res[f"{args.workload}_seeds"] = {"runs": steps,
+                                     "median_step_s": statistics.median([o["step_s"] for o in steps]),
+                                     "median_iters": statistics.median([o["iters"] for o in steps])}
+    return res
 
 
 # ------------------------------------------------------------------ ranks
@@ -545,6 +648,12 @@ def ours(args, rank, world, local_rank):
                      "patterns_equal_host_generator": bool(same),
                      "e2e_from_seed_s": statistics.mean(seed_s), "iters": it_g, "relres": rr_g}
 
+    others = None
+    if args.other_workloads and not args.N:
+        del ctx
+        torch.cuda.empty_cache()
+        others = other_workloads(fs, args, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -588,6 +697,7 @@ def ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "generator": generator,
+        "other_workloads": others,
         "gpu_launches": int(launches),
         "clocks": clk,
     }

@@ -201,6 +201,60 @@ def tentative(agg: np.ndarray, nc: int, B: int) -> sp.csr_matrix:
                          shape=(n * B, nc * B))
 
 
+def rigid_modes(coords: np.ndarray) -> np.ndarray:
+    """The six rigid-body motions of nodes at `coords` (n x 3): three
+    translations and three rotations (x, y, z interleaved per node)."""
+    n = coords.shape[0]
+    Z = np.zeros((3 * n, 6))
+    for d in range(3):
+        Z[d::3, d] = 1.0
+    x, y, z = coords[:, 0], coords[:, 1], coords[:, 2]
+    Z[0::3, 3], Z[1::3, 3] = -y, x
+    Z[1::3, 4], Z[2::3, 4] = -z, y
+    Z[0::3, 5], Z[2::3, 5] = z, -x
+    return Z
+
+
+def tentative_nullspace(agg: np.ndarray, nc: int, B: int, Z: np.ndarray, tol: float = 1e-10):
+    """Tentative prolongator that reproduces the candidate vectors Z (B n x k)
+    on every aggregate (smoothed aggregation with a general near-null space,
+    Vanek, Mandel and Brezina): per aggregate, the thin QR of Z restricted to
+    the aggregate's rows gives the block of P_tent (Q) and the coarse
+    candidates (R), so that P_tent Z_c = Z there.  A column of R whose
+    diagonal falls below tol times the largest (an aggregate too small or too
+    flat to carry all k modes) is a dead coarse dof: its column of P_tent is
+    zero.  Returns (P_tent, Z_c (k nc x k), dead mask over the k nc coarse
+    dofs)."""
+    k = Z.shape[1]
+    rows_p, cols_p, vals_p = [], [], []
+    Zc = np.zeros((k * nc, k))
+    dead = np.zeros(k * nc, dtype=bool)
+    nodes_of = [[] for _ in range(nc)]
+    for i in np.nonzero(agg >= 0)[0]:
+        nodes_of[agg[i]].append(i)
+    for a in range(nc):
+        nodes = np.array(nodes_of[a], dtype=np.int64)
+        r = (B * nodes[:, None] + np.arange(B)).ravel()
+        Q, R = np.linalg.qr(Z[r], mode="complete" if len(r) < k else "reduced")
+        Q, R = Q[:, :k], R[:k]
+        if Q.shape[1] < k:                      # fewer rows than candidates
+            Q = np.hstack([Q, np.zeros((len(r), k - Q.shape[1]))])
+            R = np.vstack([R, np.zeros((k - R.shape[0], k))])
+        diag = np.abs(np.diag(R))
+        off = diag <= tol * max(diag.max(), 1e-300)
+        Q[:, off] = 0.0
+        R[off] = 0.0
+        dead[k * a + np.nonzero(off)[0]] = True
+        Zc[k * a:k * a + k] = R
+        rr, cc = np.nonzero(Q)
+        rows_p.append(r[rr])
+        cols_p.append(k * a + cc)
+        vals_p.append(Q[rr, cc])
+    Pt = sp.csr_matrix((np.concatenate(vals_p), (np.concatenate(rows_p), np.concatenate(cols_p))),
+                       shape=(len(agg) * B, nc * k))
+    return Pt, Zc, dead
+
+
 def apply_blockdiag(Dinv: np.ndarray, r: np.ndarray) -> np.ndarray:
     B = Dinv.shape[1]
     return np.einsum("nij,nj->ni", Dinv, r.reshape(-1, B)).reshape(-1)
@@ -223,13 +277,19 @@ class AMG:
     """Hierarchy and V-cycle for one operator (block size B)."""
 
     def __init__(self, S: sp.csr_matrix, B: int, opt: AmgOptions | None = None,
-                 aggregates: list | None = None):
+                 aggregates: list | None = None, near_null: np.ndarray | None = None):
         """``aggregates``: the (agg, n_coarse) pair of every coarsening step of
         an earlier hierarchy.  Given, the hierarchy is rebuilt on new values
         of S with those aggregates (no strength graph, no MIS-2): the same
-        levels, with D^-1, lambda, P, R and the Galerkin products recomputed."""
+        levels, with D^-1, lambda, P, R and the Galerkin products recomputed.
+        ``near_null``: candidate vectors (rows of S x k), e.g. the six rigid
+        modes of ``rigid_modes``; P_tent then reproduces them aggregate by
+        aggregate (``tentative_nullspace``), every coarse level has k x k
+        blocks, and dead coarse dofs get a unit diagonal in S_c.  None: the
+        translations I_B / sqrt|agg| of step 4."""
         self.opt = opt or AmgOptions()
         self.B = B
+        Z = near_null
         self.levels: list[Level] = []
         S = S.tocsr()
         S.sort_indices()
@@ -255,17 +315,24 @@ class AMG:
             D = diag_blocks(Sb, B)
             Dinv = np.linalg.inv(D)
             lam = power_lambda(S, Dinv, B, lvl, self.opt)
-            Pt = tentative(agg, nc, B)
+            if Z is None:
+                Pt, Bc, dead = tentative(agg, nc, B), B, None
+            else:
+                Pt, Z, dead = tentative_nullspace(agg, nc, B, Z)
+                Bc = Z.shape[1]
             omega = self.opt.omega_num / lam
             Dinv_sp = sp.block_diag(list(Dinv), format="csr")
             P = (Pt - omega * (Dinv_sp @ (S @ Pt))).tocsr()
             R = P.T.tocsr()
             Sc = (R @ S @ P).tocsr()
+            if dead is not None and dead.any():
+                Sc = (Sc + sp.diags(dead.astype(float))).tocsr()
             Sc.sort_indices()
             L.Dinv, L.lam, L.P, L.R, L.agg = Dinv, lam, P, R, agg
-            L.info = dict(n_coarse=nc, n_roots=int(is_root.sum()))
+            L.info = dict(n_coarse=nc, n_roots=int(is_root.sum()), dead=int(dead.sum()) if dead is not None else 0)
             L.nc = nc
             S = Sc
+            B = Bc
             lvl += 1
         last = self.levels[-1]
         if last.S.shape[0] > self.opt.dense_limit:

@@ -28,9 +28,9 @@ class _Exact:
         return self.lu.solve(f) if self.lu is not None else np.zeros_like(f)
 
 
-def _solver(M, B, kind, opt, aggregates=None):
+def _solver(M, B, kind, opt, aggregates=None, near_null=None):
     if kind == "amg":
-        return AMG(M, B, opt, aggregates=aggregates)
+        return AMG(M, B, opt, aggregates=aggregates, near_null=near_null)
     if kind == "exact":
         return _Exact(M)
     raise ValueError(kind)
@@ -44,13 +44,15 @@ class BlockPreconditioner:
     def __init__(self, P, variant: str, u_solver: str = "amg", p_solver: str = "amg",
                  opt: AmgOptions | None = None, blk: dict | None = None,
                  opt_p: AmgOptions | None = None, u_matrix=None, p_matrix=None,
-                 u_aggregates=None, p_aggregates=None):
+                 u_aggregates=None, p_aggregates=None, u_near_null=None):
         """``u_matrix`` / ``p_matrix`` replace the matrix the inner u / p
         solver is built on (S~ or S1, T or S~2); used to form the exact block
         factorisation of Eq. P1 / Eq. P2 on tiny cases.  ``u_aggregates`` /
         ``p_aggregates`` rebuild the AMG hierarchies on the aggregates of an
         earlier setup (``AMG.aggregates()``): the numeric refresh for new
-        values of the same patterns."""
+        values of the same patterns.  ``u_near_null``: candidate vectors for
+        the elasticity AMG (e.g. the six rigid modes of ``amg.rigid_modes``)
+        instead of the three translations."""
         self.P = P
         self.variant = variant
         b = blk or osp.blocks(P)
@@ -62,13 +64,15 @@ class BlockPreconditioner:
         if variant == "tpu":
             self.S1 = schur.s1(P, b)
             self.Su = schur.s_tilde(P, b, self.S1)                    # S~ (Alg. 1)
-            self.u_inv = _solver(self.Su if u_matrix is None else u_matrix, 3, u_solver, opt, u_aggregates)
+            self.u_inv = _solver(self.Su if u_matrix is None else u_matrix, 3, u_solver, opt, u_aggregates,
+                                 u_near_null)
             self.p_inv = _solver(b["T"] if p_matrix is None else p_matrix, 1, p_solver, opt_p, p_aggregates)
         elif variant in ("tup", "tup_star"):
             self.S1 = schur.s1(P, b)                                  # S1 (Alg. 3)
             self.Su = self.S1
             self.S2 = schur.s2_tilde(P, self.S1, b)                   # S~2 = T - FS (Alg. 3)
-            self.u_inv = _solver(self.S1 if u_matrix is None else u_matrix, 3, u_solver, opt, u_aggregates)
+            self.u_inv = _solver(self.S1 if u_matrix is None else u_matrix, 3, u_solver, opt, u_aggregates,
+                                 u_near_null)
             self.p_inv = _solver(self.S2 if p_matrix is None else p_matrix, 1, p_solver, opt_p, p_aggregates)
         else:
             raise ValueError(variant)
