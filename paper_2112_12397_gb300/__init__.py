@@ -29,7 +29,7 @@ SYMBOLS = ["fc_default_gen_config", "fc_generate", "fc_generate_error", "fc_inst
            "fc_apply_prec", "fc_solve", "fc_spmv_adjoint", "fc_apply_prec_adjoint", "fc_solve_adjoint",
            "fc_vcycle_adjoint", "fc_aperture_gradient",
            "fc_solve_host", "fc_num_levels", "fc_get_bsr", "fc_get_aggregates", "fc_vcycle",
-           "fc_get_fixed_stress", "fc_profile", "fc_kernel_stats", "fc_launch_count", "fc_destroy",
+           "fc_get_fixed_stress", "fc_krylov_basis", "fc_profile", "fc_kernel_stats", "fc_launch_count", "fc_destroy",
            "fc_strerror", "fc_last_error"]
 (FC_K_SMOOTH0, FC_K_JAC, FC_K_CGS, FC_K_VCYCLE, FC_K_PREC, FC_K_RESID0, FC_K_RESTRICT0, FC_K_PROLONG0,
  FC_K_COARSE0, FC_K_VCYCLE_P) = range(10)
@@ -143,6 +143,7 @@ def _open(path: str, build_if_missing: bool):
         "fc_get_aggregates": (C.c_int, [vp, C.c_int, C.c_int, vp, pd]),
         "fc_vcycle": (C.c_int, [vp, C.c_int, vp, vp]),
         "fc_get_fixed_stress": (C.c_int, [vp, vp]),
+        "fc_krylov_basis": (C.c_int, [vp, pint, vp]),
         "fc_profile": (C.c_int, [vp, C.c_int]),
         "fc_kernel_stats": (C.c_int, [vp, C.c_int, pi64, pd, pd]),
         "fc_launch_count": (C.c_ulonglong, []),
@@ -361,6 +362,16 @@ class Context:
 
     def vcycle(self, hier: int, f, x):
         self._check(self.lib.fc_vcycle(self.h, hier, _ptr(f), _ptr(x)), self.h)
+
+    def krylov_basis(self):
+        """The Arnoldi basis of the last FGMRES cycle as a (k, n) CUDA tensor."""
+        import torch
+        k = C.c_int(0)
+        self._check(self.lib.fc_krylov_basis(self.h, C.byref(k), None), self.h)
+        V = torch.empty((k.value, self.n), dtype=torch.float64, device="cuda")
+        if k.value:
+            self._check(self.lib.fc_krylov_basis(self.h, C.byref(k), _ptr(V)), self.h)
+        return V
 
     def profile(self, enable: bool = True):
         self._check(self.lib.fc_profile(self.h, 1 if enable else 0), self.h)

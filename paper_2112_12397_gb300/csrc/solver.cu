@@ -177,6 +177,131 @@ __global__ void __launch_bounds__(kCgsT)
   }
 }
 
+// ---------------------------------------------------------------- float pairs
+// The mixed mode's Gram-Schmidt keeps V and w in double but does the dot
+// products and the update sums on the FP32 pipes, in float-pair ("double-
+// float") arithmetic: a double d is carried as hi + lo with |d - hi - lo|
+// <= 2^-47 |d| (Dekker, "A floating-point technique for extending the
+// available precision", 1971: exact products by FMA, error-free sums).
+// GB300 issues FP64 at 1/64 of its FP32 rate, so one FP64 instruction per
+// basis entry is what bounds the double kernels; here the basis entries never
+// pass through the FP64 pipe, and double arithmetic is left for once per
+// vector entry (the final w update) or once per thread (the partial sums).
+
+// hi: the sign, exponent and leading 24 significand bits of d (truncated);
+// lo: the remaining 29 bits rounded to a float.  Built from the bit pattern
+// with integer operations, for 2^-74 <= |d| < 2^128; other values (zero,
+// tiny or huge) take the conversion path.
+__device__ __forceinline__ void ff_split_bits(double d, float &hi, float &lo) {
+  const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  if (e < 950 || e > 1150) {
+    hi = __double2float_rz(d);
+    lo = __double2float_rn(d - (double)hi);
+    return;
+  }
+  const unsigned sgn = hw & 0x80000000u;
+  hi = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);   // 2^(e - 1023 - 52)
+  const float r = __uint2float_rn(lw & 0x1FFFFFFFu) * scale;
+  lo = __uint_as_float(__float_as_uint(r) ^ sgn);
+}
+
+// (sh, sl) += (ah + al) (bh + bl), the al bl term dropped (2^-48 relative)
+__device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, float &sh, float &sl) {
+  const float p = ah * bh;
+  const float pe = fmaf(ah, bh, -p);                 // exact error of the product
+  const float c = fmaf(ah, bl, al * bh);             // cross terms
+  const float s = sh + p;                            // two-sum of sh and p
+  const float bp = s - sh;
+  const float err = (sh - (s - bp)) + (p - bp);
+  sl += err + (pe + c);
+  sh = s;
+}
+
+// partial[i * gridDim.x + block] = V_i . w (i < m), row m = w . w when
+// with_norm; same layout and reduction as k_cgs_dot, float-pair arithmetic
+constexpr int kCgsQF = 8;
+__global__ void __launch_bounds__(kCgsT)
+    k_cgs_dot_ff(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ w, double *partial,
+                 int with_norm) {
+  __shared__ double red[kCgsT / 32][kCgsQF];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int mm = m + (with_norm ? 1 : 0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int i0 = 0; i0 < mm; i0 += kCgsQF) {
+    const int nq = min(kCgsQF, mm - i0);
+    float sh[kCgsQF], sl[kCgsQF];
+#pragma unroll
+    for (int q = 0; q < kCgsQF; q++) sh[q] = sl[q] = 0.0f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + tid; e < n; e += stride) {
+      float wh, wl;
+      ff_split_bits(__ldg(w + e), wh, wl);
+#pragma unroll
+      for (int q = 0; q < kCgsQF; q++)
+        if (q < nq) {
+          const int i = i0 + q;
+          float vh = wh, vl = wl;
+          if (i < m) ff_split_bits(__ldg(V + (int64_t)i * n + e), vh, vl);
+          ff_fma(vh, vl, wh, wl, sh[q], sl[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kCgsQF; q++) {
+      const double r = warp_sum((double)sh[q] + (double)sl[q]);
+      if (lane == 0) red[wid][q] = r;
+    }
+    __syncthreads();
+    if (tid < nq) {
+      double sum = 0.0;
+#pragma unroll
+      for (int k = 0; k < kCgsT / 32; k++) sum += red[k][tid];
+      partial[(int64_t)(i0 + tid) * gridDim.x + blockIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// w -= V h with the sum V h in float pairs (h split once into shared
+// memory), the subtraction and ||w||^2 in double, once per entry
+__global__ void __launch_bounds__(kCgsT)
+    k_cgs_sub_ff(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ h, double *w,
+                 double *partial_norm) {
+  extern __shared__ float hsf[];   // 2 m floats: hi, lo
+  __shared__ double red[kCgsT / 32];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double hv = h[i];
+    const float hh = __double2float_rn(hv);
+    hsf[2 * i] = hh;
+    hsf[2 * i + 1] = __double2float_rn(hv - (double)hh);
+  }
+  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double nn = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + tid; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    float sh = 0.0f, sl = 0.0f;
+#pragma unroll 4
+    for (int i = 0; i < m; i++) {
+      float vh, vl;
+      ff_split_bits(__ldg(V + (int64_t)i * n + e), vh, vl);
+      ff_fma(vh, vl, hsf[2 * i], hsf[2 * i + 1], sh, sl);
+    }
+    const double we = w[e] - ((double)sh + (double)sl);
+    w[e] = we;
+    nn += we * we;
+  }
+  if (partial_norm) {
+    nn = warp_sum(nn);
+    if (lane == 0) red[wid] = nn;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int k = 0; k < kCgsT / 32; k++) sum += red[k];
+      partial_norm[blockIdx.x] = sum;
+    }
+  }
+}
+
 // Arnoldi column j: Hessenberg entries from hacc and ||w||^2, previous Givens
 // rotations, a new rotation, the residual recurrence.  stat[0] = |g_{j+1}|/beta,
 // stat[1] = h_{j+1,j}, stat[2] = w0 (norm before orthogonalisation),
@@ -252,6 +377,7 @@ struct fc_ctx {
   int kcap = 0;          // iterations the Krylov workspace holds ...
   int64_t kn = 0;        // ... for vectors of this length
   int kprec = -1;        // ... in this precision mode
+  int kbasis = 0;        // orthonormal vectors of V left by the last FGMRES cycle
   DBuf<double> V, Hm, cs, sn, g, y, hacc, htmp, partial, stat, w2, w02, red;
   DBuf<float> Zf;
   DBuf<double> Zd;
@@ -552,28 +678,36 @@ void ensure_krylov(fc_ctx &c, int maxit) {
 // Classical Gram-Schmidt applied twice against V_0..V_{m-1}:
 //   h = V^T w; w -= V h; h' = V^T w; w -= V h'; h += h'
 // with ||w||^2 before (w02) and after (w2) folded into the passes.
+// In FC_MIXED mode the passes run in float-pair arithmetic (k_cgs_*_ff).
 void cgs2(fc_ctx &c, int m, double *w) {
   NvtxRange nvtx("CGS2");
   const int64_t n = c.n;
   cudaStream_t s = c.s;
   const int nd = kCgsDotGrid, ns = kCgsSubGrid;
   const int fg = blocks_for((int64_t)(m + 1) * 32, 256, 1024);
-  const size_t hsh = sizeof(double) * m;
+  const bool ff = c.opt.precision == FC_MIXED;
+  const size_t hsh = ff ? sizeof(float) * 2 * m : sizeof(double) * m;
+  auto dot_pass = [&](int with_norm) {
+    if (ff) k_cgs_dot_ff<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, with_norm);
+    else k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, with_norm);
+    FS_LAUNCHED();
+  };
+  auto sub_pass = [&](double *pn) {
+    if (ff) k_cgs_sub_ff<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, pn);
+    else k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, pn);
+    FS_LAUNCHED();
+  };
   c.prof.start(PK_CGS, s);
-  k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, 1);
-  FS_LAUNCHED();
+  dot_pass(1);
   k_cgs_final<<<fg, 256, 0, s>>>(c.partial.p, m, m + 1, nd, c.htmp.p, c.hacc.p, 0, c.w02.p);
   FS_LAUNCHED();
-  k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, nullptr);
-  FS_LAUNCHED();
+  sub_pass(nullptr);
   c.prof.stop(PK_CGS, s, (2.0 * m + 3.0) * n * sizeof(double));
   c.prof.start(PK_CGS, s);
-  k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, 0);
-  FS_LAUNCHED();
+  dot_pass(0);
   k_cgs_final<<<fg, 256, 0, s>>>(c.partial.p, m, m, nd, c.htmp.p, c.hacc.p, 1, nullptr);
   FS_LAUNCHED();
-  k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, c.partial.p);
-  FS_LAUNCHED();
+  sub_pass(c.partial.p);
   k_cgs_final<<<1, 32, 0, s>>>(c.partial.p, 0, 1, ns, nullptr, nullptr, 0, c.w2.p);
   FS_LAUNCHED();
   c.prof.stop(PK_CGS, s, (2.0 * m + 3.0) * n * sizeof(double));
@@ -637,6 +771,7 @@ FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rt
     if (k == maxit) out.status = FC_NOT_CONVERGED;
   }
   out.iters = k;
+  c.kbasis = out.status == FC_BREAKDOWN ? k : k + 1;
   k_trisolve<<<1, 1, 0, s>>>(k, maxit + 1, c.Hm.p, c.g.p, c.y.p);
   FS_LAUNCHED();
   k_mcomb<TP><<<vgrid(n), 256, sizeof(double) * k, s>>>(Z, k, n, c.y.p, x);
@@ -1426,6 +1561,18 @@ int fc_kernel_stats(fc_ctx *c, int kernel, int64_t *launches, double *total_ms, 
 }
 
 unsigned long long fc_launch_count(void) { return fs::launch_count(); }
+
+int fc_krylov_basis(fc_ctx *c, int *nvec, double *d_V) {
+  if (!c || !nvec) return FC_BAD_ARG;
+  return run(c, [&]() {
+    *nvec = c->kbasis;
+    if (d_V && c->kbasis)
+      FS_CUDA(cudaMemcpyAsync(d_V, c->V.p, sizeof(double) * (size_t)c->kbasis * c->n, cudaMemcpyDeviceToDevice,
+                              c->s));
+    FS_CUDA(cudaStreamSynchronize(c->s));
+    return FC_OK;
+  });
+}
 
 int fc_residual_noalloc(fc_ctx *c, const double *b, const double *x, double *relres) {
   if (!c || !b || !x || !relres) return FC_BAD_ARG;

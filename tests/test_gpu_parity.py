@@ -278,6 +278,29 @@ def test_solve_host_equals_device(fs):
     assert it == ith and np.array_equal(hx, x.cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["rects16", "network16"])
+def test_arnoldi_basis_stays_orthonormal(fs, precision, name):
+    """CGS2 keeps V orthonormal to 1e-12 in both modes: in double, and in
+    the mixed mode's float-pair Gram-Schmidt (dot products and update sums
+    on the FP32 pipes, about 2^-47 relative)."""
+    P, ctx64, _, _ = case(name, fs)
+    preset, over, cm, cmp = CASES[name]
+    ctx = ctx64 if precision == "fp64" else fs.context_for(
+        P, fs.default_options(precision="mixed", coarse_max=cm, coarse_max_p=cmp))
+    b = cuda(P.b)
+    x = torch.zeros_like(b)
+    _, it, rr = ctx.solve("tup", b, x, 1e-8, 400)
+    V = ctx.krylov_basis()
+    assert V.shape[0] == it + 1
+    G = V @ V.T
+    err = float((G - torch.eye(V.shape[0], dtype=torch.float64, device="cuda")).abs().max())
+    print(f"{name} {precision}: {V.shape[0]} basis vectors, max |V^T V - I| = {err:.2e}")
+    assert err <= 1e-12
+    if ctx is not ctx64:
+        ctx.close()
+
+
 def test_setup_from_host_blocks_equals_device_blocks(fs):
     """fc_setup_host (blocks in host memory, numpy or pinned tensors) builds
     the same operators as fc_setup: bitwise equal applications and solves."""
@@ -383,6 +406,10 @@ def test_full_size_bench_configuration(fs):
     ctx = fs.context_for(P, fs.default_options(precision="mixed", variants=2))
     x = torch.zeros_like(b)
     rc, it, rr = ctx.solve("tup", b, x, 1e-8, 600)
+    V = ctx.krylov_basis()
+    orth = float((V @ V.T - torch.eye(V.shape[0], dtype=torch.float64, device="cuda")).abs().max())
+    del V
+    assert orth <= 1e-12, orth
     J = osp.jacobian(P)
     true = np.linalg.norm(P.b - J @ x.cpu().numpy()) / np.linalg.norm(P.b)
     assert true <= 1e-8 and abs(true - rr) <= 1e-3 * true
