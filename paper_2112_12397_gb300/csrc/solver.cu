@@ -178,15 +178,20 @@ __global__ void __launch_bounds__(kCgsT)
 }
 
 // ---------------------------------------------------------------- float pairs
-// The mixed mode's Gram-Schmidt keeps V and w in double but does the dot
-// products and the update sums on the FP32 pipes, in float-pair ("double-
-// float") arithmetic: a double d is carried as hi + lo with |d - hi - lo|
-// <= 2^-47 |d| (Dekker, "A floating-point technique for extending the
-// available precision", 1971: exact products by FMA, error-free sums).
-// GB300 issues FP64 at 1/64 of its FP32 rate, so one FP64 instruction per
-// basis entry is what bounds the double kernels; here the basis entries never
-// pass through the FP64 pipe, and double arithmetic is left for once per
-// vector entry (the final w update) or once per thread (the partial sums).
+// The mixed mode's Gram-Schmidt keeps V and w in double and takes the dot
+// products h = V^T w on the FP32 pipes, in float-pair ("double-float")
+// arithmetic: a double d is carried as hi + lo with |d - hi - lo| <= 2^-47 |d|
+// (Dekker, "A floating-point technique for extending the available
+// precision", 1971: exact products by FMA, error-free sums).  GB300 issues
+// FP64 at 1/64 of its FP32 rate, so one FP64 instruction per basis entry is
+// what bounds the double kernels; the dot kernel never passes a basis entry
+// through the FP64 pipe.  The update w -= V h stays in double: the Arnoldi
+// relation J z_j = V h + h_{j+1,j} v_{j+1} then holds to double rounding
+// whatever the error of h (an error in h only leaves a component along V,
+// which the second pass removes).  Summing V h in float pairs was measured:
+// its 2^-47 ||w|| error entered the Arnoldi relation and widened the gap
+// between the recurrence and the true residual (65 -> 76 iterations of the
+// incomplete t-u-p form on an 8^3 case).
 
 // hi: the sign, exponent and leading 24 significand bits of d (truncated);
 // lo: the remaining 29 bits rounded to a float.  Built from the bit pattern
@@ -259,46 +264,6 @@ __global__ void __launch_bounds__(kCgsT)
       partial[(int64_t)(i0 + tid) * gridDim.x + blockIdx.x] = sum;
     }
     __syncthreads();
-  }
-}
-
-// w -= V h with the sum V h in float pairs (h split once into shared
-// memory), the subtraction and ||w||^2 in double, once per entry
-__global__ void __launch_bounds__(kCgsT)
-    k_cgs_sub_ff(const double *__restrict__ V, int m, int64_t n, const double *__restrict__ h, double *w,
-                 double *partial_norm) {
-  extern __shared__ float hsf[];   // 2 m floats: hi, lo
-  __shared__ double red[kCgsT / 32];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double hv = h[i];
-    const float hh = __double2float_rn(hv);
-    hsf[2 * i] = hh;
-    hsf[2 * i + 1] = __double2float_rn(hv - (double)hh);
-  }
-  __syncthreads();
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  double nn = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + tid; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    float sh = 0.0f, sl = 0.0f;
-#pragma unroll 4
-    for (int i = 0; i < m; i++) {
-      float vh, vl;
-      ff_split_bits(__ldg(V + (int64_t)i * n + e), vh, vl);
-      ff_fma(vh, vl, hsf[2 * i], hsf[2 * i + 1], sh, sl);
-    }
-    const double we = w[e] - ((double)sh + (double)sl);
-    w[e] = we;
-    nn += we * we;
-  }
-  if (partial_norm) {
-    nn = warp_sum(nn);
-    if (lane == 0) red[wid] = nn;
-    __syncthreads();
-    if (tid == 0) {
-      double sum = 0.0;
-      for (int k = 0; k < kCgsT / 32; k++) sum += red[k];
-      partial_norm[blockIdx.x] = sum;
-    }
   }
 }
 
@@ -678,7 +643,7 @@ void ensure_krylov(fc_ctx &c, int maxit) {
 // Classical Gram-Schmidt applied twice against V_0..V_{m-1}:
 //   h = V^T w; w -= V h; h' = V^T w; w -= V h'; h += h'
 // with ||w||^2 before (w02) and after (w2) folded into the passes.
-// In FC_MIXED mode the passes run in float-pair arithmetic (k_cgs_*_ff).
+// In FC_MIXED mode the dot passes run in float-pair arithmetic (k_cgs_dot_ff).
 void cgs2(fc_ctx &c, int m, double *w) {
   NvtxRange nvtx("CGS2");
   const int64_t n = c.n;
@@ -686,15 +651,14 @@ void cgs2(fc_ctx &c, int m, double *w) {
   const int nd = kCgsDotGrid, ns = kCgsSubGrid;
   const int fg = blocks_for((int64_t)(m + 1) * 32, 256, 1024);
   const bool ff = c.opt.precision == FC_MIXED;
-  const size_t hsh = ff ? sizeof(float) * 2 * m : sizeof(double) * m;
+  const size_t hsh = sizeof(double) * m;
   auto dot_pass = [&](int with_norm) {
     if (ff) k_cgs_dot_ff<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, with_norm);
     else k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, with_norm);
     FS_LAUNCHED();
   };
   auto sub_pass = [&](double *pn) {
-    if (ff) k_cgs_sub_ff<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, pn);
-    else k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, pn);
+    k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, pn);
     FS_LAUNCHED();
   };
   c.prof.start(PK_CGS, s);
