@@ -195,21 +195,26 @@ __global__ void __launch_bounds__(kCgsT)
 
 // hi: the sign, exponent and leading 24 significand bits of d (truncated);
 // lo: the remaining 29 bits rounded to a float.  Built from the bit pattern
-// with integer operations, for 2^-74 <= |d| < 2^128; other values (zero,
-// tiny or huge) take the conversion path.
+// with integer operations and selects (no branch, no FP64 instruction):
+// exact to 2^-47 |d| for 2^-74 <= |d| < 2^128; below 2^-74 lo is dropped and
+// below 2^-126 (zero included) both parts are zero, an absolute error under
+// 2^-98 that no dot product of the normalised basis notices.  Larger values
+// (never met: basis vectors have unit norm and w = J z stays far below
+// 2^128) take the conversion path.
 __device__ __forceinline__ void ff_split_bits(double d, float &hi, float &lo) {
   const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
   const int e = (int)((hw >> 20) & 0x7FFu);
-  if (e < 950 || e > 1150) {
+  if (e > 1150) {
     hi = __double2float_rz(d);
     lo = __double2float_rn(d - (double)hi);
     return;
   }
   const unsigned sgn = hw & 0x80000000u;
-  hi = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
-  const float scale = __uint_as_float((unsigned)(e - 948) << 23);   // 2^(e - 1023 - 52)
+  const unsigned hb = sgn | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  hi = __uint_as_float(e >= 897 ? hb : sgn);
+  const float scale = __uint_as_float((unsigned)max(e - 948, 0) << 23);   // 2^(e - 1023 - 52)
   const float r = __uint2float_rn(lw & 0x1FFFFFFFu) * scale;
-  lo = __uint_as_float(__float_as_uint(r) ^ sgn);
+  lo = e >= 950 ? __uint_as_float(__float_as_uint(r) ^ sgn) : 0.0f;
 }
 
 // (sh, sl) += (ah + al) (bh + bl), the al bl term dropped (2^-48 relative)
