@@ -194,13 +194,15 @@ __global__ void __launch_bounds__(kCgsT)
 // incomplete t-u-p form on an 8^3 case).
 
 // hi: the sign, exponent and leading 24 significand bits of d (truncated);
-// lo: the remaining 29 bits rounded to a float.  Built from the bit pattern
-// with integer operations and selects (no branch, no FP64 instruction):
-// exact to 2^-47 |d| for 2^-74 <= |d| < 2^128; below 2^-74 lo is dropped and
-// below 2^-126 (zero included) both parts are zero, an absolute error under
-// 2^-98 that no dot product of the normalised basis notices.  Larger values
-// (never met: basis vectors have unit norm and w = J z stays far below
-// 2^128) take the conversion path.
+// lo: the remaining 29 bits truncated to a float's 24, normalised by a
+// count of leading zeros.  Built from the bit pattern with integer
+// operations and selects only (no branch; conversions are avoided because
+// this part issues them on its FP64 pipe, as ncu showed for an I2F-based
+// split): within 2^-47 |d| for 2^-74 <= |d| < 2^128; below 2^-74 lo is
+// dropped and below 2^-126 (zero included) both parts are zero, an absolute
+// error under 2^-98 that no dot product of the normalised basis notices.
+// Larger values (never met: basis vectors have unit norm and w = J z stays
+// far below 2^128) take the conversion path.
 __device__ __forceinline__ void ff_split_bits(double d, float &hi, float &lo) {
   const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
   const int e = (int)((hw >> 20) & 0x7FFu);
@@ -212,9 +214,13 @@ __device__ __forceinline__ void ff_split_bits(double d, float &hi, float &lo) {
   const unsigned sgn = hw & 0x80000000u;
   const unsigned hb = sgn | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
   hi = __uint_as_float(e >= 897 ? hb : sgn);
-  const float scale = __uint_as_float((unsigned)max(e - 948, 0) << 23);   // 2^(e - 1023 - 52)
-  const float r = __uint2float_rn(lw & 0x1FFFFFFFu) * scale;
-  lo = e >= 950 ? __uint_as_float(__float_as_uint(r) ^ sgn) : 0.0f;
+  // the low 29 bits weigh 2^(e - 1075); leading one at bit p gives the
+  // exponent field p + e - 948 and 23 fraction bits below it
+  const unsigned r = lw & 0x1FFFFFFFu;
+  const int p = 31 - __clz(r);
+  const unsigned frac = (p >= 23 ? (r >> (p - 23)) : (r << (23 - p))) & 0x7FFFFFu;
+  const unsigned lb = sgn | ((unsigned)(p + e - 948) << 23) | frac;
+  lo = (e >= 950 && r != 0u) ? __uint_as_float(lb) : 0.0f;
 }
 
 // (sh, sl) += (ah + al) (bh + bl), the al bl term dropped (2^-48 relative)
