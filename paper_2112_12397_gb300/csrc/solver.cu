@@ -201,26 +201,24 @@ __global__ void __launch_bounds__(kCgsT)
 // split): within 2^-47 |d| for 2^-74 <= |d| < 2^128; below 2^-74 lo is
 // dropped and below 2^-126 (zero included) both parts are zero, an absolute
 // error under 2^-98 that no dot product of the normalised basis notices.
-// Larger values (never met: basis vectors have unit norm and w = J z stays
-// far below 2^128) take the conversion path.
+// From 2^128 up (never met: basis vectors have unit norm and w = J z stays
+// far below) hi is an infinity of d's sign, which the solver reports as a
+// non-finite Hessenberg entry.  (A conversion fallback for that case was
+// if-converted by the compiler into FP64 instructions issued for every
+// entry.)
 __device__ __forceinline__ void ff_split_bits(double d, float &hi, float &lo) {
   const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
   const int e = (int)((hw >> 20) & 0x7FFu);
-  if (e > 1150) {
-    hi = __double2float_rz(d);
-    lo = __double2float_rn(d - (double)hi);
-    return;
-  }
   const unsigned sgn = hw & 0x80000000u;
   const unsigned hb = sgn | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-  hi = __uint_as_float(e >= 897 ? hb : sgn);
+  hi = __uint_as_float(e > 1150 ? (sgn | 0x7F800000u) : e >= 897 ? hb : sgn);
   // the low 29 bits weigh 2^(e - 1075); leading one at bit p gives the
   // exponent field p + e - 948 and 23 fraction bits below it
   const unsigned r = lw & 0x1FFFFFFFu;
   const int p = 31 - __clz(r);
   const unsigned frac = (p >= 23 ? (r >> (p - 23)) : (r << (23 - p))) & 0x7FFFFFu;
   const unsigned lb = sgn | ((unsigned)(p + e - 948) << 23) | frac;
-  lo = (e >= 950 && r != 0u) ? __uint_as_float(lb) : 0.0f;
+  lo = (e >= 950 && e <= 1150 && r != 0u) ? __uint_as_float(lb) : 0.0f;
 }
 
 // (sh, sl) += (ah + al) (bh + bl), the al bl term dropped (2^-48 relative)
