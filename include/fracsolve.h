@@ -60,11 +60,9 @@ enum { FC_TPU = 0, FC_TUP = 1, FC_TUP_STAR = 2 };
 
 /* Precision modes. FP64: everything in double.  MIXED: the AMG hierarchies,
  * smoothers, H~^-1 and the coupling blocks used inside the preconditioner are
- * stored and applied in float; the outer Krylov method (J z, Givens, solution
- * update, true residual) and the coarsest dense solve stay in double, and the
- * Arnoldi basis and its updates stay in double, with the Gram-Schmidt dot
- * products taken in float-pair arithmetic (about 2^-47 relative, on the FP32
- * pipes). */
+ * stored and applied in float; the outer Krylov method (J z, Arnoldi,
+ * Givens, solution update, true residual) and the coarsest dense solve stay
+ * in double. */
 enum { FC_FP64 = 0, FC_MIXED = 1 };
 
 /* Block sparse row matrix (row-major dense blocks of br x bc), DEVICE
@@ -361,9 +359,7 @@ int fc_vcycle_adjoint(fc_ctx *ctx, int hier, const double *d_f, double *d_x);
 /* The orthonormal Arnoldi basis V_0 .. V_{nvec-1} left by the last FGMRES
  * cycle of fc_solve / fc_solve_adjoint (Sec. 4), row-major nvec x n doubles,
  * copied to d_V (DEVICE, caller-owned) unless d_V is NULL; *nvec receives
- * the count (0 before any solve).  In FC_MIXED mode the Gram-Schmidt dot
- * products that built it run in float-pair arithmetic (about 2^-47
- * relative). */
+ * the count (0 before any solve). */
 int fc_krylov_basis(fc_ctx *ctx, int *nvec, double *d_V);
 
 /* The fixed-stress diagonal [S_K]_k of Eq. FS_algebraic to HOST (n_face). */

@@ -177,126 +177,6 @@ __global__ void __launch_bounds__(kCgsT)
   }
 }
 
-// ---------------------------------------------------------------- float pairs
-// The mixed mode's Gram-Schmidt keeps V and w in double and takes the dot
-// products h = V^T w on the FP32 pipes, in float-pair ("double-float")
-// arithmetic: a double d is carried as hi + lo with |d - hi - lo| <= 2^-47 |d|
-// (Dekker, "A floating-point technique for extending the available
-// precision", 1971: exact products by FMA, error-free sums).  GB300 issues
-// FP64 at 1/64 of its FP32 rate, so one FP64 instruction per basis entry is
-// what bounds the double kernels; the dot kernel never passes a basis entry
-// through the FP64 pipe.  Each basis vector is split once, when it is formed,
-// into a float-pair copy (same 8 bytes per entry) that the dot kernel reads;
-// splitting it inside the dot kernel cost about 20 integer operations per
-// entry and vector, which made that kernel slower than the double one.  The update w -= V h stays in double: the Arnoldi
-// relation J z_j = V h + h_{j+1,j} v_{j+1} then holds to double rounding
-// whatever the error of h (an error in h only leaves a component along V,
-// which the second pass removes).  Summing V h in float pairs was measured:
-// its 2^-47 ||w|| error entered the Arnoldi relation and widened the gap
-// between the recurrence and the true residual (65 -> 76 iterations of the
-// incomplete t-u-p form on an 8^3 case).
-
-// hi: the sign, exponent and leading 24 significand bits of d (truncated);
-// lo: the remaining 29 bits rounded to a float's 24.  Built from the bit
-// pattern with integer and FP32 operations and selects only (no branch;
-// integer-to-float conversions and leading-zero counts are avoided: this part
-// issues them on its FP64 pipe, as ncu showed for split variants that used
-// them): within 2^-47 |d| for 2^-74 <= |d| < 2^128; below 2^-74 lo is
-// dropped and below 2^-126 (zero included) both parts are zero, an absolute
-// error under 2^-98 that no dot product of the normalised basis notices.
-// From 2^128 up (never met: basis vectors have unit norm and w = J z stays
-// far below) hi is an infinity of d's sign, which the solver reports as a
-// non-finite Hessenberg entry.  (A conversion fallback for that case was
-// if-converted by the compiler into FP64 instructions issued for every
-// entry.)
-__device__ __forceinline__ void ff_split_bits(unsigned long long bits, float &hi, float &lo) {
-  const unsigned hw = (unsigned)(bits >> 32), lw = (unsigned)bits;
-  const int e = (int)((hw >> 20) & 0x7FFu);
-  const unsigned sgn = hw & 0x80000000u;
-  const unsigned hb = sgn | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-  hi = __uint_as_float(e > 1150 ? (sgn | 0x7F800000u) : e >= 897 ? hb : sgn);
-  // the low 29 bits r weigh 2^(e - 1075): r = r1 2^23 + r0, each part
-  // turned into a float exactly by the 2^23 bias trick, recombined by one
-  // rounded FMA and scaled by a power of two built from the exponent
-  const unsigned r = lw & 0x1FFFFFFFu;
-  const float f0 = __uint_as_float(0x4B000000u | (r & 0x7FFFFFu)) - 8388608.0f;
-  const float f1 = __uint_as_float(0x4B000000u | (r >> 23)) - 8388608.0f;
-  const float scale = __uint_as_float((unsigned)max(e - 948, 1) << 23);   // 2^(e - 1075)
-  const float mag = fmaf(f1, 8388608.0f, f0) * scale;
-  lo = (e >= 950 && e <= 1150) ? __uint_as_float(__float_as_uint(mag) ^ sgn) : 0.0f;
-}
-
-// (sh, sl) += (ah + al) (bh + bl), the al bl term dropped (2^-48 relative)
-__device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, float &sh, float &sl) {
-  const float p = ah * bh;
-  const float pe = fmaf(ah, bh, -p);                 // exact error of the product
-  const float c = fmaf(ah, bl, al * bh);             // cross terms
-  const float s = sh + p;                            // two-sum of sh and p
-  const float bp = s - sh;
-  const float err = (sh - (s - bp)) + (p - bp);
-  sl += err + (pe + c);
-  sh = s;
-}
-
-// partial[i * gridDim.x + block] = V_i . w (i < m), row m = w . w when
-// with_norm; same layout and reduction as k_cgs_dot, float-pair arithmetic.
-// V is the float-pair copy written when each basis vector was formed; w
-// arrives as the bit patterns of its doubles and is split here.
-constexpr int kCgsQF = 8;
-__global__ void __launch_bounds__(kCgsT)
-    k_cgs_dot_ff(const float2 *__restrict__ V, int m, int64_t n,
-                 const unsigned long long *__restrict__ w, double *partial, int with_norm) {
-  __shared__ double red[kCgsT / 32][kCgsQF];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int mm = m + (with_norm ? 1 : 0);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int i0 = 0; i0 < mm; i0 += kCgsQF) {
-    const int nq = min(kCgsQF, mm - i0);
-    float sh[kCgsQF], sl[kCgsQF];
-#pragma unroll
-    for (int q = 0; q < kCgsQF; q++) sh[q] = sl[q] = 0.0f;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + tid; e < n; e += stride) {
-      float wh, wl;
-      ff_split_bits(__ldg(w + e), wh, wl);
-#pragma unroll
-      for (int q = 0; q < kCgsQF; q++)
-        if (q < nq) {
-          const int i = i0 + q;
-          float vh = wh, vl = wl;
-          if (i < m) {
-            const float2 v = __ldg(V + (int64_t)i * n + e);
-            vh = v.x;
-            vl = v.y;
-          }
-          ff_fma(vh, vl, wh, wl, sh[q], sl[q]);
-        }
-    }
-    // warp reduction in float pairs (error-free sums of the high parts);
-    // the one conversion to double per warp keeps the FP64 pipe out of the
-    // per-thread epilogue, which dominated when each thread holds few entries
-#pragma unroll
-    for (int q = 0; q < kCgsQF; q++) {
-      float h = sh[q], l = sl[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
-        const float t = h + oh, bp = t - h;
-        l += ol + ((h - (t - bp)) + (oh - bp));
-        h = t;
-      }
-      if (lane == 0) red[wid][q] = (double)h + (double)l;
-    }
-    __syncthreads();
-    if (tid < nq) {
-      double sum = 0.0;
-#pragma unroll
-      for (int k = 0; k < kCgsT / 32; k++) sum += red[k][tid];
-      partial[(int64_t)(i0 + tid) * gridDim.x + blockIdx.x] = sum;
-    }
-    __syncthreads();
-  }
-}
-
 // Arnoldi column j: Hessenberg entries from hacc and ||w||^2, previous Givens
 // rotations, a new rotation, the residual recurrence.  stat[0] = |g_{j+1}|/beta,
 // stat[1] = h_{j+1,j}, stat[2] = w0 (norm before orthogonalisation),
@@ -327,21 +207,11 @@ __global__ void k_givens(int j, int ld, const double *hacc, const double *w2, co
   stat[3] = (hn > 1e-14 * w0 && hn > 0.0) ? 1.0 / hn : 0.0;
 }
 
-// v *= *sc (sc: device scalar or NULL for none) and, when vf is given, the
-// float-pair copy vf[e] = (hi, lo) of the new v (the mixed mode's basis
-// copy for the Gram-Schmidt dot products)
-__global__ void k_scale_split(double *v, int64_t n, const double *sc, float2 *vf) {
-  const double a = sc ? *sc : 1.0;
+__global__ void k_scale_by(double *v, int64_t n, const double *sc) {
+  const double a = *sc;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const double x = v[e] * a;
-    v[e] = x;
-    if (vf) {
-      float h, l;
-      ff_split_bits((unsigned long long)__double_as_longlong(x), h, l);
-      vf[e] = make_float2(h, l);
-    }
-  }
+       e += (int64_t)gridDim.x * blockDim.x)
+    v[e] *= a;
 }
 
 __global__ void k_trisolve(int k, int ld, const double *Hm, const double *g, double *y) {
@@ -385,7 +255,6 @@ struct fc_ctx {
   int kbasis = 0;        // orthonormal vectors of V left by the last FGMRES cycle
   DBuf<double> V, Hm, cs, sn, g, y, hacc, htmp, partial, stat, w2, w02, red;
   DBuf<float> Zf;
-  DBuf<float2> Vff;     // FC_MIXED: float-pair copy of V for the Gram-Schmidt dot products
   DBuf<double> Zd;
   DBuf<double> xk, rk, bk, hb, hx;
   DBuf<double> zd;   // a float direction widened to double for J z / J^T z
@@ -670,13 +539,8 @@ void ensure_krylov(fc_ctx &c, int maxit) {
   c.kcap = 0;
   const int64_t n = c.n;
   c.V.alloc((size_t)(maxit + 1) * n);
-  if (c.opt.precision == FC_MIXED) {
-    c.Zf.alloc((size_t)maxit * n);
-    c.Vff.alloc((size_t)(maxit + 1) * n);
-  } else {
-    c.Zd.alloc((size_t)maxit * n);
-    c.Vff.release();
-  }
+  if (c.opt.precision == FC_MIXED) c.Zf.alloc((size_t)maxit * n);
+  else c.Zd.alloc((size_t)maxit * n);
   c.Hm.alloc((size_t)(maxit + 1) * maxit);
   c.cs.alloc(maxit); c.sn.alloc(maxit); c.g.alloc(maxit + 1); c.y.alloc(maxit);
   c.hacc.alloc(maxit + 1); c.htmp.alloc(maxit + 1);
@@ -689,37 +553,28 @@ void ensure_krylov(fc_ctx &c, int maxit) {
 // Classical Gram-Schmidt applied twice against V_0..V_{m-1}:
 //   h = V^T w; w -= V h; h' = V^T w; w -= V h'; h += h'
 // with ||w||^2 before (w02) and after (w2) folded into the passes.
-// In FC_MIXED mode the dot passes run in float-pair arithmetic (k_cgs_dot_ff).
 void cgs2(fc_ctx &c, int m, double *w) {
   NvtxRange nvtx("CGS2");
   const int64_t n = c.n;
   cudaStream_t s = c.s;
   const int nd = kCgsDotGrid, ns = kCgsSubGrid;
   const int fg = blocks_for((int64_t)(m + 1) * 32, 256, 1024);
-  const bool ff = c.opt.precision == FC_MIXED;
   const size_t hsh = sizeof(double) * m;
-  auto dot_pass = [&](int with_norm) {
-    if (ff)
-      k_cgs_dot_ff<<<nd, kCgsT, 0, s>>>(c.Vff.p, m, n, reinterpret_cast<const unsigned long long *>(w),
-                                        c.partial.p, with_norm);
-    else k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, with_norm);
-    FS_LAUNCHED();
-  };
-  auto sub_pass = [&](double *pn) {
-    k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, pn);
-    FS_LAUNCHED();
-  };
   c.prof.start(PK_CGS, s);
-  dot_pass(1);
+  k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, 1);
+  FS_LAUNCHED();
   k_cgs_final<<<fg, 256, 0, s>>>(c.partial.p, m, m + 1, nd, c.htmp.p, c.hacc.p, 0, c.w02.p);
   FS_LAUNCHED();
-  sub_pass(nullptr);
+  k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, nullptr);
+  FS_LAUNCHED();
   c.prof.stop(PK_CGS, s, (2.0 * m + 3.0) * n * sizeof(double));
   c.prof.start(PK_CGS, s);
-  dot_pass(0);
+  k_cgs_dot<<<nd, kCgsT, 0, s>>>(c.V.p, m, n, w, c.partial.p, 0);
+  FS_LAUNCHED();
   k_cgs_final<<<fg, 256, 0, s>>>(c.partial.p, m, m, nd, c.htmp.p, c.hacc.p, 1, nullptr);
   FS_LAUNCHED();
-  sub_pass(c.partial.p);
+  k_cgs_sub<<<ns, kCgsT, hsh, s>>>(c.V.p, m, n, c.htmp.p, w, c.partial.p);
+  FS_LAUNCHED();
   k_cgs_final<<<1, 32, 0, s>>>(c.partial.p, 0, 1, ns, nullptr, nullptr, 0, c.w2.p);
   FS_LAUNCHED();
   c.prof.stop(PK_CGS, s, (2.0 * m + 3.0) * n * sizeof(double));
@@ -745,11 +600,6 @@ FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rt
     return out;
   }
   scale_to(c.V.p, rhs, 1.0 / beta, n, s);
-  float2 *vff = c.opt.precision == FC_MIXED ? c.Vff.p : nullptr;
-  if (vff) {
-    k_scale_split<<<vgrid(n), 256, 0, s>>>(c.V.p, n, nullptr, vff);
-    FS_LAUNCHED();
-  }
   k_set_scalar<<<1, 1, 0, s>>>(c.g.p, beta);
   FS_LAUNCHED();
   TP *Z = zbase<TP>(c);
@@ -774,7 +624,7 @@ FgmresOut fgmres(fc_ctx &c, int variant, const double *rhs, double *x, double rt
     cgs2(c, j + 1, w);
     k_givens<<<1, 1, 0, s>>>(j, maxit + 1, c.hacc.p, c.w2.p, c.w02.p, beta, c.Hm.p, c.cs.p, c.sn.p, c.g.p, c.stat.p);
     FS_LAUNCHED();
-    k_scale_split<<<vgrid(n), 256, 0, s>>>(w, n, c.stat.p + 3, vff ? vff + (int64_t)(j + 1) * n : nullptr);
+    k_scale_by<<<vgrid(n), 256, 0, s>>>(w, n, c.stat.p + 3);
     FS_LAUNCHED();
     FS_CUDA(cudaMemcpyAsync(c.stat_host, c.stat.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     FS_CUDA(cudaStreamSynchronize(s));

@@ -281,9 +281,8 @@ def test_solve_host_equals_device(fs):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["rects16", "network16"])
 def test_arnoldi_basis_stays_orthonormal(fs, precision, name):
-    """CGS2 keeps V orthonormal to 1e-12 in both modes: in double, and with
-    the mixed mode's float-pair dot products (on the FP32 pipes, about 2^-47
-    relative; the updates stay in double)."""
+    """CGS2 keeps the Arnoldi basis orthonormal to 1e-12 in both modes (the
+    Arnoldi process runs in double in both)."""
     P, ctx64, _, _ = case(name, fs)
     preset, over, cm, cmp = CASES[name]
     ctx = ctx64 if precision == "fp64" else fs.context_for(
