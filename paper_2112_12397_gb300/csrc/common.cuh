@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -43,22 +44,45 @@ void add_launches(long long delta);   // kernels replayed by a graph (+) or capt
   } while (0)
 
 // ---------------------------------------------------------------- buffers
+// Device blocks released by a context are kept for its next allocations of
+// the same size instead of going back to the driver: a repeated fc_setup
+// (a Newton sequence, or the bench) then allocates and frees nothing, where
+// cudaFree would synchronise the device and cudaMalloc pay a driver call for
+// each of the hierarchy's buffers.  Every kernel of a context runs on its one
+// stream, so a block reused by the same context is stream-ordered after its
+// previous use.  The cache belongs to the context (the first member, freed
+// last) and is the one a DBuf sees while that context's entry point runs
+// (g_cache); allocations made outside a context call go to the driver.
+struct BlockCache {
+  std::multimap<size_t, void *> blocks;
+  size_t bytes = 0;
+  void *take(size_t sz);
+  void put(void *p, size_t sz);
+  void flush();   // returns every kept block to the driver
+  ~BlockCache() { flush(); }
+};
+extern thread_local BlockCache *g_cache;
+void *device_alloc(size_t sz, BlockCache *cache);   // throws Error(FC_OOM) when the device is full
+
+struct CacheScope {   // g_cache for the duration of one entry point
+  BlockCache *prev;
+  explicit CacheScope(BlockCache *c) : prev(g_cache) { g_cache = c; }
+  ~CacheScope() { g_cache = prev; }
+};
+
 template <typename T>
 struct DBuf {
   T *p = nullptr;
   size_t n = 0;
+  BlockCache *cache = nullptr;   // where p goes back on release (nullptr: the driver)
   DBuf() = default;
   explicit DBuf(size_t n_) { alloc(n_); }
+  static size_t rounded(size_t n_) { return (n_ * sizeof(T) + 255) & ~size_t(255); }
   void alloc(size_t n_) {
     release();
     if (n_ == 0) return;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), n_ * sizeof(T));
-    if (e == cudaErrorMemoryAllocation) {
-      (void)cudaGetLastError();
-      p = nullptr;
-      throw Error(FC_OOM, "cudaMalloc of " + std::to_string(n_ * sizeof(T)) + " bytes failed");
-    }
-    FS_CUDA(e);
+    cache = g_cache;
+    p = static_cast<T *>(device_alloc(rounded(n_), cache));
     n = n_;
   }
   // grow-only reallocation (contents are not kept)
@@ -66,16 +90,21 @@ struct DBuf {
     if (n_ > n) alloc(n_);
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (cache) cache->put(p, rounded(n));
+      else cudaFree(p);
+    }
     p = nullptr;
     n = 0;
+    cache = nullptr;
   }
   ~DBuf() { release(); }
-  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf(DBuf &&o) noexcept : p(o.p), n(o.n), cache(o.cache) { o.p = nullptr; o.n = 0; o.cache = nullptr; }
   DBuf &operator=(DBuf &&o) noexcept {
     if (this != &o) {
       release();
-      p = o.p; n = o.n; o.p = nullptr; o.n = 0;
+      p = o.p; n = o.n; cache = o.cache;
+      o.p = nullptr; o.n = 0; o.cache = nullptr;
     }
     return *this;
   }

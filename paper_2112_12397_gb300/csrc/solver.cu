@@ -231,6 +231,7 @@ inline int vgrid(int64_t n) { return blocks_for(n, 256, kSMs * 16); }
 
 // ============================================================ context
 struct fc_ctx {
+  BlockCache cache;   // first member: destroyed after every buffer that returns to it
   fc_options opt;
   cudaStream_t s = nullptr;
   int device = 0;
@@ -824,6 +825,7 @@ __global__ void k_noalloc_final(double *part) {
 // ============================================================ error plumbing
 namespace {
 int run(fc_ctx *c, const std::function<int()> &fn) {
+  CacheScope scope(c ? &c->cache : nullptr);
   try {
     if (c) {
       c->err.clear();

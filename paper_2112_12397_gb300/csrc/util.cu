@@ -14,6 +14,46 @@ void add_launches(long long delta) {
   g_launches.fetch_add((unsigned long long)delta, std::memory_order_relaxed);
 }
 
+thread_local BlockCache *g_cache = nullptr;
+
+void *BlockCache::take(size_t sz) {
+  auto it = blocks.find(sz);
+  if (it == blocks.end()) return nullptr;
+  void *p = it->second;
+  blocks.erase(it);
+  bytes -= sz;
+  return p;
+}
+
+void BlockCache::put(void *p, size_t sz) {
+  blocks.emplace(sz, p);
+  bytes += sz;
+}
+
+void BlockCache::flush() {
+  for (auto &b : blocks) cudaFree(b.second);
+  blocks.clear();
+  bytes = 0;
+}
+
+void *device_alloc(size_t sz, BlockCache *cache) {
+  if (cache)
+    if (void *p = cache->take(sz)) return p;
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sz);
+  if (e == cudaErrorMemoryAllocation && cache && cache->bytes) {
+    (void)cudaGetLastError();   // kept blocks of other sizes go back first
+    cache->flush();
+    e = cudaMalloc(&p, sz);
+  }
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    throw Error(FC_OOM, "cudaMalloc of " + std::to_string(sz) + " bytes failed");
+  }
+  FS_CUDA(e);
+  return p;
+}
+
 cudaEvent_t Profiler::get() {
   if (used == pool.size()) {
     cudaEvent_t e;
