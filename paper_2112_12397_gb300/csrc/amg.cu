@@ -12,7 +12,8 @@
 //      neighbour, leftovers seed singletons; numbered by seed index
 //   5. lambda from 15 normalised power steps of D^-1 S
 //   6. P = (I - omega D^-1 S) P_tent with P_tent(i, agg i) = I / sqrt(|agg|)
-//   7. R = P^T, S_c = R (S P) by the block SpGEMM
+//   7. R = P^T, S_c = R (S P) by the block SpGEMM (in float in the mixed
+//      mode, whose cycle keeps the level operators in float)
 // The coarsest operator is inverted explicitly (Gauss-Jordan, partial
 // pivoting) in double.
 //
@@ -1013,6 +1014,40 @@ void level_lambda(LevelSetup &L, const AmgParams &p, int l, int precision, cudaS
   }
 }
 
+// The Galerkin product S_c = R (S P).  In the mixed mode, whose cycle
+// stores and applies every level operator in float, the block products and
+// their sums run in float: the double SpGEMM is bound by this part's FP64
+// FMA rate (1/64 of FP32).  The float result is widened to double for the
+// next level's setup (strength, aggregation, prolongator).  The FP64 mode
+// keeps the double products.  numeric_only: the patterns of S P and S_c are
+// those of an earlier call (a numeric rebuild).
+void galerkin(LevelSetup &L, Bsr<double> &Sc, int precision, bool numeric_only, cudaStream_t s) {
+  if (precision != FC_MIXED) {
+    if (numeric_only) {
+      spgemm_numeric(L.S.view(), L.P.view(), L.SP, s);
+      spgemm_numeric(L.R.view(), L.SP.view(), Sc, s);
+    } else {
+      L.SP = spgemm(L.S.view(), L.P.view(), s);
+      Sc = spgemm(L.R.view(), L.SP.view(), s);
+    }
+    return;
+  }
+  const Bsr<float> Sf = copy_cast<float, double>(L.S.view(), s);
+  const Bsr<float> Pf = copy_cast<float, double>(L.P.view(), s);
+  const Bsr<float> Rf = copy_cast<float, double>(L.R.view(), s);
+  if (numeric_only) {
+    spgemm_numeric(Sf.view(), Pf.view(), L.SPf, s);
+    Bsr<float> Scf = copy_cast<float, double>(Sc.view(), s);   // the pattern of S_c
+    spgemm_numeric(Rf.view(), L.SPf.view(), Scf, s);
+    cast(Sc.val.p, Scf.val.p, Sc.nnzb * Sc.br * Sc.bc, s);
+  } else {
+    L.SPf = spgemm(Sf.view(), Pf.view(), s);
+    const Bsr<float> Scf = spgemm(Rf.view(), L.SPf.view(), s);
+    Sc = copy_cast<double, float>(Scf.view(), s);
+  }
+  FS_CUDA(cudaStreamSynchronize(s));   // the float temporaries go out of scope here
+}
+
 template <int B>
 void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s) {
   const AmgParams &p = H.prm;
@@ -1049,10 +1084,9 @@ void setup_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s)
     pt.mark("prolongator");
     L.R = transpose(L.P.view(), s);
     pt.mark("transpose");
-    L.SP = spgemm(L.S.view(), L.P.view(), s);
-    pt.mark("spgemm S P");
-    Bsr<double> Sc = spgemm(L.R.view(), L.SP.view(), s);
-    pt.mark("spgemm R (S P)");
+    Bsr<double> Sc;
+    galerkin(L, Sc, precision, false, s);
+    pt.mark("Galerkin R (S P)");
     LevelSetup next;
     next.B = B;
     next.S = std::move(Sc);
@@ -1090,8 +1124,7 @@ void refresh_levels(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t 
     prolongator_values<B>(L, p.omega_num / L.lam, s);
     L.R = transpose(L.P.view(), s);
     pt.mark("prolongator + transpose");
-    spgemm_numeric(L.S.view(), L.P.view(), L.SP, s);
-    spgemm_numeric(L.R.view(), L.SP.view(), H.lev[l + 1].S, s);
+    galerkin(L, H.lev[l + 1].S, precision, true, s);
     pt.mark("spgemm numeric");
   }
   invert_coarsest(H, s);

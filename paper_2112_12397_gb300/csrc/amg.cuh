@@ -31,7 +31,8 @@ struct LevelSetup {
   DBuf<int> agg;        // aggregate of each block row (-1: none)
   DBuf<int> asize;      // size of each aggregate
   int nc = 0;           // number of aggregates (coarse block rows)
-  Bsr<double> SP;       // S P, kept for numeric rebuilds
+  Bsr<double> SP;       // S P, kept for numeric rebuilds (FP64 mode)
+  Bsr<float> SPf;       // S P in float (mixed mode: the Galerkin products run in float)
   double lam = 0.0;     // power estimate of the largest eigenvalue of D^-1 S
   // sliced-ELL operator and D^-1 in the cycle precision, built during setup
   // (the power iteration runs on them) and handed to the cycle

@@ -177,7 +177,8 @@ __device__ inline bool hash_insert(WarpHash &h, int key) {
 
 // Prefix of the B-row lengths over the row of A (a0, na): pre[x] = products
 // of entries 0..x-1, pre[na] = T (returned to every lane).
-__device__ inline int row_product_prefix(const BsrView<double> &A, const BsrView<double> &B, int a0, int na,
+template <typename TV>
+__device__ inline int row_product_prefix(const BsrView<TV> &A, const BsrView<TV> &B, int a0, int na,
                                          int *pre, int lane) {
   int run = 0;
   for (int x0 = 0; x0 < na; x0 += 32) {
@@ -308,16 +309,17 @@ struct SpgemmTask {
   int64_t soff;
 };
 
-template <int BR, int BK, int BC, bool GS>
+template <typename T, int BR, int BK, int BC, bool GS>
 __global__ void __launch_bounds__(256)
-    k_spgemm_numeric_mp(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC, double *valC,
-                        const int *rows, const int *nrows, const SpgemmTask *tasks, double *scratch, int capA,
+    k_spgemm_numeric_mp(BsrView<T> A, BsrView<T> B, const int *rpC, const int *ciC, T *valC,
+                        const int *rows, const int *nrows, const SpgemmTask *tasks, T *scratch, int capA,
                         int capC, int capT, int *bad) {
   constexpr int BS = BR * BC, AS = BR * BK, BB = BK * BC, kPL = kSegT / 32;
-  extern __shared__ double dsm[];
+  extern __shared__ double dsm_raw[];
+  T *dsm = reinterpret_cast<T *>(dsm_raw);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  const int dw = (GS ? 0 : capC) + 32;                   // doubles per warp, in blocks
-  double *carry = dsm + (size_t)wid * dw * BS;            // 32 continuation sums
+  const int dw = (GS ? 0 : capC) + 32;                   // values per warp, in blocks
+  T *carry = dsm + (size_t)wid * dw * BS;                 // 32 continuation sums
   int *cols = reinterpret_cast<int *>(dsm + (size_t)wpb * dw * BS) +
               (size_t)wid * (3 * capC + 2 * capA + 2 + 4 * capT);
   int *pre = cols + capC;          // capA + 1
@@ -337,16 +339,16 @@ __global__ void __launch_bounds__(256)
     const int a0 = A.rp[i], na = A.rp[i + 1] - a0;
     // the slot sums: in shared memory, or (long rows) the row of C itself or
     // this task's share of the scratch
-    double *sums = !GS ? carry + 32 * BS : tk.soff >= 0 ? scratch + tk.soff : valC + (int64_t)cs * BS;
+    T *sums = !GS ? carry + 32 * BS : tk.soff >= 0 ? scratch + tk.soff : valC + (int64_t)cs * BS;
     row_product_prefix(A, B, a0, na, pre, lane);
     for (int x = lane; x < na; x += 32) kb[x] = B.rp[A.ci[a0 + x]];
     for (int t = lane; t < p_n; t += 32) cols[t] = ciC[cs + t];
     __syncwarp();
-    const int T = min(pre[na], tk.t_hi);
-    for (int x = lane; x < p_n * BS; x += 32) sums[x] = 0.0;
+    const int tend = min(pre[na], tk.t_hi);
+    for (int x = lane; x < p_n * BS; x += 32) sums[x] = T(0);
     bool okp = true;
-    for (int t0 = tk.t_lo; t0 < T; t0 += capT) {
-      const int tn = min(capT, T - t0);
+    for (int t0 = tk.t_lo; t0 < tend; t0 += capT) {
+      const int tn = min(capT, tend - t0);
       for (int t = lane; t < p_n; t += 32) {
         start[t] = 0;
         off[t] = 0;
@@ -424,14 +426,14 @@ __global__ void __launch_bounds__(256)
       int cur = -1;
       bool own = false;
       if (q_lo < q_hi) {
-        double acc[BS], av[AS], bv[BB], an[AS], bn[BB];
+        T acc[BS], av[AS], bv[BB], an[AS], bn[BB];
         int tl = srt[q_lo];
         cur = pl[tl];
         own = start[cur] == q_lo;
 #pragma unroll
-        for (int x = 0; x < BS; x++) acc[x] = own ? sums[cur * BS + x] : 0.0;
+        for (int x = 0; x < BS; x++) acc[x] = own ? sums[cur * BS + x] : T(0);
         {
-          const double *a = A.val + (int64_t)ee[tl] * AS, *b = B.val + (int64_t)ff[tl] * BB;
+          const T *a = A.val + (int64_t)ee[tl] * AS, *b = B.val + (int64_t)ff[tl] * BB;
 #pragma unroll
           for (int x = 0; x < AS; x++) av[x] = a[x];
 #pragma unroll
@@ -441,7 +443,7 @@ __global__ void __launch_bounds__(256)
           int tn2 = 0;
           if (q + 1 < q_hi) {   // fetch the next product's blocks while this one is summed
             tn2 = srt[q + 1];
-            const double *a = A.val + (int64_t)ee[tn2] * AS, *b = B.val + (int64_t)ff[tn2] * BB;
+            const T *a = A.val + (int64_t)ee[tn2] * AS, *b = B.val + (int64_t)ff[tn2] * BB;
 #pragma unroll
             for (int x = 0; x < AS; x++) an[x] = a[x];
 #pragma unroll
@@ -552,14 +554,15 @@ __global__ void k_classify_rows(const int *rpA, const int *rpC, int nbr, RowClas
 // summed in the same order on every run, with no atomics.
 constexpr int kProdChunk = 128;
 
-template <int BR, int BK, int BC>
-__global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const int *rpC, const int *ciC,
-                                    double *valC, const int *pending, int ulo, int ucap) {
+template <typename T, int BR, int BK, int BC>
+__global__ void k_spgemm_numeric_sh(BsrView<T> A, BsrView<T> B, const int *rpC, const int *ciC,
+                                    T *valC, const int *pending, int ulo, int ucap) {
   constexpr int BS = BR * BC;
-  extern __shared__ double smem[];
+  extern __shared__ double smem_raw[];
+  T *smem = reinterpret_cast<T *>(smem_raw);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  double *acc = smem + (size_t)wid * ucap * BS;
+  T *acc = smem + (size_t)wid * ucap * BS;
   int *ibase = reinterpret_cast<int *>(smem + (size_t)wpb * ucap * BS);
   int *cols = ibase + (size_t)wid * (ucap + 4 * kProdChunk * BR);
   int *ch_e = cols + ucap;
@@ -572,7 +575,7 @@ __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const 
     const int cs = rpC[i], cn = rpC[i + 1] - cs;
     if (cn <= ulo || cn > ucap) continue;   // another tier
     for (int t = lane; t < cn; t += 32) cols[t] = ciC[cs + t];
-    for (int t = lane; t < cn * BS; t += 32) acc[t] = 0.0;
+    for (int t = lane; t < cn * BS; t += 32) acc[t] = T(0);
     __syncwarp();
     int cnt = 0;
     auto flush = [&]() {
@@ -607,15 +610,15 @@ __global__ void k_spgemm_numeric_sh(BsrView<double> A, BsrView<double> B, const 
         if (q < mine) {
           const int code = list[off + q];
           const int t = code / BR, r = code - t * BR;
-          const double *a = A.val + (int64_t)ch_e[t] * BR * BK + r * BK;
-          const double *b = B.val + (int64_t)ch_f[t] * BK * BC;
-          double *c = acc + ch_p[t] * BS + r * BC;
-          double av[BK];
+          const T *a = A.val + (int64_t)ch_e[t] * BR * BK + r * BK;
+          const T *b = B.val + (int64_t)ch_f[t] * BK * BC;
+          T *c = acc + ch_p[t] * BS + r * BC;
+          T av[BK];
 #pragma unroll
           for (int tt = 0; tt < BK; tt++) av[tt] = a[tt];
 #pragma unroll
           for (int cc = 0; cc < BC; cc++) {
-            double v = c[cc];
+            T v = c[cc];
 #pragma unroll
             for (int tt = 0; tt < BK; tt++) v = fma(av[tt], b[tt * BC + cc], v);
             c[cc] = v;
@@ -656,8 +659,9 @@ __global__ void k_max_pending_len(const int *rp, int n, const int *pending, int 
 }
 
 // products and columns of the listed rows of C = A B
-__global__ void k_row_info(BsrView<double> A, BsrView<double> B, const int *rpC, const int *rows, int n,
-                           int *T, int *pn) {
+template <typename T>
+__global__ void k_row_info(BsrView<T> A, BsrView<T> B, const int *rpC, const int *rows, int n,
+                           int *nprod, int *pn) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < n; w += nw) {
@@ -669,7 +673,7 @@ __global__ void k_row_info(BsrView<double> A, BsrView<double> B, const int *rpC,
     }
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) {
-      T[w] = t;
+      nprod[w] = t;
       pn[w] = rpC[i + 1] - rpC[i];
     }
   }
@@ -681,34 +685,35 @@ struct SplitRow {
 };
 
 // a row split over nt tasks: its sums, added in task order
-__global__ void k_sum_split(const SplitRow *sr, int n, const int *rpC, const double *scratch, int bs,
-                            double *valC) {
+template <typename T>
+__global__ void k_sum_split(const SplitRow *sr, int n, const int *rpC, const T *scratch, int bs,
+                            T *valC) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < n; w += nw) {
     const SplitRow r = sr[w];
     const int64_t len = (int64_t)r.pn * bs;
     for (int64_t x = lane; x < len; x += 32) {
-      double v = scratch[r.soff + x];
+      T v = scratch[r.soff + x];
       for (int k = 1; k < r.nt; k++) v += scratch[r.soff + k * len + x];
       valC[(int64_t)rpC[r.row] * bs + x] = v;
     }
   }
 }
 
-template <int BR, int BK, int BC, bool GS>
-void launch_mp(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, const int *rows,
-               const int *nrows, const SpgemmTask *tasks, double *scratch, int capC, int capA, int capT,
+template <typename T, int BR, int BK, int BC, bool GS>
+void launch_mp(const BsrView<T> &A, const BsrView<T> &B, Bsr<T> &C, const int *rows,
+               const int *nrows, const SpgemmTask *tasks, T *scratch, int capC, int capA, int capT,
                int *flags, cudaStream_t s) {
   // shared memory per warp; up to eight warps per block, as many blocks per SM as fit
-  const size_t per_warp = (size_t)((GS ? 0 : capC) + 32) * BR * BC * sizeof(double) +
+  const size_t per_warp = (size_t)((GS ? 0 : capC) + 32) * BR * BC * sizeof(T) +
                           (size_t)(3 * capC + 2 * capA + 2 + 4 * capT) * sizeof(int);
   const size_t budget = 225 * 1024;
   FS_REQUIRE(per_warp <= budget, FC_INTERNAL, "spgemm: row class does not fit in shared memory");
   const int wpb = (int)std::min<size_t>(8, budget / per_warp);
   const size_t shm = per_warp * wpb;
   const int per_sm = (int)std::min<size_t>(4, std::max<size_t>(1, budget / shm));
-  auto kern = k_spgemm_numeric_mp<BR, BK, BC, GS>;
+  auto kern = k_spgemm_numeric_mp<T, BR, BK, BC, GS>;
   FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
   kern<<<kSMs * per_sm, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, rows, nrows, tasks, scratch, capA, capC,
                                             capT, flags);
@@ -718,8 +723,8 @@ void launch_mp(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &
 constexpr int kTaskT = 8 * kSegT;                  // products per task of a split row, at least
 constexpr size_t kSplitScratch = (size_t)512 << 20;   // bytes of partial sums, at most
 
-template <int BR, int BK, int BC>
-void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s) {
+template <typename T, int BR, int BK, int BC>
+void numeric(const BsrView<T> &A, const BsrView<T> &B, Bsr<T> &C, cudaStream_t s) {
   constexpr int BS = BR * BC;
   if (C.nbr == 0) return;
   // three length classes of C rows (columns, A-row entries): short rows sum
@@ -755,9 +760,9 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   // segments of kSegT products in every class (longer segments for the
   // longer rows, 768 and 1536 products, were slower at 128^3: fewer warps
   // per SM)
-  launch_mp<BR, BK, BC, false>(A, B, C, lists.p, counts.p, nullptr, nullptr, rc.caps[0], rc.capa[0], kSegT,
+  launch_mp<T, BR, BK, BC, false>(A, B, C, lists.p, counts.p, nullptr, nullptr, rc.caps[0], rc.capa[0], kSegT,
                                flags.p, s);
-  launch_mp<BR, BK, BC, true>(A, B, C, lists.p + C.nbr, counts.p + 1, nullptr, nullptr, rc.caps[1], rc.capa[1],
+  launch_mp<T, BR, BK, BC, true>(A, B, C, lists.p + C.nbr, counts.p + 1, nullptr, nullptr, rc.caps[1], rc.capa[1],
                               kSegT, flags.p, s);
   int hc[3] = {0, 0, 0};
   FS_CUDA(cudaMemcpyAsync(hc, counts.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
@@ -765,7 +770,7 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   const int n2 = hc[2];
   DBuf<SpgemmTask> dtasks;
   DBuf<SplitRow> dsplit;
-  DBuf<double> scratch;
+  DBuf<T> scratch;
   DBuf<int> ntask;
   int nsplit = 0;
   if (n2 > 0) {
@@ -784,7 +789,7 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
       size_t bytes = 0;
       for (int w = 0; w < n2; w++) {
         const int64_t nt = std::max<int64_t>(1, (ht[w] + chunk - 1) / chunk);
-        if (nt > 1) bytes += (size_t)nt * hp[w] * BS * sizeof(double);
+        if (nt > 1) bytes += (size_t)nt * hp[w] * BS * sizeof(T);
       }
       if (bytes <= kSplitScratch) break;
       chunk *= 2;
@@ -793,14 +798,14 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
     std::vector<SplitRow> split;
     int64_t soff = 0;
     for (int w = 0; w < n2; w++) {
-      const int T = ht[w];
-      const int nt = (int)std::max<int64_t>(1, (T + chunk - 1) / chunk);
+      const int np = ht[w];
+      const int nt = (int)std::max<int64_t>(1, (np + chunk - 1) / chunk);
       if (nt == 1) {
-        tasks.push_back({hr[w], 0, T, -1});
+        tasks.push_back({hr[w], 0, np, -1});
         continue;
       }
       for (int k = 0; k < nt; k++)
-        tasks.push_back({hr[w], (int)((int64_t)T * k / nt), (int)((int64_t)T * (k + 1) / nt),
+        tasks.push_back({hr[w], (int)((int64_t)np * k / nt), (int)((int64_t)np * (k + 1) / nt),
                          soff + (int64_t)k * hp[w] * BS});
       split.push_back({hr[w], nt, hp[w], soff});
       soff += (int64_t)nt * hp[w] * BS;
@@ -816,7 +821,7 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
       scratch.alloc((size_t)soff);
       FS_CUDA(cudaMemcpyAsync(dsplit.p, split.data(), sizeof(SplitRow) * nsplit, cudaMemcpyHostToDevice, s));
     }
-    launch_mp<BR, BK, BC, true>(A, B, C, nullptr, ntask.p, dtasks.p, scratch.p, rc.caps[2], rc.capa[2], kSegT,
+    launch_mp<T, BR, BK, BC, true>(A, B, C, nullptr, ntask.p, dtasks.p, scratch.p, rc.caps[2], rc.capa[2], kSegT,
                                 flags.p, s);
     if (nsplit) {
       k_sum_split<<<blocks_for((int64_t)nsplit * 32, 256, kSMs * 8), 256, 0, s>>>(dsplit.p, nsplit, C.rp.p,
@@ -838,7 +843,7 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
   // the chunked kernel, in tiers of C-row length so that short rows run at
   // higher occupancy: per warp, ucap slots (accumulator + column) and the
   // product chunk
-  const size_t per_slot = BS * sizeof(double) + sizeof(int);
+  const size_t per_slot = BS * sizeof(T) + sizeof(int);
   const size_t fixed = (size_t)4 * kProdChunk * BR * sizeof(int);
   const int ctiers[3] = {64, 256, kListCap};
   FS_REQUIRE(umax <= kListCap, FC_INTERNAL, "spgemm: product row longer than the symbolic pass allows");
@@ -848,7 +853,7 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
     int wpb = 8;
     while (wpb > 1 && (size_t)wpb * (ucap * per_slot + fixed) > 200 * 1024) wpb >>= 1;
     const size_t shm = (size_t)wpb * (ucap * per_slot + fixed);
-    auto kern = k_spgemm_numeric_sh<BR, BK, BC>;
+    auto kern = k_spgemm_numeric_sh<T, BR, BK, BC>;
     FS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     kern<<<kSMs * 8, wpb * 32, shm, s>>>(A, B, C.rp.p, C.ci.p, C.val.p, pending.p, ulo, ucap);
     FS_LAUNCHED();
@@ -858,20 +863,30 @@ void numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C,
 
 }  // namespace
 
-void spgemm_numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s) {
-  FS_REQUIRE(A.bc == B.br && A.nbc == B.nbr && C.nbr == A.nbr && C.nbc == B.nbc && C.br == A.br && C.bc == B.bc,
-             FC_BAD_ARG, "spgemm_numeric: shape mismatch");
-  if (C.nnzb == 0) return;
+namespace {
+template <typename T>
+void numeric_any(const BsrView<T> &A, const BsrView<T> &B, Bsr<T> &C, cudaStream_t s) {
   const int sh = A.br * 100 + A.bc * 10 + B.bc;
   switch (sh) {
-    case 333: numeric<3, 3, 3>(A, B, C, s); break;
-    case 313: numeric<3, 1, 3>(A, B, C, s); break;
-    case 111: numeric<1, 1, 1>(A, B, C, s); break;
-    case 331: numeric<3, 3, 1>(A, B, C, s); break;
-    case 133: numeric<1, 3, 3>(A, B, C, s); break;
+    case 333: numeric<T, 3, 3, 3>(A, B, C, s); break;
+    case 313: numeric<T, 3, 1, 3>(A, B, C, s); break;
+    case 111: numeric<T, 1, 1, 1>(A, B, C, s); break;
+    case 331: numeric<T, 3, 3, 1>(A, B, C, s); break;
+    case 133: numeric<T, 1, 3, 3>(A, B, C, s); break;
     default: throw Error(FC_BAD_ARG, "spgemm: unsupported block shapes");
   }
 }
+}  // namespace
+
+template <typename T>
+void spgemm_numeric(const BsrView<T> &A, const BsrView<T> &B, Bsr<T> &C, cudaStream_t s) {
+  FS_REQUIRE(A.bc == B.br && A.nbc == B.nbr && C.nbr == A.nbr && C.nbc == B.nbc && C.br == A.br && C.bc == B.bc,
+             FC_BAD_ARG, "spgemm_numeric: shape mismatch");
+  if (C.nnzb == 0) return;
+  numeric_any<T>(A, B, C, s);
+}
+template void spgemm_numeric<double>(const BsrView<double> &, const BsrView<double> &, Bsr<double> &, cudaStream_t);
+template void spgemm_numeric<float>(const BsrView<float> &, const BsrView<float> &, Bsr<float> &, cudaStream_t);
 
 namespace {
 __global__ void k_diff_int(const int *a, const int *b, int64_t n, int *out) {
@@ -968,9 +983,22 @@ bool same_pattern(const BsrView<double> &A, const BsrView<double> &B, cudaStream
   return h == 0;
 }
 
-Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s) {
-  FS_REQUIRE(A.bc == B.br && A.nbc == B.nbr, FC_BAD_ARG, "spgemm: shape mismatch");
-  Bsr<double> C;
+namespace {
+// the sparsity pattern only (the symbolic kernel reads no values)
+template <typename T>
+BsrView<double> pattern_view(const BsrView<T> &M) {
+  BsrView<double> v;
+  v.nbr = M.nbr; v.nbc = M.nbc; v.br = M.br; v.bc = M.bc; v.nnzb = M.nnzb;
+  v.rp = M.rp; v.ci = M.ci; v.val = nullptr;
+  return v;
+}
+}  // namespace
+
+template <typename T>
+Bsr<T> spgemm(const BsrView<T> &At, const BsrView<T> &Bt, cudaStream_t s) {
+  FS_REQUIRE(At.bc == Bt.br && At.nbc == Bt.nbr, FC_BAD_ARG, "spgemm: shape mismatch");
+  const BsrView<double> A = pattern_view(At), B = pattern_view(Bt);
+  Bsr<T> C;
   C.shape(A.nbr, B.nbc, A.br, B.bc);
   C.rp.alloc(A.nbr + 1);
   DBuf<int> cnt(A.nbr + 1), ovf(1);
@@ -995,15 +1023,7 @@ Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStrea
   k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 1, nullptr, C.rp.p, C.ci.p, ovf.p);
   FS_LAUNCHED();
   pt.mark("symbolic fill");
-  const int sh = A.br * 100 + A.bc * 10 + B.bc;
-  switch (sh) {
-    case 333: numeric<3, 3, 3>(A, B, C, s); break;
-    case 313: numeric<3, 1, 3>(A, B, C, s); break;
-    case 111: numeric<1, 1, 1>(A, B, C, s); break;
-    case 331: numeric<3, 3, 1>(A, B, C, s); break;
-    case 133: numeric<1, 3, 3>(A, B, C, s); break;
-    default: throw Error(FC_BAD_ARG, "spgemm: unsupported block shapes");
-  }
+  numeric_any<T>(At, Bt, C, s);
   pt.mark("numeric");
   if (g_verbose > 1)
     fprintf(stderr, "[fracsolve] spgemm %d x %d blocks (%dx%d * %dx%d): A %lld, B %lld, C %lld blocks\n", A.nbr, B.nbc,
@@ -1011,6 +1031,8 @@ Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStrea
   FS_CUDA(cudaStreamSynchronize(s));
   return C;
 }
+template Bsr<double> spgemm<double>(const BsrView<double> &, const BsrView<double> &, cudaStream_t);
+template Bsr<float> spgemm<float>(const BsrView<float> &, const BsrView<float> &, cudaStream_t);
 
 // ============================================================ sparse add
 namespace {
@@ -1191,6 +1213,8 @@ Bsr<TO> copy_cast(const BsrView<TI> &A, cudaStream_t s) {
 }
 template Bsr<float> copy_cast<float, double>(const BsrView<double> &, cudaStream_t);
 template Bsr<double> copy_cast<double, double>(const BsrView<double> &, cudaStream_t);
+template Bsr<double> copy_cast<double, float>(const BsrView<float> &, cudaStream_t);
+template Bsr<float> copy_cast<float, float>(const BsrView<float> &, cudaStream_t);
 
 // ============================================================ sliced ELL
 namespace {

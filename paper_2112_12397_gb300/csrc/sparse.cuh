@@ -24,12 +24,15 @@ Bsr<double> transpose(const BsrView<double> &A, cudaStream_t s);
 
 // C = A B for block shapes (A.br x A.bc) (B.br x B.bc), A.bc == B.br.
 // Supported shapes: 3x3*3x3, 3x1*1x3, 1x1*1x1, 3x3*3x1, 1x3*3x3.
-// Rows of C sorted; entries that cancel to zero are kept.
-Bsr<double> spgemm(const BsrView<double> &A, const BsrView<double> &B, cudaStream_t s);
+// Rows of C sorted; entries that cancel to zero are kept.  T = double or
+// float (the products and sums in T; the same pattern and summation order).
+template <typename T>
+Bsr<T> spgemm(const BsrView<T> &A, const BsrView<T> &B, cudaStream_t s);
 
 // Numeric pass only: C (whose pattern is that of A B, e.g. from an earlier
 // spgemm of the same patterns) receives the values of A B.
-void spgemm_numeric(const BsrView<double> &A, const BsrView<double> &B, Bsr<double> &C, cudaStream_t s);
+template <typename T>
+void spgemm_numeric(const BsrView<T> &A, const BsrView<T> &B, Bsr<T> &C, cudaStream_t s);
 
 // True when the n doubles at a and b are bitwise identical (device arrays).
 bool same_values(const double *a, const double *b, int64_t n, cudaStream_t s);
