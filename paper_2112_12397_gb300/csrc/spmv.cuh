@@ -22,16 +22,7 @@ __device__ inline T group_sum(T v) {
 template <int BR, int BC, int G, typename TA, typename TX, typename Epi>
 __global__ void __launch_bounds__(256) k_bsr_spmv(BsrView<TA> A, const TX *__restrict__ x, Epi epi) {
   constexpr int BS = BR * BC;
-  // the group's next G blocks are read as G * BS consecutive scalars (lane l
-  // takes scalars l, l + G, ...: each load instruction reads contiguous
-  // memory) and staged in shared memory, from which each lane takes its own
-  // block (stride BS, odd for 3x3 blocks: no bank conflicts).  Reading a
-  // block per lane directly strides the lanes by BS scalars and multiplied
-  // the L1 requests per byte.
-  __shared__ TA stage[256 * BS];
   const int lane = threadIdx.x & (G - 1);
-  TA *st = stage + (threadIdx.x & ~(G - 1)) * BS;
-  const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1)));
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
   const bool valid = row < A.nbr;
   TA acc[BR];
@@ -39,27 +30,20 @@ __global__ void __launch_bounds__(256) k_bsr_spmv(BsrView<TA> A, const TX *__res
   for (int q = 0; q < BR; q++) acc[q] = TA(0);
   if (valid) {
     const int s = __ldg(A.rp + row), e = __ldg(A.rp + row + 1);
-    for (int b0 = s; b0 < e; b0 += G) {
-      const int64_t nv = (int64_t)min(G, e - b0) * BS;   // scalars of this chunk
-      const TA *src = A.val + (int64_t)b0 * BS;
+    // each lane takes whole blocks: no index arithmetic per scalar entry
+#pragma unroll 4
+    for (int b = s + lane; b < e; b += G) {
+      const int col = __ldg(A.ci + b);
+      TA a[BS];
 #pragma unroll
-      for (int q = 0; q < BS; q++) {
-        const int k = q * G + lane;
-        if (k < nv) st[k] = __ldg(src + k);
-      }
-      __syncwarp(gmask);
-      const int b = b0 + lane;
-      if (b < e) {
-        const int col = __ldg(A.ci + b);
-        TA xv[BC];
+      for (int q = 0; q < BS; q++) a[q] = __ldg(A.val + (int64_t)b * BS + q);
+      TA xv[BC];
 #pragma unroll
-        for (int j = 0; j < BC; j++) xv[j] = (TA)__ldg(x + (int64_t)col * BC + j);
+      for (int j = 0; j < BC; j++) xv[j] = (TA)__ldg(x + (int64_t)col * BC + j);
 #pragma unroll
-        for (int r = 0; r < BR; r++)
+      for (int r = 0; r < BR; r++)
 #pragma unroll
-          for (int j = 0; j < BC; j++) acc[r] += st[lane * BS + r * BC + j] * xv[j];
-      }
-      __syncwarp(gmask);
+        for (int j = 0; j < BC; j++) acc[r] += a[r * BC + j] * xv[j];
     }
   }
 #pragma unroll
