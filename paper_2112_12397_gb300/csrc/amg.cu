@@ -47,6 +47,8 @@ inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
 #define FS_SELL_MAX_MEAN_ROW 40.0
 #endif
 constexpr double kSellMaxMeanRow = FS_SELL_MAX_MEAN_ROW;
+// prolongators of at most this many block rows run as lane-group BSR
+constexpr int kProlongBsrMaxRows = 200000;
 
 __device__ inline double frob2(const double *v, int bs) {
   double s = 0.0;
@@ -957,7 +959,20 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
     c.op.bv = c.S;
     c.op.nnzb = L.S.nnzb;
     c.op.nbr = L.nb;
-    if (!last) c.Ps = to_sell<TP>(L.P.view(), s);
+    if (!last) {
+      c.Ps = to_sell<TP>(L.P.view(), s);
+      // levels with few rows prolong through the lane-group BSR kernel: a
+      // warp per 32-row slice leaves most of the GPU idle there
+      if (L.nb <= kProlongBsrMaxRows) {
+        if constexpr (std::is_same<TP, double>::value) c.P = L.P.view();
+        else {
+          c.P_own = copy_cast<TP, double>(L.P.view(), s);
+          c.P = c.P_own.view();
+        }
+      } else {
+        c.P = BsrView<TP>();
+      }
+    }
     c.f.alloc(n > 0 ? n : 1);
     c.x.alloc(n > 0 ? n : 1);
     c.xa.alloc(n > 0 ? n : 1);
@@ -1273,7 +1288,8 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
   else cycle_level<B, TP, TR>(H, C, l + 1, cn.f.p, cn.x.p, s);
   if (pf) pf->stop(PK_COARSE0, s, 0.0);
   if (pf) pf->start(PK_PROLONG0, s);
-  sell_axpby<B, B>(c.Ps.view(), cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
+  if (c.P.nbr > 0 && c.P.nbr <= kProlongBsrMaxRows) spmv_axpby<B, B>(c.P, cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
+  else sell_axpby<B, B>(c.Ps.view(), cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
   if (pf) pf->stop(PK_PROLONG0, s, (double)c.Ps.nnzb * (B * B * sizeof(TP) + 4) + (double)c.Ps.nbr * 4);
   // post-smoothing from the corrected iterate
   rho = 1.0 / c.sigma;

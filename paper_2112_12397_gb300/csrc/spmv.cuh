@@ -131,6 +131,53 @@ struct EpiHinvUpdate {
   }
 };
 
+// One block of 256 threads per row, for matrices with few, very long rows
+// (the restrictions of the coarse levels: ~100-5000 rows of hundreds of
+// blocks): each thread takes whole blocks with a stride of 256, the warps
+// reduce with shuffles and the block through shared memory, and thread 0
+// hands the sums to the epilogue.
+template <int BR, int BC, typename TA, typename TX, typename Epi>
+__global__ void __launch_bounds__(256) k_bsr_spmv_rowcta(BsrView<TA> A, const TX *__restrict__ x, Epi epi) {
+  constexpr int BS = BR * BC;
+  __shared__ TA part[8][BR];
+  const int64_t row = blockIdx.x;
+  const int s = __ldg(A.rp + row), e = __ldg(A.rp + row + 1);
+  TA acc[BR];
+#pragma unroll
+  for (int q = 0; q < BR; q++) acc[q] = TA(0);
+  for (int b = s + threadIdx.x; b < e; b += 256) {
+    const int col = __ldg(A.ci + b);
+    TA xv[BC];
+#pragma unroll
+    for (int j = 0; j < BC; j++) xv[j] = (TA)__ldg(x + (int64_t)col * BC + j);
+#pragma unroll
+    for (int r = 0; r < BR; r++)
+#pragma unroll
+      for (int j = 0; j < BC; j++) acc[r] += __ldg(A.val + (int64_t)b * BS + r * BC + j) * xv[j];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < BR; q++) {
+    const TA v = group_sum<32>(acc[q]);
+    if (lane == 0) part[wid][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < BR; q++) {
+      TA v = part[0][q];
+      for (int w = 1; w < 8; w++) v += part[w][q];
+      acc[q] = v;
+    }
+    epi(row, acc);
+  }
+}
+
+// rows of at least this many blocks on average, in a matrix of at most
+// kRowCtaMaxRows rows, take one block of threads each
+constexpr double kRowCtaMinMean = 200.0;
+constexpr int kRowCtaMaxRows = 8 * 152 * 4;
+
 // lanes per row from the mean number of blocks per row (a sweep on the
 // 128^3 workload: 16 lanes for the ~69-block rows of the first coarse level
 // beat 32 by 11% on the coarse part of the cycle; the ~126-block rows of
@@ -160,6 +207,11 @@ inline void spmv_g(const BsrView<TA> &A, const TX *x, const Epi &epi, cudaStream
 template <int BR, int BC, typename TA, typename TX, typename Epi>
 inline void spmv(const BsrView<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
   if (A.nbr <= 0) return;
+  if (A.nbr <= kRowCtaMaxRows && (double)A.nnzb / A.nbr >= kRowCtaMinMean) {
+    k_bsr_spmv_rowcta<BR, BC, TA, TX, Epi><<<(unsigned)A.nbr, 256, 0, s>>>(A, x, epi);
+    FS_LAUNCHED();
+    return;
+  }
   switch (lanes_for(A.nnzb, A.nbr, BR * BC)) {
     case 32: spmv_g<BR, BC, 32>(A, x, epi, s); break;
     case 16: spmv_g<BR, BC, 16>(A, x, epi, s); break;
