@@ -48,7 +48,7 @@ inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
 #endif
 constexpr double kSellMaxMeanRow = FS_SELL_MAX_MEAN_ROW;
 // prolongators of at most this many block rows run as lane-group BSR
-constexpr int kProlongBsrMaxRows = 200000;
+constexpr int kProlongBsrMaxRows = 20000;
 
 __device__ inline double frob2(const double *v, int bs) {
   double s = 0.0;

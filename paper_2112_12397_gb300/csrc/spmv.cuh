@@ -185,11 +185,14 @@ constexpr int kRowCtaMaxRows = 8 * 152 * 4;
 #ifndef FS_BSR_LANES32_ABOVE
 #define FS_BSR_LANES32_ABOVE 100.0
 #endif
+#ifndef FS_BSR_LANES16_ABOVE
+#define FS_BSR_LANES16_ABOVE 12.0
+#endif
 inline int lanes_for(int64_t nnzb, int nbr, int bs) {
   (void)bs;
   double per = nbr > 0 ? (double)nnzb / nbr : 0.0;
   if (per > FS_BSR_LANES32_ABOVE) return 32;
-  if (per > 12) return 16;
+  if (per > FS_BSR_LANES16_ABOVE) return 16;
   if (per > 6) return 8;
   return 4;
 }
