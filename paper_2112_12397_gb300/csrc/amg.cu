@@ -49,6 +49,8 @@ inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
 constexpr double kSellMaxMeanRow = FS_SELL_MAX_MEAN_ROW;
 // prolongators of at most this many block rows run as lane-group BSR
 constexpr int kProlongBsrMaxRows = 20000;
+// scalar hierarchies of at most this many rows run their whole cycle as a graph
+constexpr int64_t kWholeGraphMaxRows = 200000;
 
 __device__ inline double frob2(const double *v, int bs) {
   double s = 0.0;
@@ -1161,6 +1163,7 @@ void amg_refresh(Hierarchy &H, Bsr<double> &&S0, int precision, cudaStream_t s) 
              "AMG refresh: the operator's pattern differs from the one the hierarchy was built on");
   for (auto &row : H.coarse)
     for (auto &g : row) g.reset();
+  for (auto &g : H.whole) g.reset();
   H.have_t = false;
   if (H.B == 3) refresh_levels<3>(H, std::move(S0), precision, s);
   else refresh_levels<1>(H, std::move(S0), precision, s);
@@ -1175,6 +1178,7 @@ void amg_setup(Hierarchy &H, Bsr<double> &&S0, int B, const AmgParams &prm, int 
   H.graphs = prm.graphs;
   for (auto &row : H.coarse)
     for (auto &g : row) g.reset();
+  for (auto &g : H.whole) g.reset();
   if (B == 3) setup_levels<3>(H, std::move(S0), precision, s);
   else if (B == 1) setup_levels<1>(H, std::move(S0), precision, s);
   else throw Error(FC_BAD_ARG, "AMG block size must be 1 or 3");
@@ -1320,8 +1324,52 @@ void amg_vcycle(Hierarchy &H, const TP *f, TP *x, cudaStream_t s) {
   if constexpr (std::is_same<TP, float>::value) C = &H.cf;
   else C = &H.cd;
   FS_REQUIRE(!C->empty(), FC_NOT_SETUP, "AMG cycle data not prepared for this precision");
-  if (H.B == 3) cycle_level<3, TP>(H, *C, 0, f, x, s);
-  else cycle_level<1, TP>(H, *C, 0, f, x, s);
+  if (H.B == 3) {
+    cycle_level<3, TP>(H, *C, 0, f, x, s);
+    return;
+  }
+  // a small scalar hierarchy (T or S~2: a few ten thousand rows) is all
+  // short kernels: its whole cycle replays as one graph on the level-0
+  // buffers, f copied in and x copied out
+  LevelCycle<TP> &c0 = (*C)[0];
+  const int64_t n0 = (int64_t)H.lev[0].nb;
+  if (!H.graphs || C->size() < 2 || n0 > kWholeGraphMaxRows || n0 == 0) {
+    cycle_level<1, TP>(H, *C, 0, f, x, s);
+    return;
+  }
+  GraphExec &ge = H.whole[sizeof(TP) == 8 ? 1 : 0];
+  if (!ge.g) {
+    cudaStream_t cs = nullptr;
+    FS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    const unsigned long long k0 = launch_count();
+    H.graphs = false;   // no nested capture of the coarse levels
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        cycle_level<1, TP>(H, *C, 0, c0.f.p, c0.x.p, cs);
+      } catch (...) {
+        H.graphs = true;
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        throw;
+      }
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    H.graphs = true;
+    const unsigned long long captured = launch_count() - k0;
+    add_launches(-(long long)captured);   // recorded, not run
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.g, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    FS_CUDA(e);
+    ge.kernels = captured;
+  }
+  FS_CUDA(cudaMemcpyAsync(c0.f.p, f, sizeof(TP) * n0, cudaMemcpyDeviceToDevice, s));
+  FS_CUDA(cudaGraphLaunch(ge.g, s));
+  add_launches((long long)ge.kernels);
+  FS_CUDA(cudaMemcpyAsync(x, c0.x.p, sizeof(TP) * n0, cudaMemcpyDeviceToDevice, s));
 }
 
 template void amg_vcycle<float>(Hierarchy &, const float *, float *, cudaStream_t);

@@ -111,6 +111,9 @@ struct Hierarchy {
   // its buffers (level-1 f and x and below) are fixed for the hierarchy
   bool graphs = true;
   GraphExec coarse[2][2];
+  // the whole cycle of a small scalar hierarchy as one graph, on its level-0
+  // buffers: [double precision]
+  GraphExec whole[2];
   int levels() const { return (int)lev.size(); }
 };
 

@@ -178,15 +178,15 @@ __global__ void __launch_bounds__(256) k_bsr_spmv_rowcta(BsrView<TA> A, const TX
 constexpr double kRowCtaMinMean = 200.0;
 constexpr int kRowCtaMaxRows = 8 * 152 * 4;
 
-// lanes per row from the mean number of blocks per row (a sweep on the
-// 128^3 workload: 16 lanes for the ~69-block rows of the first coarse level
-// beat 32 by 11% on the coarse part of the cycle; the ~126-block rows of
-// the finest restriction keep 32)
+// lanes per row from the mean number of blocks per row (sweeps on the
+// 128^3 workload, coarse part of the cycle: for the ~69-block rows of the
+// first coarse level 8 lanes 0.359 ms, 16 lanes 0.373 ms, 32 lanes
+// 0.425 ms; the ~126-block rows of the finest restriction keep 32)
 #ifndef FS_BSR_LANES32_ABOVE
 #define FS_BSR_LANES32_ABOVE 100.0
 #endif
 #ifndef FS_BSR_LANES16_ABOVE
-#define FS_BSR_LANES16_ABOVE 12.0
+#define FS_BSR_LANES16_ABOVE 100.0
 #endif
 inline int lanes_for(int64_t nnzb, int nbr, int bs) {
   (void)bs;
