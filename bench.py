@@ -603,17 +603,27 @@ def ours(args, rank, world, local_rank):
         hx = torch.zeros_like(hb).pin_memory()
         h2d += hb.numel() * 8
         d2h = hx.numel() * 8
-        times = []
+        times, t_setup = [], []
         for k in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ctx.setup_host(host, P.n_node, P.n_face)
+            t1 = time.perf_counter()
             rc, it, rr = ctx.solve_host(args.variant, hb, hx, args.tol, args.maxit, allow_fail=True)
             torch.cuda.synchronize()
             if k > 0:
                 times.append(time.perf_counter() - t0)
+                t_setup.append(t1 - t0)
+        # the host-to-device bandwidth alone: one pinned copy of A's values
+        a_h, a_d = host["A"][2], blocks["A"][2]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a_d.copy_(a_h, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = a_h.numel() * 8 / (time.perf_counter() - t0) / 1e9
         e2e = {"value": statistics.mean(times), "unit": "s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "api": "fc_setup_host + fc_solve_host"}
+               "d2h_bytes_per_step": int(d2h), "api": "fc_setup_host + fc_solve_host",
+               "setup_host_s": statistics.mean(t_setup), "pinned_h2d_GBps": h2d_gbs}
         del host
 
     # the instance assembled on the device by fc_generate (same seed and
