@@ -77,8 +77,9 @@ def parse():
                     help="time the oracle at the workload's full size (long: minutes per solve)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--verbose", type=int, default=0, help="library diagnostics (setup phase times) to stderr")
-    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle"],
-                    help="vcycle: fc_setup then two V-cycles of the elasticity hierarchy (profiling case)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle", "generate"],
+                    help="vcycle: fc_setup then two V-cycles of the elasticity hierarchy (profiling case); "
+                         "generate: fc_generate of the workload, --steps times (profiling case)")
     return ap.parse_args()
 
 
@@ -733,10 +734,35 @@ def vcycle_case(args):
     print(json.dumps({"mode": "vcycle", "workload": args.workload, "norm": float(x.norm())}))
 
 
+def generate_case(args):
+    """fc_generate of the workload, timed with CUDA events (the instance is
+    freed between calls)."""
+    import torch
+
+    import paper_2112_12397_gb300 as fs
+    fs.load()
+    ms = []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        inst = fs.generate(args.workload, **({"N": args.N} if args.N else {}))
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+        n = inst.n
+        inst.close()
+    print(json.dumps({"mode": "generate", "workload": args.workload, "unknowns": int(n),
+                      "ms": statistics.mean(ms) if ms else None}))
+
+
 def main():
     args = parse()
     if args.mode == "vcycle":
         vcycle_case(args)
+        return
+    if args.mode == "generate":
+        generate_case(args)
         return
     rank, world, local_rank = rank_env()
     if args.impl == "reference":
