@@ -139,6 +139,7 @@ namespace {
 constexpr int kHashCap = 1024;     // per-warp hash slots (power of two)
 constexpr int kListCap = 768;      // unique columns a row may hold
 constexpr int kWarpsPerBlock = 4;
+constexpr int64_t kStashMax = (int64_t)1 << 30;   // stash entries of the one-enumeration symbolic pass, at most
 
 struct WarpHash {
   int *keys;   // kHashCap
@@ -216,12 +217,13 @@ __device__ inline int product_entry(const int *pre, int na, int t) {
 
 constexpr int kSymPre = 512;   // A-row entries the flattened symbolic pass takes
 
-// pass 0: count unique columns per row; pass 1: write sorted columns.  The
-// products of a row are enumerated flat (all lanes busy even when the rows
-// of B are short); rows of A longer than kSymPre take the entry-by-entry loop.
+// pass 0: count unique columns per row and, when stash is given, keep them
+// (unsorted) at stash + soff[i]; pass 1: write sorted columns.  The products
+// of a row are enumerated flat (all lanes busy even when the rows of B are
+// short); rows of A longer than kSymPre take the entry-by-entry loop.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_spgemm_symbolic(BsrView<double> A, BsrView<double> B, int pass, int *cnt, const int *rpC,
-                      int *ciC, int *overflow) {
+                      int *ciC, int *overflow, int *stash = nullptr, const int *soff = nullptr) {
   __shared__ int s_keys[kWarpsPerBlock][kHashCap];
   __shared__ int s_list[kWarpsPerBlock][kListCap];
   __shared__ int s_pre[kWarpsPerBlock][kSymPre + 1];
@@ -271,6 +273,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
     if (pass == 0) {
       if (lane == 0) cnt[i] = u;
+      if (stash)
+        for (int a = lane; a < u; a += 32) stash[soff[i] + a] = h.list[a];
     } else {
       int base = rpC[i];
       for (int a = lane; a < u; a += 32) {
@@ -281,6 +285,37 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       }
     }
     __syncwarp();
+  }
+}
+
+// stash capacity of each row of C = A B: its product count, at most kListCap
+__global__ void k_stash_cap(BsrView<double> A, BsrView<double> B, int *cap) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < A.nbr; i += nw) {
+    int t = 0;
+    for (int e = A.rp[i] + lane; e < A.rp[i + 1]; e += 32) {
+      const int k = A.ci[e];
+      t += B.rp[k + 1] - B.rp[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) cap[i] = min(t, kListCap);
+  }
+}
+
+// columns of row i of C: its stashed unique columns, sorted by rank
+__global__ void k_stash_sort(int nbr, const int *stash, const int *soff, const int *rpC, int *ciC) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nbr; i += nw) {
+    const int base = rpC[i], u = rpC[i + 1] - base;
+    const int *l = stash + soff[i];
+    for (int a = lane; a < u; a += 32) {
+      const int key = l[a];
+      int rank = 0;
+      for (int b = 0; b < u; b++) rank += (l[b] < key);
+      ciC[base + rank] = key;
+    }
   }
 }
 
@@ -1006,22 +1041,43 @@ Bsr<T> spgemm(const BsrView<T> &At, const BsrView<T> &Bt, cudaStream_t s) {
   FS_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int) * (A.nbr + 1), s));
   const int grid = kSMs * 8;
   PhaseTimer pt(g_verbose > 1, s, "spgemm");
+  // one enumeration of the products: the count pass keeps each row's unique
+  // columns in a stash sized by the row's product count (at most kListCap),
+  // and the fill sorts them; rows are enumerated and hashed once instead of
+  // twice.  A stash beyond kStashMax entries falls back to a second pass.
+  DBuf<int> scap(A.nbr + 1), soff(A.nbr + 1), stash;
+  int64_t stash_n = 0;
   if (A.nbr > 0) {
-    k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 0, cnt.p, nullptr, nullptr, ovf.p);
+    k_stash_cap<<<blocks_for((int64_t)A.nbr * 32, 256, kSMs * 8), 256, 0, s>>>(A, B, scap.p);
+    FS_LAUNCHED();
+    stash_n = exclusive_scan(scap.p, soff.p, A.nbr, s);
+  }
+  const bool stashed = stash_n > 0 && stash_n <= kStashMax;
+  if (stashed) stash.alloc((size_t)stash_n);
+  if (A.nbr > 0) {
+    k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 0, cnt.p, nullptr, nullptr, ovf.p,
+                                                          stashed ? stash.p : nullptr, soff.p);
     FS_LAUNCHED();
   }
   pt.mark("symbolic count");
   int64_t nnz = exclusive_scan(cnt.p, C.rp.p, A.nbr, s);
   int hovf = 0;
-  FS_CUDA(cudaMemcpy(&hovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
+  FS_CUDA(cudaMemcpyAsync(&hovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
   FS_REQUIRE(!hovf, FC_INTERNAL, "spgemm: a product row has more than 768 block columns");
   C.nnzb = nnz;
   C.ci.alloc(nnz);
   C.val.alloc(nnz * C.br * C.bc);
   if (nnz == 0) return C;
   pt.mark("scan + alloc");
-  k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 1, nullptr, C.rp.p, C.ci.p, ovf.p);
-  FS_LAUNCHED();
+  if (stashed) {
+    k_stash_sort<<<blocks_for((int64_t)A.nbr * 32, 256, kSMs * 16), 256, 0, s>>>(A.nbr, stash.p, soff.p, C.rp.p,
+                                                                                C.ci.p);
+    FS_LAUNCHED();
+  } else {
+    k_spgemm_symbolic<<<grid, kWarpsPerBlock * 32, 0, s>>>(A, B, 1, nullptr, C.rp.p, C.ci.p, ovf.p);
+    FS_LAUNCHED();
+  }
   pt.mark("symbolic fill");
   numeric_any<T>(At, Bt, C, s);
   pt.mark("numeric");
