@@ -5,9 +5,10 @@ file under _build/, then linked into lib/libfracsolve.so.  Rebuilds only
 when a source or header is newer than the library.
 
 A second library, lib/libfracsolve_testhooks.so, links the same objects
-except the block SpGEMM, which is compiled once more with FS_TEST_HOOKS: in
-that build an environment variable can force the SpGEMM's long-row and
-chunked paths on small problems, so that a GPU test covers them.  Only that
+except the block SpGEMM and sliced-ELL conversions and the AMG, which are
+compiled once more with FS_TEST_HOOKS: in that build environment variables
+can force the SpGEMM's long-row and chunked paths, jagged slices and the
+fused prolongation on small problems, so that GPU tests cover them.  Only that
 test loads it; the product library reads no environment variable.
 """
 from __future__ import annotations
@@ -23,7 +24,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libfracsolve.so")
 LIB_HOOKS = os.path.join(LIBDIR, "libfracsolve_testhooks.so")
-HOOKED = "sparse.cu"          # the translation unit with the test hook
+HOOKED = ("sparse.cu", "amg.cu")   # the translation units with test hooks
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -73,11 +74,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return obj
 
     srcs = _sources()
-    jobs = [(s, False) for s in srcs] + [(s, True) for s in srcs if os.path.basename(s) == HOOKED]
+    jobs = [(s, False) for s in srcs] + [(s, True) for s in srcs if os.path.basename(s) in HOOKED]
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         objs = list(ex.map(one, jobs))
     plain = objs[:len(srcs)]
-    hooked = [o for o, (s, _) in zip(plain, jobs) if os.path.basename(s) != HOOKED] + objs[len(srcs):]
+    hooked = [o for o, (s, _) in zip(plain, jobs) if os.path.basename(s) not in HOOKED] + objs[len(srcs):]
     for out, parts in ((LIB, plain), (LIB_HOOKS, hooked)):
         tmp = out + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *parts, "-lcudart"]

@@ -21,6 +21,7 @@
 // Chebyshev smoother on [cheb_lo * cheb_hi * lambda, cheb_hi * lambda]
 // (Saad, Alg. 12.1) fused with the residual in one pass over S.
 #include <cmath>
+#include <cstdlib>
 #include <type_traits>
 
 #include "amg.cuh"
@@ -47,8 +48,18 @@ inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
 #define FS_SELL_MAX_MEAN_ROW 40.0
 #endif
 constexpr double kSellMaxMeanRow = FS_SELL_MAX_MEAN_ROW;
-// prolongators of at most this many block rows run as lane-group BSR
+// prolongators of at most this many block rows run as lane-group BSR; larger
+// levels prolong through [P | S P] fused with the first post-smoothing step
 constexpr int kProlongBsrMaxRows = 20000;
+// test hook, compiled only into the test build (FS_TEST_HOOKS):
+// FS_PROLONG_BSR_MAX_ROWS=<rows> moves the threshold, so that small problems
+// run the fused prolongation that only large levels take
+inline int prolong_bsr_max_rows() {
+#ifdef FS_TEST_HOOKS
+  if (const char *ev = std::getenv("FS_PROLONG_BSR_MAX_ROWS")) return (int)std::strtol(ev, nullptr, 10);
+#endif
+  return kProlongBsrMaxRows;
+}
 // scalar hierarchies of at most this many rows run their whole cycle as a graph
 constexpr int64_t kWholeGraphMaxRows = 200000;
 
@@ -965,7 +976,7 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
       c.Ps = to_sell<TP>(L.P.view(), s);
       // levels with few rows prolong through the lane-group BSR kernel: a
       // warp per 32-row slice leaves most of the GPU idle there
-      if (L.nb <= kProlongBsrMaxRows) {
+      if (L.nb <= prolong_bsr_max_rows()) {
         if constexpr (std::is_same<TP, double>::value) c.P = L.P.view();
         else {
           c.P_own = copy_cast<TP, double>(L.P.view(), s);
@@ -973,6 +984,13 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
         }
       } else {
         c.P = BsrView<TP>();
+        // the prolongation and the first post-smoothing step read P and S P
+        // (in the cycle precision: S P is formed in it by the Galerkin product)
+        if constexpr (std::is_same<TP, float>::value) {
+          if (L.SPf.nbr == L.nb && L.SPf.rp.p) c.PSP = to_jag2<float, float>(L.P.view(), L.SPf.view(), s);
+        } else {
+          if (L.SP.nbr == L.nb && L.SP.rp.p) c.PSP = to_jag2<double, double>(L.P.view(), L.SP.view(), s);
+        }
       }
     }
     c.f.alloc(n > 0 ? n : 1);
@@ -1291,13 +1309,24 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
   if (l == 0 && H.graphs && L > 2) coarse_graph<B, TP, TR>(H, C, s);
   else cycle_level<B, TP, TR>(H, C, l + 1, cn.f.p, cn.x.p, s);
   if (pf) pf->stop(PK_COARSE0, s, 0.0);
-  if (pf) pf->start(PK_PROLONG0, s);
-  if (c.P.nbr > 0 && c.P.nbr <= kProlongBsrMaxRows) spmv_axpby<B, B>(c.P, cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
-  else sell_axpby<B, B>(c.Ps.view(), cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
-  if (pf) pf->stop(PK_PROLONG0, s, (double)c.Ps.nnzb * (B * B * sizeof(TP) + 4) + (double)c.Ps.nbr * 4);
-  // post-smoothing from the corrected iterate
   rho = 1.0 / c.sigma;
-  {
+  if (!TR && c.PSP.nbr > 0) {
+    // prolongation and the first post-smoothing step in one pass: the
+    // residual of the corrected iterate is r - (S P) x_c
+    EpiProlongCheb<B, TP> e{buf[cur], c.r.p, Dv, buf[1 - cur], c.d.p, (TP)(1.0 / c.theta)};
+    if (pf) pf->start(PK_PROLONG0, s);
+    jag2_spmv<B, B>(c.PSP.view(), cn.x.p, e, s);
+    if (pf)
+      pf->stop(PK_PROLONG0, s,
+               (double)c.PSP.nnzb * (B * B * sizeof(TP) + 4) + (double)c.PSP.nbr * (8 + 5 * B * sizeof(TP)) +
+                   (double)c.PSP.nbr * B * B * sizeof(TP));
+    cur ^= 1;
+  } else {
+    if (pf) pf->start(PK_PROLONG0, s);
+    if (c.P.nbr > 0) spmv_axpby<B, B>(c.P, cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
+    else sell_axpby<B, B>(c.Ps.view(), cn.x.p, buf[cur], 1.0, 1.0, buf[cur], s);
+    if (pf) pf->stop(PK_PROLONG0, s, (double)c.Ps.nnzb * (B * B * sizeof(TP) + 4) + (double)c.Ps.nbr * 4);
+    // post-smoothing from the corrected iterate
     EpiCheb<B, TP> e{f, buf[cur], buf[1 - cur], c.d.p, Dv, (TP)0, (TP)(1.0 / c.theta)};
     if (pf) pf->start(PK_SMOOTH0, s);
     op_spmv<B, B>(Sop, buf[cur], e, s);

@@ -11,6 +11,17 @@
 // point at column 0 with zero values.  Each thread accumulates its own BR
 // outputs in registers, so there is no cross-lane reduction and the epilogue
 // runs on all lanes at once.
+//
+// Jagged slices, for matrices with much padding (prolongators; the node rows
+// of C1 and Q1, empty away from the fractures): the rows of a slice are given
+// to the lanes in order of decreasing length, so at entry slot k the lanes
+// that still hold an entry are a prefix of the warp, of length a_k = the
+// popcount of a ballot; slot k stores only those a_k entries (a_k column
+// indices, then each block scalar as a_k consecutive values), the slots of a
+// slice one after the other (the jagged-diagonal layout within a slice of 32
+// rows).  A slice then starts at the row pointer of its first row, and there
+// is no padding to read.  The permutation stays inside the slice, so the
+// epilogue's row accesses still fall in the slice's own lines.
 #pragma once
 
 #include "common.cuh"
@@ -23,30 +34,42 @@ constexpr int kSellH = 32;   // block rows per slice
 template <typename T>
 struct SellView {
   int nbr = 0, nbc = 0, br = 0, bc = 0, nslice = 0;
-  int64_t slots = 0;           // sum over slices of their widths
-  const int64_t *sp = nullptr; // nslice + 1 slot offsets
-  const int *ci = nullptr;     // slots * kSellH
-  const T *val = nullptr;      // slots * br * bc * kSellH
+  const int64_t *sp = nullptr; // nslice + 1 offsets (in slots of kSellH entries; jagged: in entries)
+  const int *ci = nullptr;
+  const T *val = nullptr;
+  // jagged slices: nslice * kSellH lane entries (row length << 5) | position
+  // of the lane's row in its slice, lanes in order of decreasing length;
+  // null for padded slices (lane l holds row l)
+  const int *lm = nullptr;
 };
 
 template <typename T>
 struct Sell {
   int nbr = 0, nbc = 0, br = 0, bc = 0, nslice = 0;
-  int64_t slots = 0, nnzb = 0;
+  int64_t nnzb = 0;
   DBuf<int64_t> sp;
   DBuf<int> ci;
   DBuf<T> val;
+  DBuf<int> lm;
   SellView<T> view() const {
     SellView<T> v;
-    v.nbr = nbr; v.nbc = nbc; v.br = br; v.bc = bc; v.nslice = nslice; v.slots = slots;
-    v.sp = sp.p; v.ci = ci.p; v.val = val.p;
+    v.nbr = nbr; v.nbc = nbc; v.br = br; v.bc = bc; v.nslice = nslice;
+    v.sp = sp.p; v.ci = ci.p; v.val = val.p; v.lm = lm.p;
     return v;
   }
 };
 
-// Convert a double BSR matrix (sorted rows) into sliced ELL of value type T.
-template <typename T>
-Sell<T> to_sell(const BsrView<double> &A, cudaStream_t s);
+// Jagged slices are used where padded slices would hold more than
+// kSellJagPadding x the entries and more than kSellJagMinBytes: smaller
+// operators (the coarse levels, the pressure hierarchies) are bound by
+// latency, not by the bytes the padding adds.
+constexpr double kSellJagPadding = 1.10;
+constexpr double kSellJagMinBytes = 32.0 * (1 << 20);
+
+// Convert a BSR matrix (sorted rows) into sliced ELL of value type T, padded
+// or jagged by the rule above.
+template <typename T, typename TI>
+Sell<T> to_sell(const BsrView<TI> &A, cudaStream_t s);
 
 template <int BR, int BC, typename TA, typename TX, typename Epi>
 __global__ void __launch_bounds__(256) k_sell_spmv(SellView<TA> A, const TX *__restrict__ x, Epi epi) {
@@ -79,12 +102,145 @@ __global__ void __launch_bounds__(256) k_sell_spmv(SellView<TA> A, const TX *__r
   if (row < A.nbr) epi(row, acc);
 }
 
+// Jagged slices (layout above): one warp per slice, the loop over the slots
+// uniform across the warp; a lane loads only while its row has entries.
+template <int BR, int BC, typename TA, typename TX, typename Epi>
+__global__ void __launch_bounds__(256) k_sell_spmv_jag(SellView<TA> A, const TX *__restrict__ x, Epi epi) {
+  constexpr int BS = BR * BC;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t slice = t / kSellH;
+  const int lane = (int)(t % kSellH);
+  if (slice >= A.nslice) return;   // whole warps: blockDim is a multiple of kSellH
+  const int m = __ldg(A.lm + t);
+  const int len = m >> 5;
+  const int w = __shfl_sync(0xffffffffu, len, 0);   // lane 0 holds the longest row
+  int64_t off = A.sp[slice];
+  TA acc[BR];
+#pragma unroll
+  for (int q = 0; q < BR; q++) acc[q] = TA(0);
+#pragma unroll 4
+  for (int k = 0; k < w; k++) {
+    const int ak = __popc(__ballot_sync(0xffffffffu, k < len));
+    if (k < len) {
+      const int c = __ldg(A.ci + off + lane);
+      const TA *__restrict__ v = A.val + off * BS + lane;
+      TA a[BS];
+#pragma unroll
+      for (int q = 0; q < BS; q++) a[q] = __ldg(v + (int64_t)q * ak);
+      TA xv[BC];
+#pragma unroll
+      for (int j = 0; j < BC; j++) xv[j] = (TA)__ldg(x + (int64_t)c * BC + j);
+#pragma unroll
+      for (int r = 0; r < BR; r++)
+#pragma unroll
+        for (int j = 0; j < BC; j++) acc[r] += a[r * BC + j] * xv[j];
+    }
+    off += ak;
+  }
+  const int64_t out = slice * kSellH + (m & 31);
+  if (out < A.nbr) epi(out, acc);
+}
+
+// Two matrices with the same rows and column space, read in one pass (the
+// prolongator P and the product S P of a V-cycle level, both applied to the
+// coarse correction): row i stores its entries of the first matrix, then
+// those of the second, in jagged 32-row slices in natural row order.  At slot
+// k the lanes whose row still has entries store theirs contiguously, in lane
+// order; a lane finds its place as the popcount of the active lanes below it.
+// A slice starts at the sum of the two row pointers of its first row.
+template <typename T>
+struct Jag2View {
+  int nbr = 0, nbc = 0, br = 0, bc = 0, nslice = 0;
+  const int64_t *sp = nullptr;   // nslice + 1 entry offsets
+  const int2 *len = nullptr;     // per row: (entries of the first matrix, entries of both)
+  const int *ci = nullptr;
+  const T *val = nullptr;
+};
+
+template <typename T>
+struct Jag2 {
+  int nbr = 0, nbc = 0, br = 0, bc = 0, nslice = 0;
+  int64_t nnzb = 0;
+  DBuf<int64_t> sp;
+  DBuf<int2> len;
+  DBuf<int> ci;
+  DBuf<T> val;
+  Jag2View<T> view() const {
+    Jag2View<T> v;
+    v.nbr = nbr; v.nbc = nbc; v.br = br; v.bc = bc; v.nslice = nslice;
+    v.sp = sp.p; v.len = len.p; v.ci = ci.p; v.val = val.p;
+    return v;
+  }
+};
+
+// [P | Q] of two BSR matrices with equal rows, block shape and columns (P in
+// double, Q in double or float), values in T.
+template <typename T, typename TQ>
+Jag2<T> to_jag2(const BsrView<double> &P, const BsrView<TQ> &Q, cudaStream_t s);
+
+// acc1 = (first matrix) x, acc2 = (second matrix) x; epi(row, acc1, acc2)
+template <int BR, int BC, typename TA, typename TX, typename Epi>
+__global__ void __launch_bounds__(256) k_jag2_spmv(Jag2View<TA> A, const TX *__restrict__ x, Epi epi) {
+  constexpr int BS = BR * BC;
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t slice = row / kSellH;
+  const int lane = (int)(row % kSellH);
+  if (slice >= A.nslice) return;   // whole warps: blockDim is a multiple of kSellH
+  const int2 ln = row < A.nbr ? A.len[row] : make_int2(0, 0);
+  int w = ln.y;
+#pragma unroll
+  for (int o = kSellH / 2; o; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+  const unsigned below = (1u << lane) - 1u;
+  int64_t off = A.sp[slice];
+  TA a1[BR], a2[BR];
+#pragma unroll
+  for (int q = 0; q < BR; q++) a1[q] = a2[q] = TA(0);
+#pragma unroll 2
+  for (int k = 0; k < w; k++) {
+    const bool on = k < ln.y;
+    const unsigned act = __ballot_sync(0xffffffffu, on);
+    const int ak = __popc(act);
+    if (on) {
+      const int rk = __popc(act & below);
+      const int c = __ldg(A.ci + off + rk);
+      const TA *__restrict__ v = A.val + off * BS + rk;
+      TA a[BS];
+#pragma unroll
+      for (int q = 0; q < BS; q++) a[q] = __ldg(v + (int64_t)q * ak);
+      TA xv[BC];
+#pragma unroll
+      for (int j = 0; j < BC; j++) xv[j] = (TA)__ldg(x + (int64_t)c * BC + j);
+      const bool first = k < ln.x;
+#pragma unroll
+      for (int r = 0; r < BR; r++) {
+        TA t = first ? a1[r] : a2[r];
+#pragma unroll
+        for (int j = 0; j < BC; j++) t += a[r * BC + j] * xv[j];
+        if (first) a1[r] = t;
+        else a2[r] = t;
+      }
+    }
+    off += ak;
+  }
+  if (row < A.nbr) epi(row, a1, a2);
+}
+
+template <int BR, int BC, typename TA, typename TX, typename Epi>
+inline void jag2_spmv(const Jag2View<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
+  if (A.nbr <= 0) return;
+  const int threads = 256;
+  const int64_t blocks = ((int64_t)A.nslice * kSellH + threads - 1) / threads;
+  k_jag2_spmv<BR, BC, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi);
+  FS_LAUNCHED();
+}
+
 template <int BR, int BC, typename TA, typename TX, typename Epi>
 inline void sell_spmv(const SellView<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
   if (A.nbr <= 0) return;
   const int threads = 256;
   const int64_t blocks = ((int64_t)A.nslice * kSellH + threads - 1) / threads;
-  k_sell_spmv<BR, BC, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi);
+  if (A.lm) k_sell_spmv_jag<BR, BC, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi);
+  else k_sell_spmv<BR, BC, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi);
   FS_LAUNCHED();
 }
 

@@ -1274,7 +1274,8 @@ template Bsr<float> copy_cast<float, float>(const BsrView<float> &, cudaStream_t
 
 // ============================================================ sliced ELL
 namespace {
-__global__ void k_sell_width(BsrView<double> A, int nslice, int *w) {
+template <typename TI>
+__global__ void k_sell_width(BsrView<TI> A, int nslice, int *w) {
   for (int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sl < nslice;
        sl += (int64_t)gridDim.x * blockDim.x) {
     int m = 0;
@@ -1294,8 +1295,38 @@ __global__ void k_to_i64(const int *in, int64_t *out, int n) {
     out[i] = in[i];
 }
 
-template <typename T>
-__global__ void k_sell_fill(BsrView<double> A, int nslice, const int64_t *sp, int *ci, T *val) {
+// Lane order of a jagged slice: the row at position r of slice sl goes to
+// lane = (number of the slice's rows that are longer) + (number of equally
+// long rows before it); rows past the matrix count as empty and come last.
+template <typename TI>
+__global__ void k_sell_sort(BsrView<TI> A, int nslice, int *lm) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nslice * kSellH;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = t / kSellH;
+    const int r = (int)(t % kSellH);
+    const int len = t < A.nbr ? A.rp[t + 1] - A.rp[t] : 0;
+    int lane = 0;
+    for (int q = 0; q < kSellH; q++) {
+      const int64_t u = sl * kSellH + q;
+      const int lq = u < A.nbr ? A.rp[u + 1] - A.rp[u] : 0;
+      lane += lq > len || (lq == len && q < r);
+    }
+    lm[sl * kSellH + lane] = (len << 5) | r;
+  }
+}
+
+// a jagged slice starts at the row pointer of its first row
+template <typename TI>
+__global__ void k_jag_offsets(BsrView<TI> A, int nslice, int64_t *sp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nslice;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i * kSellH < A.nbr ? i * kSellH : A.nbr;
+    sp[i] = A.rp[r];
+  }
+}
+
+template <typename T, typename TI>
+__global__ void k_sell_fill(BsrView<TI> A, int nslice, const int64_t *sp, int *ci, T *val) {
   const int bs = A.br * A.bc;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nslice * kSellH;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -1317,10 +1348,34 @@ __global__ void k_sell_fill(BsrView<double> A, int nslice, const int64_t *sp, in
     }
   }
 }
+
+// jagged fill: one warp per slice, the same slot walk as the product kernel
+template <typename T, typename TI>
+__global__ void k_sell_fill_jag(BsrView<TI> A, int nslice, const int64_t *sp, const int *lm, int *ci, T *val) {
+  const int bs = A.br * A.bc;
+  const int lane = (int)(threadIdx.x % kSellH);
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) / kSellH;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kSellH; sl < nslice; sl += nwarp) {
+    const int m = lm[sl * kSellH + lane];
+    const int len = m >> 5;
+    const int64_t row = sl * kSellH + (m & 31);
+    const int b0 = row < A.nbr ? A.rp[row] : 0;
+    const int w = __shfl_sync(0xffffffffu, len, 0);
+    int64_t off = sp[sl];
+    for (int k = 0; k < w; k++) {
+      const int ak = __popc(__ballot_sync(0xffffffffu, k < len));
+      if (k < len) {
+        ci[off + lane] = A.ci[b0 + k];
+        for (int q = 0; q < bs; q++) val[(off * bs) + (int64_t)q * ak + lane] = (T)A.val[(int64_t)(b0 + k) * bs + q];
+      }
+      off += ak;
+    }
+  }
+}
 }  // namespace
 
-template <typename T>
-Sell<T> to_sell(const BsrView<double> &A, cudaStream_t s) {
+template <typename T, typename TI>
+Sell<T> to_sell(const BsrView<TI> &A, cudaStream_t s) {
   Sell<T> S;
   S.nbr = A.nbr; S.nbc = A.nbc; S.br = A.br; S.bc = A.bc; S.nnzb = A.nnzb;
   S.nslice = (A.nbr + kSellH - 1) / kSellH;
@@ -1329,23 +1384,125 @@ Sell<T> to_sell(const BsrView<double> &A, cudaStream_t s) {
     FS_CUDA(cudaMemsetAsync(S.sp.p, 0, sizeof(int64_t), s));
     return S;
   }
+  const int bs = A.br * A.bc;
   DBuf<int> w(S.nslice + 1), wp(S.nslice + 1);
-  k_sell_width<<<blocks_for(S.nslice, 128, kSMs * 8), 128, 0, s>>>(A, S.nslice, w.p);
+  k_sell_width<TI><<<blocks_for(S.nslice, 128, kSMs * 8), 128, 0, s>>>(A, S.nslice, w.p);
   FS_LAUNCHED();
-  S.slots = exclusive_scan(w.p, wp.p, S.nslice, s);
+  const int64_t slots = exclusive_scan(w.p, wp.p, S.nslice, s);
+  const double padded = (double)slots * kSellH;
+  // every slice is at most `slots` wide, so the row lengths fit the 27 bits
+  // of a lane entry
+  bool jag = padded > kSellJagPadding * (double)A.nnzb &&
+             padded * (bs * sizeof(T) + sizeof(int)) > kSellJagMinBytes && slots < (int64_t(1) << 26);
+  // test hook, compiled only into the test build (FS_TEST_HOOKS):
+  // FS_SELL_FORCE_JAG=1 makes every sliced-ELL copy jagged, so that small
+  // problems run the layout only large ones choose
+#ifdef FS_TEST_HOOKS
+  if (const char *ev = std::getenv("FS_SELL_FORCE_JAG"))
+    if (std::strtol(ev, nullptr, 10) == 1 && slots < (int64_t(1) << 26)) jag = true;
+#endif
+  if (jag) {
+    S.lm.alloc((size_t)S.nslice * kSellH);
+    k_sell_sort<TI><<<blocks_for((int64_t)S.nslice * kSellH, 128, kSMs * 16), 128, 0, s>>>(A, S.nslice, S.lm.p);
+    FS_LAUNCHED();
+    k_jag_offsets<TI><<<blocks_for(S.nslice + 1, 256, kSMs * 4), 256, 0, s>>>(A, S.nslice, S.sp.p);
+    FS_LAUNCHED();
+    S.ci.alloc((size_t)A.nnzb + kSellH);
+    S.val.alloc(((size_t)A.nnzb + kSellH) * bs);
+    if (A.nnzb) {
+      k_sell_fill_jag<T, TI><<<blocks_for((int64_t)S.nslice * kSellH, 128, kSMs * 16), 128, 0, s>>>(
+          A, S.nslice, S.sp.p, S.lm.p, S.ci.p, S.val.p);
+      FS_LAUNCHED();
+    }
+    return S;
+  }
   k_to_i64<<<blocks_for(S.nslice + 1, 256, kSMs * 4), 256, 0, s>>>(wp.p, S.sp.p, S.nslice);
   FS_LAUNCHED();
-  S.ci.alloc(S.slots * kSellH);
-  S.val.alloc(S.slots * kSellH * A.br * A.bc);
-  if (S.slots) {
-    k_sell_fill<T><<<blocks_for((int64_t)S.nslice * kSellH, 128, kSMs * 16), 128, 0, s>>>(A, S.nslice, S.sp.p, S.ci.p,
-                                                                                       S.val.p);
+  S.ci.alloc(slots * kSellH);
+  S.val.alloc(slots * kSellH * bs);
+  if (slots) {
+    k_sell_fill<T, TI><<<blocks_for((int64_t)S.nslice * kSellH, 128, kSMs * 16), 128, 0, s>>>(A, S.nslice, S.sp.p,
+                                                                                          S.ci.p, S.val.p);
     FS_LAUNCHED();
   }
   return S;
 }
-template Sell<float> to_sell<float>(const BsrView<double> &, cudaStream_t);
-template Sell<double> to_sell<double>(const BsrView<double> &, cudaStream_t);
+namespace {
+template <typename TQ>
+__global__ void k_jag2_offsets(BsrView<double> P, BsrView<TQ> Q, int nslice, int64_t *sp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nslice;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i * kSellH < P.nbr ? i * kSellH : P.nbr;
+    sp[i] = (int64_t)P.rp[r] + Q.rp[r];
+  }
+}
+
+// one warp per slice, the slot walk of k_jag2_spmv
+template <typename T, typename TQ>
+__global__ void k_jag2_fill(BsrView<double> P, BsrView<TQ> Q, int nslice, const int64_t *sp, int2 *len, int *ci,
+                            T *val) {
+  const int bs = P.br * P.bc;
+  const int lane = (int)(threadIdx.x % kSellH);
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) / kSellH;
+  for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kSellH; sl < nslice; sl += nwarp) {
+    const int64_t row = sl * kSellH + lane;
+    const bool real = row < P.nbr;
+    const int p0 = real ? P.rp[row] : 0, lp = real ? P.rp[row + 1] - p0 : 0;
+    const int q0 = real ? Q.rp[row] : 0, lq = real ? Q.rp[row + 1] - q0 : 0;
+    const int L = lp + lq;
+    if (real) len[row] = make_int2(lp, L);
+    int w = L;
+    for (int o = kSellH / 2; o; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+    int64_t off = sp[sl];
+    for (int k = 0; k < w; k++) {
+      const bool on = k < L;
+      const unsigned act = __ballot_sync(0xffffffffu, on);
+      const int ak = __popc(act);
+      if (on) {
+        const int rk = __popc(act & below);
+        T *v = val + off * bs + rk;
+        if (k < lp) {
+          ci[off + rk] = P.ci[p0 + k];
+          for (int q = 0; q < bs; q++) v[(int64_t)q * ak] = (T)P.val[(int64_t)(p0 + k) * bs + q];
+        } else {
+          const int kk = k - lp;
+          ci[off + rk] = Q.ci[q0 + kk];
+          for (int q = 0; q < bs; q++) v[(int64_t)q * ak] = (T)Q.val[(int64_t)(q0 + kk) * bs + q];
+        }
+      }
+      off += ak;
+    }
+  }
+}
+}  // namespace
+
+template <typename T, typename TQ>
+Jag2<T> to_jag2(const BsrView<double> &P, const BsrView<TQ> &Q, cudaStream_t s) {
+  FS_REQUIRE(P.nbr == Q.nbr && P.nbc == Q.nbc && P.br == Q.br && P.bc == Q.bc, FC_INTERNAL,
+             "to_jag2: the two matrices differ in shape");
+  Jag2<T> J;
+  J.nbr = P.nbr; J.nbc = P.nbc; J.br = P.br; J.bc = P.bc; J.nnzb = P.nnzb + Q.nnzb;
+  J.nslice = (P.nbr + kSellH - 1) / kSellH;
+  J.sp.alloc((size_t)J.nslice + 1);
+  J.len.alloc((size_t)std::max(P.nbr, 1));
+  J.ci.alloc((size_t)J.nnzb + kSellH);
+  J.val.alloc(((size_t)J.nnzb + kSellH) * P.br * P.bc);
+  k_jag2_offsets<TQ><<<blocks_for(J.nslice + 1, 256, kSMs * 4), 256, 0, s>>>(P, Q, J.nslice, J.sp.p);
+  FS_LAUNCHED();
+  if (J.nslice) {
+    k_jag2_fill<T, TQ><<<blocks_for((int64_t)J.nslice * kSellH, 128, kSMs * 16), 128, 0, s>>>(
+        P, Q, J.nslice, J.sp.p, J.len.p, J.ci.p, J.val.p);
+    FS_LAUNCHED();
+  }
+  return J;
+}
+template Jag2<float> to_jag2<float, float>(const BsrView<double> &, const BsrView<float> &, cudaStream_t);
+template Jag2<double> to_jag2<double, double>(const BsrView<double> &, const BsrView<double> &, cudaStream_t);
+
+template Sell<float> to_sell<float, double>(const BsrView<double> &, cudaStream_t);
+template Sell<double> to_sell<double, double>(const BsrView<double> &, cudaStream_t);
+template Sell<float> to_sell<float, float>(const BsrView<float> &, cudaStream_t);
 
 Bsr<double> upload_bsr(int nbr, int nbc, int br, int bc, int64_t nnzb, const int *rp_dev,
                        const int *ci_dev, const double *val_dev, cudaStream_t s) {

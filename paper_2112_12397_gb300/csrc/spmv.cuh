@@ -112,6 +112,39 @@ struct EpiCheb {
   }
 };
 
+// The prolongation of a V-cycle level fused with the first post-smoothing
+// step (a Chebyshev step from the corrected iterate, no previous direction).
+// With x1 = x + P x_c, the residual f - S x1 equals r - (S P) x_c, where
+// r = f - S x is the residual already formed for the restriction, so the step
+// reads P and S P instead of P and S:
+//   x1 = x + acc1;  d = cr Dinv (r - acc2);  x_out = x1 + d
+// (acc1 = (P x_c)[row], acc2 = (S P x_c)[row]).
+template <int BR, typename TA>
+struct EpiProlongCheb {
+  const TA *x;
+  const TA *r;
+  const TA *Dinv;
+  TA *x_out;
+  TA *d;
+  TA cr;
+  __device__ void operator()(int64_t row, const TA *acc1, const TA *acc2) const {
+    TA res[BR];
+#pragma unroll
+    for (int q = 0; q < BR; q++) res[q] = r[row * BR + q] - acc2[q];
+    const TA *D = Dinv + row * BR * BR;
+#pragma unroll
+    for (int a = 0; a < BR; a++) {
+      TA s = 0;
+#pragma unroll
+      for (int b = 0; b < BR; b++) s += D[a * BR + b] * res[b];
+      const TA dn = cr * s;
+      d[row * BR + a] = dn;
+      const TA x1 = x[row * BR + a] + acc1[a];
+      x_out[row * BR + a] = x1 + dn;
+    }
+  }
+};
+
 // The last step of Alg. 2 and Alg. 4 fused with the C2 product:
 //   v_t[row] = -t_t[row] + Hinv[row] * (C2 v_u)[row]
 template <typename TA>

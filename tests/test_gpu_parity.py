@@ -551,3 +551,100 @@ def test_galerkin_products_in_the_long_row_class(fs, task, monkeypatch):
         ctx.vcycle(hier, cuda(f), x)
         assert rel(x.cpu().numpy(), ref(f)) <= 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["planes7_ragged", "rects16", "network16"])
+def test_jagged_slices_match_the_oracle(fs, name, precision, monkeypatch):
+    """Every sliced-ELL copy (the blocks of J and J^T, the preconditioner's
+    coupling blocks, every level's operator and prolongator) built as jagged
+    slices, the layout chosen for large padded matrices (rows sorted by length
+    within each slice of 32, only the entries stored): J x and J^T x within
+    the row-wise rounding bound, V-cycles and applications as with padded
+    slices, and the solve takes the same iterations to the same x."""
+    monkeypatch.setenv("FS_SELL_FORCE_JAG", "1")
+    preset, over, cm, cmp = CASES[name]
+    P = fracgen.generate(preset, **over)
+    opt = dict(precision=precision, coarse_max=cm, coarse_max_p=cmp)
+    ctx = fs.context_for(P, fs.default_options(**opt), lib=fs.load_test_hooks())
+    monkeypatch.delenv("FS_SELL_FORCE_JAG")
+    base = fs.context_for(P, fs.default_options(**opt))
+    J = osp.jacobian(P)
+    x = np.random.default_rng(11).standard_normal(P.n)
+    for fwd, M in ((True, J), (False, J.T.tocsr())):
+        y = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+        (ctx.spmv if fwd else ctx.spmv_adjoint)(cuda(x), y)
+        assert np.all(np.abs(y.cpu().numpy() - M @ x) <= 2e-14 * (abs(M) @ np.abs(x))), fwd
+    w = np.random.default_rng(12).standard_normal(P.n)
+    for variant in ("tpu", "tup", "tup_star"):
+        for adj in (False, True):
+            v, vb = (torch.zeros(P.n, dtype=torch.float64, device="cuda") for _ in range(2))
+            (ctx.apply_prec_adjoint if adj else ctx.apply_prec)(variant, cuda(w), v)
+            (base.apply_prec_adjoint if adj else base.apply_prec)(variant, cuda(w), vb)
+            # the same sums in the same order: only the slice layout differs
+            assert_fields(P, v.cpu().numpy(), vb.cpu().numpy(), 1e-12, f"{name} {variant} adj={adj}")
+    if precision == "fp64":
+        S1 = schur.s1(P)
+        ref = AMG(S1, 3, AmgOptions(coarse_max=cm))
+        f = np.random.default_rng(13).standard_normal(S1.shape[0])
+        xv = torch.zeros(S1.shape[0], dtype=torch.float64, device="cuda")
+        ctx.vcycle(fs.FC_H_TUP_U, cuda(f), xv)
+        assert rel(xv.cpu().numpy(), ref(f)) <= 1e-10
+    b = cuda(P.b)
+    for variant in ("tpu", "tup"):
+        x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+        _, it1, rr1 = ctx.solve(variant, b, x1, 1e-8, 400)
+        _, it2, _ = base.solve(variant, b, x2, 1e-8, 400)
+        assert it1 == it2 and rr1 <= 1e-8
+        assert_fields(P, x1.cpu().numpy(), x2.cpu().numpy(), 1e-10, f"{name} {variant} x")
+    ctx.close()
+    base.close()
+
+
+@pytest.mark.parametrize("name", ["planes7_ragged", "rects16", "network16"])
+def test_fused_prolongation_matches_the_oracle(fs, name, monkeypatch):
+    """Every level's prolongation run as the one pass over [P | S P] fused
+    with the first post-smoothing step (the form that levels of more than
+    20,000 block rows take): with x1 = x + P x_c, the step's residual is
+    r - (S P) x_c with r the residual formed for the restriction.  FP64
+    V-cycles of all four hierarchies and both applications match the oracle
+    as the unfused cycle does; FP64 and mixed solves take the iterations of
+    the unfused cycle.  A dropped term or a sign error in the fused residual
+    changes every V-cycle by far more than 1e-10."""
+    monkeypatch.setenv("FS_PROLONG_BSR_MAX_ROWS", "0")
+    preset, over, cm, cmp = CASES[name]
+    P = fracgen.generate(preset, **over)
+    lib = fs.load_test_hooks()
+    ctx = fs.context_for(P, fs.default_options(coarse_max=cm, coarse_max_p=cmp), lib=lib)
+    ctxm = fs.context_for(P, fs.default_options(precision="mixed", coarse_max=cm, coarse_max_p=cmp), lib=lib)
+    monkeypatch.delenv("FS_PROLONG_BSR_MAX_ROWS")
+    base = fs.context_for(P, fs.default_options(precision="mixed", coarse_max=cm, coarse_max_p=cmp))
+    opt, optp = AmgOptions(coarse_max=cm), AmgOptions(coarse_max=cmp)
+    S1 = schur.s1(P)
+    for hier, M, B, o in ((fs.FC_H_TPU_U, schur.s_tilde(P, S1=S1), 3, opt), (fs.FC_H_TPU_P, osp.csr(P.T), 1, optp),
+                          (fs.FC_H_TUP_U, S1, 3, opt), (fs.FC_H_TUP_P, schur.s2_tilde(P, S1), 1, optp)):
+        ref = AMG(M, B, o)
+        f = np.random.default_rng(hier + 20).standard_normal(M.shape[0])
+        x = torch.zeros(M.shape[0], dtype=torch.float64, device="cuda")
+        ctx.vcycle(hier, cuda(f), x)
+        assert rel(x.cpu().numpy(), ref(f)) <= 1e-10, hier
+    J = osp.jacobian(P)
+    w = np.random.default_rng(21).standard_normal(P.n)
+    b = cuda(P.b)
+    for variant in ("tpu", "tup"):
+        M = BlockPreconditioner(P, variant, opt=opt, opt_p=optp)
+        v = torch.zeros(P.n, dtype=torch.float64, device="cuda")
+        ctx.apply_prec(variant, cuda(w), v)
+        assert_fields(P, v.cpu().numpy(), M(w), 1e-10, f"{name} {variant} fused M^-1 w")
+        x = torch.zeros_like(b)
+        _, it, rr = ctx.solve(variant, b, x, 1e-8, 400)
+        ref = fgmres(lambda q: J @ q, M, P.b, 1e-8, 400)
+        assert abs(it - ref.iters) <= 1 and rr <= 1e-8
+        assert_fields(P, x.cpu().numpy(), ref.x, 1e-8, f"{name} {variant} fused x")
+        xm, xb = torch.zeros_like(b), torch.zeros_like(b)
+        _, itm, rrm = ctxm.solve(variant, b, xm, 1e-8, 400)
+        _, itb, _ = base.solve(variant, b, xb, 1e-8, 400)
+        assert itm <= 1.15 * itb + 1 and rrm <= 1e-8
+        assert_fields(P, xm.cpu().numpy(), ref.x, 1e-9, f"{name} {variant} fused mixed x vs FP64 oracle")
+    for c in (ctx, ctxm, base):
+        c.close()
