@@ -373,8 +373,10 @@ int fc_get_fixed_stress(fc_ctx *ctx, double *h_sk);
  * blocks); FC_K_CGS = one classical Gram-Schmidt pass (dots + update);
  * FC_K_PREC = one preconditioner application; FC_K_VCYCLE = one V-cycle of
  * the elasticity hierarchy inside t-u-p (first of the two); FC_K_RESID0,
- * FC_K_RESTRICT0, FC_K_PROLONG0 = residual, restriction, prolongation on the
- * finest level; FC_K_COARSE0 = everything below the finest level;
+ * FC_K_RESTRICT0 = residual and restriction on the finest level;
+ * FC_K_PROLONG0 = the finest level's prolongation fused with its first
+ * post-smoothing step (one pass over P and S P); FC_K_COARSE0 = everything
+ * below the finest level;
  * FC_K_VCYCLE_P = the pressure V-cycle of t-u-p. */
 enum {
   FC_K_SMOOTH0 = 0, FC_K_JAC = 1, FC_K_CGS = 2, FC_K_VCYCLE = 3, FC_K_PREC = 4, FC_K_RESID0 = 5,

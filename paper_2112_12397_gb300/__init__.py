@@ -98,8 +98,13 @@ def load(build_if_missing: bool = False):
 
 
 def load_test_hooks():
-    """The test build of the library (same entry points; its block SpGEMM
-    honours the FS_SPGEMM_FORCE_LONG test variable).  Only tests use it."""
+    """The test build of the library: the same entry points, and it honours
+    test variables read at setup that send small problems down the paths
+    large ones take (FS_SPGEMM_FORCE_LONG: the SpGEMM's long-row and chunked
+    kernels; FS_SELL_FORCE_JAG: jagged sliced ELL everywhere; FS_JAG_LANES:
+    the lanes per row of the fused prolongation) or keep the prolongation and
+    the first post-smoothing step apart (FS_FUSE_PROLONG=0).  Only tests use
+    it."""
     global _lib_hooks
     if _lib_hooks is None:
         _lib_hooks = _open(LIB_HOOKS_PATH, False)

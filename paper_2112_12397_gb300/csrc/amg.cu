@@ -48,17 +48,26 @@ inline int grid_rows(int64_t n) { return blocks_for(n, kT, kSMs * 32); }
 #define FS_SELL_MAX_MEAN_ROW 40.0
 #endif
 constexpr double kSellMaxMeanRow = FS_SELL_MAX_MEAN_ROW;
-// prolongators of at most this many block rows run as lane-group BSR; larger
-// levels prolong through [P | S P] fused with the first post-smoothing step
+// The forward cycle prolongs through [P | S P], fused with the first
+// post-smoothing step; the transposed cycle (adjoint solves) prolongs with P
+// alone: as lane-group BSR on levels of at most this many block rows, as
+// sliced ELL above
 constexpr int kProlongBsrMaxRows = 20000;
-// test hook, compiled only into the test build (FS_TEST_HOOKS):
-// FS_PROLONG_BSR_MAX_ROWS=<rows> moves the threshold, so that small problems
-// run the fused prolongation that only large levels take
-inline int prolong_bsr_max_rows() {
+// lanes per row of the jagged copies; test hook: FS_JAG_LANES=<g> sets every
+// one to g lanes, so that small problems run the lane counts large ones take
+inline int jag_lanes_for(int64_t nnzb, int nbr) {
 #ifdef FS_TEST_HOOKS
-  if (const char *ev = std::getenv("FS_PROLONG_BSR_MAX_ROWS")) return (int)std::strtol(ev, nullptr, 10);
+  if (const char *ev = std::getenv("FS_JAG_LANES")) return (int)std::strtol(ev, nullptr, 10);
 #endif
-  return kProlongBsrMaxRows;
+  return jag_lanes(nnzb, nbr);
+}
+// the prolongation fused with the first post-smoothing step; test hook:
+// FS_FUSE_PROLONG=0 keeps them apart, so that a test can compare the two
+inline bool fuse_prolongation() {
+#ifdef FS_TEST_HOOKS
+  if (const char *ev = std::getenv("FS_FUSE_PROLONG")) return std::strtol(ev, nullptr, 10) != 0;
+#endif
+  return true;
 }
 // scalar hierarchies of at most this many rows run their whole cycle as a graph
 constexpr int64_t kWholeGraphMaxRows = 200000;
@@ -976,7 +985,7 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
       c.Ps = to_sell<TP>(L.P.view(), s);
       // levels with few rows prolong through the lane-group BSR kernel: a
       // warp per 32-row slice leaves most of the GPU idle there
-      if (L.nb <= prolong_bsr_max_rows()) {
+      if (L.nb <= kProlongBsrMaxRows) {
         if constexpr (std::is_same<TP, double>::value) c.P = L.P.view();
         else {
           c.P_own = copy_cast<TP, double>(L.P.view(), s);
@@ -984,12 +993,20 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
         }
       } else {
         c.P = BsrView<TP>();
-        // the prolongation and the first post-smoothing step read P and S P
-        // (in the cycle precision: S P is formed in it by the Galerkin product)
+      }
+      // the prolongation and the first post-smoothing step read P and S P
+      // (in the cycle precision: S P is formed in it by the Galerkin product)
+      if (fuse_prolongation() && L.nb > 0) {
         if constexpr (std::is_same<TP, float>::value) {
-          if (L.SPf.nbr == L.nb && L.SPf.rp.p) c.PSP = to_jag2<float, float>(L.P.view(), L.SPf.view(), s);
+          if (L.SPf.nbr == L.nb && L.SPf.rp.p) {
+            const BsrView<float> q = L.SPf.view();
+            c.PSP = to_jag<float, float>(L.P.view(), &q, jag_lanes_for(L.P.nnzb + q.nnzb, L.nb), s);
+          }
         } else {
-          if (L.SP.nbr == L.nb && L.SP.rp.p) c.PSP = to_jag2<double, double>(L.P.view(), L.SP.view(), s);
+          if (L.SP.nbr == L.nb && L.SP.rp.p) {
+            const BsrView<double> q = L.SP.view();
+            c.PSP = to_jag<double, double>(L.P.view(), &q, jag_lanes_for(L.P.nnzb + q.nnzb, L.nb), s);
+          }
         }
       }
     }

@@ -63,7 +63,7 @@ struct LevelCycle {
   Bsr<TP> S_own, P_own, R_own;   // used when TP differs from double
   Sell<TP> Ss, Ps;               // sliced-ELL copies of S and P used by the cycle
   Sell<TP> SsT;                  // S^T for the transposed cycle (adjoint solves)
-  Jag2<TP> PSP;                  // [P | S P] for the fused prolongation and first post-smoothing step
+  Jag<TP> PSP;                   // [P | S P] for the fused prolongation and first post-smoothing step
   DBuf<TP> DinvT;                // transposed diagonal blocks
   DBuf<TP> Dinv_own;
   DBuf<TP> f, x, xa, d, r;       // right-hand side, iterate (two buffers), direction, residual

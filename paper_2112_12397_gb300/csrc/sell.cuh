@@ -141,16 +141,22 @@ __global__ void __launch_bounds__(256) k_sell_spmv_jag(SellView<TA> A, const TX 
   if (out < A.nbr) epi(out, acc);
 }
 
-// Two matrices with the same rows and column space, read in one pass (the
-// prolongator P and the product S P of a V-cycle level, both applied to the
-// coarse correction): row i stores its entries of the first matrix, then
-// those of the second, in jagged 32-row slices in natural row order.  At slot
-// k the lanes whose row still has entries store theirs contiguously, in lane
-// order; a lane finds its place as the popcount of the active lanes below it.
-// A slice starts at the sum of the two row pointers of its first row.
+// Jagged lane-group slices, of one matrix or of two with the same rows and
+// column space read in one pass (the prolongator P and the product S P of a
+// V-cycle level, both applied to the coarse correction).  G lanes work on a
+// row (G = 1, 4, 8, 16 or 32; a slice of 32 lanes holds 32 / G rows in
+// natural order): lane j of a row takes its entries j, j + G, j + 2G, ... (for
+// two matrices, the row's entries of the first, then those of the second).
+// At slot k the lanes that still have an entry store theirs contiguously in
+// lane order, a column index each and then each block scalar as one run of
+// the active count; a lane finds its place as the popcount of the active
+// lanes below it.  Every load a warp issues is then one contiguous run with
+// no padding in it, however uneven the rows, and a slice starts at the sum of
+// the row pointers of its first row.  Sums over a row's lanes are taken with
+// shuffles, and the row's first lane runs the epilogue.
 template <typename T>
-struct Jag2View {
-  int nbr = 0, nbc = 0, br = 0, bc = 0, nslice = 0;
+struct JagView {
+  int nbr = 0, nbc = 0, br = 0, bc = 0, nslice = 0, g = 1;
   const int64_t *sp = nullptr;   // nslice + 1 entry offsets
   const int2 *len = nullptr;     // per row: (entries of the first matrix, entries of both)
   const int *ci = nullptr;
@@ -158,36 +164,63 @@ struct Jag2View {
 };
 
 template <typename T>
-struct Jag2 {
-  int nbr = 0, nbc = 0, br = 0, bc = 0, nslice = 0;
+struct Jag {
+  int nbr = 0, nbc = 0, br = 0, bc = 0, nslice = 0, g = 1;
   int64_t nnzb = 0;
   DBuf<int64_t> sp;
   DBuf<int2> len;
   DBuf<int> ci;
   DBuf<T> val;
-  Jag2View<T> view() const {
-    Jag2View<T> v;
-    v.nbr = nbr; v.nbc = nbc; v.br = br; v.bc = bc; v.nslice = nslice;
+  JagView<T> view() const {
+    JagView<T> v;
+    v.nbr = nbr; v.nbc = nbc; v.br = br; v.bc = bc; v.nslice = nslice; v.g = g;
     v.sp = sp.p; v.len = len.p; v.ci = ci.p; v.val = val.p;
     return v;
   }
 };
 
-// [P | Q] of two BSR matrices with equal rows, block shape and columns (P in
-// double, Q in double or float), values in T.
-template <typename T, typename TQ>
-Jag2<T> to_jag2(const BsrView<double> &P, const BsrView<TQ> &Q, cudaStream_t s);
+// Lanes per row for a jagged layout with `per` entries per row on average:
+// the fewest that leave a row at most kJagMaxSlots slots, then more while
+// the launch would hold fewer than kJagMinWarps warps (32 per SM).  Measured
+// on the fused prolongation at 128^3: one lane per row on the finest level
+// (22 entries per row) and 4 on the first coarse level (42 per row) gave the
+// shortest cycle; one lane everywhere made the coarse part 29% slower, and
+// every rule with more lanes on the finest level made its pass slower.
+#ifndef FS_JAG_MAX_SLOTS
+#define FS_JAG_MAX_SLOTS 24.0
+#endif
+#ifndef FS_JAG_MIN_WARPS
+#define FS_JAG_MIN_WARPS (32 * 152)
+#endif
+constexpr double kJagMaxSlots = FS_JAG_MAX_SLOTS;
+constexpr int64_t kJagMinWarps = FS_JAG_MIN_WARPS;
+inline int jag_lanes(int64_t nnzb, int nbr) {
+  const double per = nbr > 0 ? (double)nnzb / nbr : 0.0;
+  const int opts[5] = {1, 4, 8, 16, 32};
+  int i = 0;
+  while (i < 4 && per / opts[i] > kJagMaxSlots) i++;
+  while (i < 4 && (int64_t)nbr * opts[i] / 32 < kJagMinWarps) i++;
+  return opts[i];
+}
 
-// acc1 = (first matrix) x, acc2 = (second matrix) x; epi(row, acc1, acc2)
-template <int BR, int BC, typename TA, typename TX, typename Epi>
-__global__ void __launch_bounds__(256) k_jag2_spmv(Jag2View<TA> A, const TX *__restrict__ x, Epi epi) {
+// [P | Q] (Q null: P alone) of BSR matrices with equal rows, block shape and
+// columns (P in double, Q in double or float), values in T, g lanes per row.
+template <typename T, typename TQ>
+Jag<T> to_jag(const BsrView<double> &P, const BsrView<TQ> *Q, int g, cudaStream_t s);
+
+// one matrix: epi(row, acc); two: epi(row, acc1, acc2)
+template <int BR, int BC, int G, bool TWO, typename TA, typename TX, typename Epi>
+__global__ void __launch_bounds__(256) k_jag_spmv(JagView<TA> A, const TX *__restrict__ x, Epi epi) {
   constexpr int BS = BR * BC;
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t slice = row / kSellH;
-  const int lane = (int)(row % kSellH);
+  constexpr int RPS = kSellH / G;   // rows per slice
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t slice = t / kSellH;
+  const int lane = (int)(t % kSellH);
   if (slice >= A.nslice) return;   // whole warps: blockDim is a multiple of kSellH
+  const int j = lane % G;
+  const int64_t row = slice * RPS + lane / G;
   const int2 ln = row < A.nbr ? A.len[row] : make_int2(0, 0);
-  int w = ln.y;
+  int w = (ln.y + G - 1) / G;
 #pragma unroll
   for (int o = kSellH / 2; o; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
   const unsigned below = (1u << lane) - 1u;
@@ -197,7 +230,8 @@ __global__ void __launch_bounds__(256) k_jag2_spmv(Jag2View<TA> A, const TX *__r
   for (int q = 0; q < BR; q++) a1[q] = a2[q] = TA(0);
 #pragma unroll 2
   for (int k = 0; k < w; k++) {
-    const bool on = k < ln.y;
+    const int e = j + G * k;
+    const bool on = e < ln.y;
     const unsigned act = __ballot_sync(0xffffffffu, on);
     const int ak = __popc(act);
     if (on) {
@@ -209,29 +243,47 @@ __global__ void __launch_bounds__(256) k_jag2_spmv(Jag2View<TA> A, const TX *__r
       for (int q = 0; q < BS; q++) a[q] = __ldg(v + (int64_t)q * ak);
       TA xv[BC];
 #pragma unroll
-      for (int j = 0; j < BC; j++) xv[j] = (TA)__ldg(x + (int64_t)c * BC + j);
-      const bool first = k < ln.x;
+      for (int jj = 0; jj < BC; jj++) xv[jj] = (TA)__ldg(x + (int64_t)c * BC + jj);
+      const bool first = !TWO || e < ln.x;
 #pragma unroll
       for (int r = 0; r < BR; r++) {
-        TA t = first ? a1[r] : a2[r];
+        TA u = first ? a1[r] : a2[r];
 #pragma unroll
-        for (int j = 0; j < BC; j++) t += a[r * BC + j] * xv[j];
-        if (first) a1[r] = t;
-        else a2[r] = t;
+        for (int jj = 0; jj < BC; jj++) u += a[r * BC + jj] * xv[jj];
+        if (first) a1[r] = u;
+        else a2[r] = u;
       }
     }
     off += ak;
   }
-  if (row < A.nbr) epi(row, a1, a2);
+#pragma unroll
+  for (int q = 0; q < BR; q++) {
+    a1[q] = group_sum<G>(a1[q]);
+    if constexpr (TWO) a2[q] = group_sum<G>(a2[q]);
+  }
+  if (row < A.nbr && j == 0) {
+    if constexpr (TWO) epi(row, a1, a2);
+    else epi(row, a1);
+  }
 }
 
-template <int BR, int BC, typename TA, typename TX, typename Epi>
-inline void jag2_spmv(const Jag2View<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
+template <int BR, int BC, bool TWO, typename TA, typename TX, typename Epi>
+inline void jag_launch(const JagView<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
   if (A.nbr <= 0) return;
   const int threads = 256;
   const int64_t blocks = ((int64_t)A.nslice * kSellH + threads - 1) / threads;
-  k_jag2_spmv<BR, BC, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi);
+  switch (A.g) {
+    case 1: k_jag_spmv<BR, BC, 1, TWO, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+    case 4: k_jag_spmv<BR, BC, 4, TWO, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+    case 8: k_jag_spmv<BR, BC, 8, TWO, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+    case 16: k_jag_spmv<BR, BC, 16, TWO, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+    default: k_jag_spmv<BR, BC, 32, TWO, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+  }
   FS_LAUNCHED();
+}
+template <int BR, int BC, typename TA, typename TX, typename Epi>
+inline void jag2_spmv(const JagView<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
+  jag_launch<BR, BC, true>(A, x, epi, s);
 }
 
 template <int BR, int BC, typename TA, typename TX, typename Epi>

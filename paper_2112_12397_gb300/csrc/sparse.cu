@@ -1428,47 +1428,50 @@ Sell<T> to_sell(const BsrView<TI> &A, cudaStream_t s) {
   return S;
 }
 namespace {
+// a slice of rows [r0, r0 + 32 / g) starts after all entries of the rows before
 template <typename TQ>
-__global__ void k_jag2_offsets(BsrView<double> P, BsrView<TQ> Q, int nslice, int64_t *sp) {
+__global__ void k_jag_offsets(BsrView<double> P, BsrView<TQ> Q, bool two, int rps, int nslice, int64_t *sp) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nslice;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i * kSellH < P.nbr ? i * kSellH : P.nbr;
-    sp[i] = (int64_t)P.rp[r] + Q.rp[r];
+    const int64_t r = i * rps < P.nbr ? i * rps : P.nbr;
+    sp[i] = (int64_t)P.rp[r] + (two ? Q.rp[r] : 0);
   }
 }
 
-// one warp per slice, the slot walk of k_jag2_spmv
+// one warp per slice, the slot walk of k_jag_spmv
 template <typename T, typename TQ>
-__global__ void k_jag2_fill(BsrView<double> P, BsrView<TQ> Q, int nslice, const int64_t *sp, int2 *len, int *ci,
-                            T *val) {
+__global__ void k_jag_fill(BsrView<double> P, BsrView<TQ> Q, bool two, int g, int nslice, const int64_t *sp,
+                           int2 *len, int *ci, T *val) {
   const int bs = P.br * P.bc;
   const int lane = (int)(threadIdx.x % kSellH);
+  const int j = lane % g, rps = kSellH / g;
   const unsigned below = (1u << lane) - 1u;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) / kSellH;
   for (int64_t sl = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kSellH; sl < nslice; sl += nwarp) {
-    const int64_t row = sl * kSellH + lane;
+    const int64_t row = sl * rps + lane / g;
     const bool real = row < P.nbr;
     const int p0 = real ? P.rp[row] : 0, lp = real ? P.rp[row + 1] - p0 : 0;
-    const int q0 = real ? Q.rp[row] : 0, lq = real ? Q.rp[row + 1] - q0 : 0;
+    const int q0 = real && two ? Q.rp[row] : 0, lq = real && two ? Q.rp[row + 1] - q0 : 0;
     const int L = lp + lq;
-    if (real) len[row] = make_int2(lp, L);
-    int w = L;
+    if (real && j == 0) len[row] = make_int2(lp, L);
+    int w = (L + g - 1) / g;
     for (int o = kSellH / 2; o; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
     int64_t off = sp[sl];
     for (int k = 0; k < w; k++) {
-      const bool on = k < L;
+      const int e = j + g * k;
+      const bool on = e < L;
       const unsigned act = __ballot_sync(0xffffffffu, on);
       const int ak = __popc(act);
       if (on) {
         const int rk = __popc(act & below);
         T *v = val + off * bs + rk;
-        if (k < lp) {
-          ci[off + rk] = P.ci[p0 + k];
-          for (int q = 0; q < bs; q++) v[(int64_t)q * ak] = (T)P.val[(int64_t)(p0 + k) * bs + q];
+        if (e < lp) {
+          ci[off + rk] = P.ci[p0 + e];
+          for (int q = 0; q < bs; q++) v[(int64_t)q * ak] = (T)P.val[(int64_t)(p0 + e) * bs + q];
         } else {
-          const int kk = k - lp;
-          ci[off + rk] = Q.ci[q0 + kk];
-          for (int q = 0; q < bs; q++) v[(int64_t)q * ak] = (T)Q.val[(int64_t)(q0 + kk) * bs + q];
+          const int ee = e - lp;
+          ci[off + rk] = Q.ci[q0 + ee];
+          for (int q = 0; q < bs; q++) v[(int64_t)q * ak] = (T)Q.val[(int64_t)(q0 + ee) * bs + q];
         }
       }
       off += ak;
@@ -1478,27 +1481,32 @@ __global__ void k_jag2_fill(BsrView<double> P, BsrView<TQ> Q, int nslice, const 
 }  // namespace
 
 template <typename T, typename TQ>
-Jag2<T> to_jag2(const BsrView<double> &P, const BsrView<TQ> &Q, cudaStream_t s) {
-  FS_REQUIRE(P.nbr == Q.nbr && P.nbc == Q.nbc && P.br == Q.br && P.bc == Q.bc, FC_INTERNAL,
-             "to_jag2: the two matrices differ in shape");
-  Jag2<T> J;
-  J.nbr = P.nbr; J.nbc = P.nbc; J.br = P.br; J.bc = P.bc; J.nnzb = P.nnzb + Q.nnzb;
-  J.nslice = (P.nbr + kSellH - 1) / kSellH;
+Jag<T> to_jag(const BsrView<double> &P, const BsrView<TQ> *Q, int g, cudaStream_t s) {
+  FS_REQUIRE(g == 1 || g == 4 || g == 8 || g == 16 || g == 32, FC_INTERNAL, "to_jag: lanes per row");
+  FS_REQUIRE(!Q || (P.nbr == Q->nbr && P.nbc == Q->nbc && P.br == Q->br && P.bc == Q->bc), FC_INTERNAL,
+             "to_jag: the two matrices differ in shape");
+  const BsrView<TQ> q = Q ? *Q : BsrView<TQ>();
+  Jag<T> J;
+  J.nbr = P.nbr; J.nbc = P.nbc; J.br = P.br; J.bc = P.bc; J.g = g;
+  J.nnzb = P.nnzb + (Q ? Q->nnzb : 0);
+  const int rps = kSellH / g;
+  J.nslice = (P.nbr + rps - 1) / rps;
   J.sp.alloc((size_t)J.nslice + 1);
   J.len.alloc((size_t)std::max(P.nbr, 1));
   J.ci.alloc((size_t)J.nnzb + kSellH);
   J.val.alloc(((size_t)J.nnzb + kSellH) * P.br * P.bc);
-  k_jag2_offsets<TQ><<<blocks_for(J.nslice + 1, 256, kSMs * 4), 256, 0, s>>>(P, Q, J.nslice, J.sp.p);
+  k_jag_offsets<TQ><<<blocks_for(J.nslice + 1, 256, kSMs * 4), 256, 0, s>>>(P, q, Q != nullptr, rps, J.nslice,
+                                                                            J.sp.p);
   FS_LAUNCHED();
   if (J.nslice) {
-    k_jag2_fill<T, TQ><<<blocks_for((int64_t)J.nslice * kSellH, 128, kSMs * 16), 128, 0, s>>>(
-        P, Q, J.nslice, J.sp.p, J.len.p, J.ci.p, J.val.p);
+    k_jag_fill<T, TQ><<<blocks_for((int64_t)J.nslice * kSellH, 128, kSMs * 16), 128, 0, s>>>(
+        P, q, Q != nullptr, g, J.nslice, J.sp.p, J.len.p, J.ci.p, J.val.p);
     FS_LAUNCHED();
   }
   return J;
 }
-template Jag2<float> to_jag2<float, float>(const BsrView<double> &, const BsrView<float> &, cudaStream_t);
-template Jag2<double> to_jag2<double, double>(const BsrView<double> &, const BsrView<double> &, cudaStream_t);
+template Jag<float> to_jag<float, float>(const BsrView<double> &, const BsrView<float> *, int, cudaStream_t);
+template Jag<double> to_jag<double, double>(const BsrView<double> &, const BsrView<double> *, int, cudaStream_t);
 
 template Sell<float> to_sell<float, double>(const BsrView<double> &, cudaStream_t);
 template Sell<double> to_sell<double, double>(const BsrView<double> &, cudaStream_t);
