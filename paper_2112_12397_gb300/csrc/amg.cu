@@ -61,6 +61,14 @@ inline int jag_lanes_for(int64_t nnzb, int nbr) {
 #endif
   return jag_lanes(nnzb, nbr);
 }
+// chunked BSR for long-row operators and restrictions; test hook:
+// FS_CHUNKED=0 keeps the lane-group BSR kernel, so that a test can compare the two
+inline bool chunked_rows() {
+#ifdef FS_TEST_HOOKS
+  if (const char *ev = std::getenv("FS_CHUNKED")) return std::strtol(ev, nullptr, 10) != 0;
+#endif
+  return true;
+}
 // the prolongation fused with the first post-smoothing step; test hook:
 // FS_FUSE_PROLONG=0 keeps them apart, so that a test can compare the two
 inline bool fuse_prolongation() {
@@ -981,6 +989,11 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
     c.op.bv = c.S;
     c.op.nnzb = L.S.nnzb;
     c.op.nbr = L.nb;
+    if (!sell && !last && chunked_rows() && !rowcta_rows(L.S.nnzb, L.nb)) {
+      c.Sk = to_chunked<TP>(L.S.view(), lanes_for(L.S.nnzb, L.nb, L.B * L.B), s);
+      c.op.chunk = true;
+      c.op.kv = c.Sk.view();
+    }
     if (!last) {
       c.Ps = to_sell<TP>(L.P.view(), s);
       // levels with few rows prolong through the lane-group BSR kernel: a
@@ -994,6 +1007,8 @@ void prepare_cycle(Hierarchy &H, std::vector<LevelCycle<TP>> &C, cudaStream_t s)
       } else {
         c.P = BsrView<TP>();
       }
+      if (chunked_rows() && L.R.nbr > 0 && !rowcta_rows(L.R.nnzb, L.R.nbr))
+        c.Rk = to_chunked<TP>(L.R.view(), lanes_for(L.R.nnzb, L.R.nbr, L.B * L.B), s);
       // the prolongation and the first post-smoothing step read P and S P
       // (in the cycle precision: S P is formed in it by the Galerkin product)
       if (fuse_prolongation() && L.nb > 0) {
@@ -1233,7 +1248,8 @@ double cheb_bytes(const LevelOp<TP> &S, bool read_d) {
 
 template <int BR, int BC, typename TP, typename TX, typename Epi>
 inline void op_spmv(const LevelOp<TP> &A, const TX *x, const Epi &e, cudaStream_t s) {
-  if (A.sell) sell_spmv<BR, BC>(A.sv, x, e, s);
+  if (A.chunk) chunk_spmv<BR, BC>(A.kv, x, e, s);
+  else if (A.sell) sell_spmv<BR, BC>(A.sv, x, e, s);
   else spmv<BR, BC>(A.bv, x, e, s);
 }
 template <int BR, int BC, typename TP, typename TX, typename TY, typename TZ>
@@ -1320,7 +1336,12 @@ void cycle_level(Hierarchy &H, std::vector<LevelCycle<TP>> &C, int l, const TP *
   if (pf) pf->stop(PK_RESID0, s, cheb_bytes<B, TP>(c.op, false) - (double)c.op.nbr * B * B * sizeof(TP));
   LevelCycle<TP> &cn = C[l + 1];
   if (pf) pf->start(PK_RESTRICT0, s);
-  spmv_axpby<B, B>(c.R, c.r.p, cn.f.p, 1.0, 0.0, (const TP *)nullptr, s);
+  if (c.Rk.nbr > 0) {
+    EpiAxpby<B, TP, TP, TP> e{cn.f.p, nullptr, (TP)1, (TP)0};
+    chunk_spmv<B, B>(c.Rk.view(), c.r.p, e, s);
+  } else {
+    spmv_axpby<B, B>(c.R, c.r.p, cn.f.p, 1.0, 0.0, (const TP *)nullptr, s);
+  }
   if (pf) pf->stop(PK_RESTRICT0, s, (double)c.R.nnzb * (B * B * sizeof(TP) + 4) + (double)c.R.nbr * 4);
   if (pf) pf->start(PK_COARSE0, s);
   if (l == 0 && H.graphs && L > 2) coarse_graph<B, TP, TR>(H, C, s);

@@ -47,6 +47,8 @@ struct LevelSetup {
 template <typename TP>
 struct LevelOp {
   bool sell = true;
+  bool chunk = false;            // long rows in chunked BSR
+  ChunkView<TP> kv;
   SellView<TP> sv;
   BsrView<TP> bv;
   int64_t nnzb = 0;
@@ -64,6 +66,7 @@ struct LevelCycle {
   Sell<TP> Ss, Ps;               // sliced-ELL copies of S and P used by the cycle
   Sell<TP> SsT;                  // S^T for the transposed cycle (adjoint solves)
   Jag<TP> PSP;                   // [P | S P] for the fused prolongation and first post-smoothing step
+  Chunked<TP> Sk, Rk;            // chunked copies of a long-row S and of R
   DBuf<TP> DinvT;                // transposed diagonal blocks
   DBuf<TP> Dinv_own;
   DBuf<TP> f, x, xa, d, r;       // right-hand side, iterate (two buffers), direction, residual

@@ -1508,6 +1508,60 @@ Jag<T> to_jag(const BsrView<double> &P, const BsrView<TQ> *Q, int g, cudaStream_
 template Jag<float> to_jag<float, float>(const BsrView<double> &, const BsrView<float> *, int, cudaStream_t);
 template Jag<double> to_jag<double, double>(const BsrView<double> &, const BsrView<double> *, int, cudaStream_t);
 
+namespace {
+__global__ void k_chunk_count(BsrView<double> A, int g, int *cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.nbr; r += (int64_t)gridDim.x * blockDim.x)
+    cnt[r] = (A.rp[r + 1] - A.rp[r] + g - 1) / g;
+}
+
+// one warp per row: position p of the row's padded chunks is entry p of the
+// row (chunk p / g, lane p % g)
+template <typename T>
+__global__ void k_chunk_fill(BsrView<double> A, int g, const int *rc, int *ci, T *val) {
+  const int bs = A.br * A.bc;
+  const int lane = (int)(threadIdx.x & 31);
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < A.nbr; r += nwarp) {
+    const int b0 = A.rp[r], len = A.rp[r + 1] - b0;
+    const int64_t c0 = rc[r];
+    const int npos = (rc[r + 1] - rc[r]) * g;
+    for (int p = lane; p < npos; p += 32) {
+      const int64_t c = c0 + p / g;
+      const int j = p % g;
+      const bool real = p < len;
+      ci[c * g + j] = real ? A.ci[b0 + p] : 0;
+      for (int q = 0; q < bs; q++)
+        val[(c * bs + q) * g + j] = real ? (T)A.val[(int64_t)(b0 + p) * bs + q] : T(0);
+    }
+  }
+}
+}  // namespace
+
+template <typename T>
+Chunked<T> to_chunked(const BsrView<double> &A, int g, cudaStream_t s) {
+  FS_REQUIRE(g == 4 || g == 8 || g == 16 || g == 32, FC_INTERNAL, "to_chunked: lanes per row");
+  Chunked<T> C;
+  C.nbr = A.nbr; C.nbc = A.nbc; C.br = A.br; C.bc = A.bc; C.g = g; C.nnzb = A.nnzb;
+  C.rc.alloc((size_t)A.nbr + 1);
+  if (A.nbr == 0) {
+    FS_CUDA(cudaMemsetAsync(C.rc.p, 0, sizeof(int), s));
+    return C;
+  }
+  DBuf<int> cnt((size_t)A.nbr + 1);
+  k_chunk_count<<<blocks_for(A.nbr, 256, kSMs * 8), 256, 0, s>>>(A, g, cnt.p);
+  FS_LAUNCHED();
+  C.nchunk = exclusive_scan(cnt.p, C.rc.p, A.nbr, s);
+  C.ci.alloc((size_t)std::max<int64_t>(C.nchunk, 1) * g);
+  C.val.alloc((size_t)std::max<int64_t>(C.nchunk, 1) * A.br * A.bc * g);
+  if (C.nchunk) {
+    k_chunk_fill<T><<<blocks_for((int64_t)A.nbr * 32, 256, kSMs * 16), 256, 0, s>>>(A, g, C.rc.p, C.ci.p, C.val.p);
+    FS_LAUNCHED();
+  }
+  return C;
+}
+template Chunked<float> to_chunked<float>(const BsrView<double> &, int, cudaStream_t);
+template Chunked<double> to_chunked<double>(const BsrView<double> &, int, cudaStream_t);
+
 template Sell<float> to_sell<float, double>(const BsrView<double> &, cudaStream_t);
 template Sell<double> to_sell<double, double>(const BsrView<double> &, cudaStream_t);
 template Sell<float> to_sell<float, float>(const BsrView<float> &, cudaStream_t);

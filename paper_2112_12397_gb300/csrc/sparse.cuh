@@ -3,6 +3,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "spmv.cuh"
 
 namespace fs {
 
@@ -53,6 +54,10 @@ Bsr<double> spadd(const BsrView<double> &A, const BsrView<double> &B, double alp
 // Deep copy of a BSR view into an owned matrix (same value type).
 template <typename TO, typename TI>
 Bsr<TO> copy_cast(const BsrView<TI> &A, cudaStream_t s);
+
+// Chunked copy (values cast to T) of a BSR matrix with g lanes per row.
+template <typename T>
+Chunked<T> to_chunked(const BsrView<double> &A, int g, cudaStream_t s);
 
 // Upload a host BSR (double) into an owned device matrix.
 Bsr<double> upload_bsr(int nbr, int nbc, int br, int bc, int64_t nnzb, const int *rp_dev,

@@ -210,6 +210,11 @@ __global__ void __launch_bounds__(256) k_bsr_spmv_rowcta(BsrView<TA> A, const TX
 // kRowCtaMaxRows rows, take one block of threads each
 constexpr double kRowCtaMinMean = 200.0;
 constexpr int kRowCtaMaxRows = 8 * 152 * 4;
+// a matrix with few, very long rows (coarse restrictions) goes to the
+// one-block-per-row kernel
+inline bool rowcta_rows(int64_t nnzb, int nbr) {
+  return nbr > 0 && nbr <= kRowCtaMaxRows && (double)nnzb / nbr >= kRowCtaMinMean;
+}
 
 // lanes per row from the mean number of blocks per row (sweeps on the
 // 128^3 workload, coarse part of the cycle: for the ~69-block rows of the
@@ -243,7 +248,7 @@ inline void spmv_g(const BsrView<TA> &A, const TX *x, const Epi &epi, cudaStream
 template <int BR, int BC, typename TA, typename TX, typename Epi>
 inline void spmv(const BsrView<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
   if (A.nbr <= 0) return;
-  if (A.nbr <= kRowCtaMaxRows && (double)A.nnzb / A.nbr >= kRowCtaMinMean) {
+  if (rowcta_rows(A.nnzb, A.nbr)) {
     k_bsr_spmv_rowcta<BR, BC, TA, TX, Epi><<<(unsigned)A.nbr, 256, 0, s>>>(A, x, epi);
     FS_LAUNCHED();
     return;
@@ -254,6 +259,83 @@ inline void spmv(const BsrView<TA> &A, const TX *x, const Epi &epi, cudaStream_t
     case 8: spmv_g<BR, BC, 8>(A, x, epi, s); break;
     default: spmv_g<BR, BC, 4>(A, x, epi, s); break;
   }
+}
+
+// Chunked BSR for long rows: a row's blocks in chunks of G (the lanes of
+// its group), each chunk stored slot-major and 32-byte aligned: G column
+// indices, then each of the BR*BC block scalars as G consecutive values; the
+// last chunk of a row is padded with zero blocks of column 0.  Lane j of a
+// group takes entry j of every chunk of its row, so each load a group issues
+// is G consecutive values (one 32-byte sector for G = 8 floats) where the BSR
+// kernel's lanes read their 36-byte blocks scalar by scalar (ncu: ~20 sectors
+// per load request there, the load queue the first stall).
+template <typename T>
+struct ChunkView {
+  int nbr = 0, nbc = 0, br = 0, bc = 0, g = 8;
+  int64_t nnzb = 0;                 // blocks of the matrix (without the padding)
+  const int *rc = nullptr;          // nbr + 1 chunk offsets
+  const int *ci = nullptr;          // chunks * g
+  const T *val = nullptr;           // chunks * br * bc * g
+};
+
+template <typename T>
+struct Chunked {
+  int nbr = 0, nbc = 0, br = 0, bc = 0, g = 8;
+  int64_t nnzb = 0, nchunk = 0;
+  DBuf<int> rc, ci;
+  DBuf<T> val;
+  ChunkView<T> view() const {
+    ChunkView<T> v;
+    v.nbr = nbr; v.nbc = nbc; v.br = br; v.bc = bc; v.g = g; v.nnzb = nnzb;
+    v.rc = rc.p; v.ci = ci.p; v.val = val.p;
+    return v;
+  }
+};
+
+template <int BR, int BC, int G, typename TA, typename TX, typename Epi>
+__global__ void __launch_bounds__(256) k_chunk_spmv(ChunkView<TA> A, const TX *__restrict__ x, Epi epi) {
+  constexpr int BS = BR * BC;
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const bool valid = row < A.nbr;
+  TA acc[BR];
+#pragma unroll
+  for (int q = 0; q < BR; q++) acc[q] = TA(0);
+  if (valid) {
+    const int c0 = __ldg(A.rc + row), c1 = __ldg(A.rc + row + 1);
+#pragma unroll 4
+    for (int c = c0; c < c1; c++) {
+      const int col = __ldg(A.ci + (int64_t)c * G + lane);
+      const TA *__restrict__ v = A.val + (int64_t)c * BS * G + lane;
+      TA a[BS];
+#pragma unroll
+      for (int q = 0; q < BS; q++) a[q] = __ldg(v + q * G);
+      TA xv[BC];
+#pragma unroll
+      for (int j = 0; j < BC; j++) xv[j] = (TA)__ldg(x + (int64_t)col * BC + j);
+#pragma unroll
+      for (int r = 0; r < BR; r++)
+#pragma unroll
+        for (int j = 0; j < BC; j++) acc[r] += a[r * BC + j] * xv[j];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < BR; q++) acc[q] = group_sum<G>(acc[q]);
+  if (valid && lane == 0) epi(row, acc);
+}
+
+template <int BR, int BC, typename TA, typename TX, typename Epi>
+inline void chunk_spmv(const ChunkView<TA> &A, const TX *x, const Epi &epi, cudaStream_t s) {
+  if (A.nbr <= 0) return;
+  const int threads = 256;
+  const int64_t blocks = ((int64_t)A.nbr * A.g + threads - 1) / threads;
+  switch (A.g) {
+    case 32: k_chunk_spmv<BR, BC, 32, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+    case 16: k_chunk_spmv<BR, BC, 16, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+    case 8: k_chunk_spmv<BR, BC, 8, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+    default: k_chunk_spmv<BR, BC, 4, TA, TX, Epi><<<(unsigned)blocks, threads, 0, s>>>(A, x, epi); break;
+  }
+  FS_LAUNCHED();
 }
 
 // y = alpha A x + beta z

@@ -680,3 +680,38 @@ def test_fused_prolongation_equals_the_two_passes(fs, name, monkeypatch):
         assert rel(xf.cpu().numpy(), xa.cpu().numpy()) <= 1e-12, hier
     apart.close()
     fused.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["rects16", "network16"])
+def test_chunked_rows_equal_lane_group_bsr(fs, name, precision, monkeypatch):
+    """Long-row level operators and restrictions in chunked BSR (a row's
+    blocks in chunks of G, each stored slot-major, the last padded with zero
+    blocks) against the same cycle on the lane-group BSR kernel (the test
+    build with FS_CHUNKED=0): lane j sums the row's blocks j, j + G, ... in the
+    same order in both, and the padding adds exact zeros, so every V-cycle
+    and application agrees bit for bit."""
+    monkeypatch.setenv("FS_CHUNKED", "0")
+    preset, over, cm, cmp = CASES[name]
+    P = fracgen.generate(preset, **over)
+    opt = dict(precision=precision, coarse_max=cm, coarse_max_p=cmp)
+    bsr = fs.context_for(P, fs.default_options(**opt), lib=fs.load_test_hooks())
+    monkeypatch.delenv("FS_CHUNKED")
+    chunked = fs.context_for(P, fs.default_options(**opt))
+    assert chunked.num_levels(fs.FC_H_TUP_U) >= 3   # a long-row level below the finest
+    for hier, M, B, o in _hierarchies(P, cm, cmp):
+        n = M().shape[0]
+        f = cuda(np.random.default_rng(hier + 40).standard_normal(n))
+        xa = torch.zeros(n, dtype=torch.float64, device="cuda")
+        xb = torch.zeros_like(xa)
+        bsr.vcycle(hier, f, xa)
+        chunked.vcycle(hier, f, xb)
+        assert torch.equal(xa, xb), hier
+    w = cuda(np.random.default_rng(41).standard_normal(P.n))
+    for variant in ("tpu", "tup"):
+        va, vb = (torch.zeros(P.n, dtype=torch.float64, device="cuda") for _ in range(2))
+        bsr.apply_prec(variant, w, va)
+        chunked.apply_prec(variant, w, vb)
+        assert torch.equal(va, vb), variant
+    bsr.close()
+    chunked.close()
