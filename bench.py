@@ -473,6 +473,47 @@ def ours(args, rank, world, local_rank):
     # max over ranks
     step_ms = max_over_ranks(total_ms / args.steps, dist)
 
+    # end to end through the C-ABI with host buffers: fc_setup_host copies
+    # the seven blocks from pinned host memory, fc_solve_host copies b in and
+    # x out.  Measured right after the headline steps, with the one context a
+    # user's process holds: after the FP64, variant and update legs (contexts
+    # of tens of GB created and freed) the same pinned copies ran at ~54
+    # instead of ~206 GB/s.
+    e2e = None
+    if args.e2e_steps > 0:
+        host = {}
+        h2d = 0
+        for name, t in blocks.items():
+            rp, ci, val = (a.cpu().pin_memory() for a in t[:3])
+            host[name] = (rp, ci, val) + tuple(t[3:])
+            h2d += sum(a.numel() * a.element_size() for a in (rp, ci, val))
+        hb = torch.from_numpy(P.b).pin_memory()
+        hx = torch.zeros_like(hb).pin_memory()
+        h2d += hb.numel() * 8
+        d2h = hx.numel() * 8
+        times, t_setup = [], []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.setup_host(host, P.n_node, P.n_face)
+            t1 = time.perf_counter()
+            rc, it, rr = ctx.solve_host(args.variant, hb, hx, args.tol, args.maxit, allow_fail=True)
+            torch.cuda.synchronize()
+            if k > 0:
+                times.append(time.perf_counter() - t0)
+                t_setup.append(t1 - t0)
+        # the host-to-device bandwidth alone: one pinned copy of A's values
+        a_h, a_d = host["A"][2], blocks["A"][2]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a_d.copy_(a_h, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = a_h.numel() * 8 / (time.perf_counter() - t0) / 1e9
+        e2e = {"value": statistics.mean(times), "unit": "s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "api": "fc_setup_host + fc_solve_host",
+               "setup_host_s": statistics.mean(t_setup), "pinned_h2d_GBps": h2d_gbs}
+        del host
+
     # FP64 form on the same workload for the FP32-vs-FP64 comparison
     fp64 = None
     if args.precision == "mixed" and args.fp64_steps > 0:
@@ -589,43 +630,6 @@ def ours(args, rank, world, local_rank):
         adjoint = {"solve_s": statistics.mean(ts) / 1e3, "iters": it_a, "relres": rr_a,
                    "aperture_gradient_ms": statistics.mean(tg), "dk_entries": int(dk["val"].numel())}
 
-    # end to end through the C-ABI with host buffers: fc_setup_host copies
-    # the seven blocks from pinned host memory, fc_solve_host copies b in and
-    # x out
-    e2e = None
-    if args.e2e_steps > 0:
-        host = {}
-        h2d = 0
-        for name, t in blocks.items():
-            rp, ci, val = (a.cpu().pin_memory() for a in t[:3])
-            host[name] = (rp, ci, val) + tuple(t[3:])
-            h2d += sum(a.numel() * a.element_size() for a in (rp, ci, val))
-        hb = torch.from_numpy(P.b).pin_memory()
-        hx = torch.zeros_like(hb).pin_memory()
-        h2d += hb.numel() * 8
-        d2h = hx.numel() * 8
-        times, t_setup = [], []
-        for k in range(args.e2e_steps + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ctx.setup_host(host, P.n_node, P.n_face)
-            t1 = time.perf_counter()
-            rc, it, rr = ctx.solve_host(args.variant, hb, hx, args.tol, args.maxit, allow_fail=True)
-            torch.cuda.synchronize()
-            if k > 0:
-                times.append(time.perf_counter() - t0)
-                t_setup.append(t1 - t0)
-        # the host-to-device bandwidth alone: one pinned copy of A's values
-        a_h, a_d = host["A"][2], blocks["A"][2]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        a_d.copy_(a_h, non_blocking=True)
-        torch.cuda.synchronize()
-        h2d_gbs = a_h.numel() * 8 / (time.perf_counter() - t0) / 1e9
-        e2e = {"value": statistics.mean(times), "unit": "s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "api": "fc_setup_host + fc_solve_host",
-               "setup_host_s": statistics.mean(t_setup), "pinned_h2d_GBps": h2d_gbs}
-        del host
 
     # the instance assembled on the device by fc_generate (same seed and
     # workload), and a step that starts from the seed: generate + setup +
