@@ -16,12 +16,14 @@ Workload (default): 128^3 unit-cube grid, ten seeded fracture rectangles,
 for the paper's private meshes.  Matrices are several GB, far above the
 129 MB L2, so no flush is needed between steps.
 
---impl reference times the CPU oracle (the tests' reference implementation)
-on a bounded sample: the same workload family at --cpu-sample-n cells per
-side (32 by default, about 4 s per solve on one core), reported as measured,
-with the sample's own size in its config.  --cpu-full runs the oracle at the
-workload's full size instead (minutes per solve at 128^3; not part of the
-default run).
+The bench line's cpu_baseline times the CPU oracle (the tests' reference
+implementation) once on a bounded sample, the same workload family at
+--cpu-sample-n cells per side (40 by default, 10-20 s on one core); --impl
+reference times it once per warm-up and timed step at --ref-sample-n cells
+per side (32 by default, about 4 s per solve), so that the whole reference
+run ends within minutes.  Both are reported as measured, with the sample's
+own size.  --cpu-full runs the oracle at the workload's full size instead
+(minutes per solve at 128^3; not part of the default run).
 """
 from __future__ import annotations
 
@@ -71,8 +73,10 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=1,
                     help="timed adjoint solves + aperture gradients after the timed region (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--cpu-sample-n", type=int, default=32,
-                    help="grid size of the oracle's bounded sample (cells per side)")
+    ap.add_argument("--cpu-sample-n", type=int, default=40,
+                    help="grid size of the cpu_baseline's bounded oracle sample (cells per side)")
+    ap.add_argument("--ref-sample-n", type=int, default=32,
+                    help="grid size of the reference arm's oracle sample per step (cells per side)")
     ap.add_argument("--cpu-full", action="store_true",
                     help="time the oracle at the workload's full size (long: minutes per solve)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -186,15 +190,15 @@ def run_oracle_sample(workload, n_cells, variant, tol, maxit, timeout=900):
 FULL_N = {"rects128": 128, "planes64": 64, "network96": 96, "tiny8": 8}
 
 
-def oracle_cells(args) -> int:
+def oracle_cells(args, sample_n: int) -> int:
     """Cells per side of the oracle's run: the bounded sample, or the full
     workload with --cpu-full (or when the sample is not smaller)."""
     full = args.N or FULL_N[args.workload]
-    return full if args.cpu_full else min(args.cpu_sample_n, full)
+    return full if args.cpu_full else min(sample_n, full)
 
 
 def cpu_baseline(args):
-    n = oracle_cells(args)
+    n = oracle_cells(args, args.cpu_sample_n)
     s = run_oracle_sample(args.workload, n, args.variant, args.tol, args.maxit,
                           timeout=7200 if args.cpu_full else 900)
     t = s["setup"] + s["solve"]
@@ -213,7 +217,7 @@ def reference(args, rank):
         return
     import fracgen
     fracgen.build()
-    n = oracle_cells(args)
+    n = oracle_cells(args, args.ref_sample_n)
     times, setups, solves = [], [], []
     last = None
     for k in range(args.warmup + args.steps):
@@ -476,9 +480,8 @@ def ours(args, rank, world, local_rank):
     # end to end through the C-ABI with host buffers: fc_setup_host copies
     # the seven blocks from pinned host memory, fc_solve_host copies b in and
     # x out.  Measured right after the headline steps, with the one context a
-    # user's process holds: after the FP64, variant and update legs (contexts
-    # of tens of GB created and freed) the same pinned copies ran at ~54
-    # instead of ~206 GB/s.
+    # user's process holds; pinned_h2d_GBps records the host-to-device rate of
+    # this run (it varies between runs on these machines).
     e2e = None
     if args.e2e_steps > 0:
         host = {}
