@@ -18,7 +18,7 @@ for the paper's private meshes.  Matrices are several GB, far above the
 
 The bench line's cpu_baseline times the CPU oracle (the tests' reference
 implementation) once on a bounded sample, the same workload family at
---cpu-sample-n cells per side (40 by default, 10-20 s on one core); --impl
+--cpu-sample-n cells per side (40 by default, about 9 s on one Grace core); --impl
 reference times it once per warm-up and timed step at --ref-sample-n cells
 per side (32 by default, about 4 s per solve), so that the whole reference
 run ends within minutes.  Both are reported as measured, with the sample's
