@@ -292,6 +292,13 @@ struct Chunked {
   }
 };
 
+#ifndef FS_CHUNK_UNROLL
+#define FS_CHUNK_UNROLL 4
+#endif
+// chunks of a row in flight per lane (128^3 sweep, coarse part of the cycle:
+// 2 / 4 / 8 gave 0.302 / 0.303 / 0.307 ms: the pass is latency-bound either way)
+constexpr int kChunkUnroll = FS_CHUNK_UNROLL;
+
 template <int BR, int BC, int G, typename TA, typename TX, typename Epi>
 __global__ void __launch_bounds__(256) k_chunk_spmv(ChunkView<TA> A, const TX *__restrict__ x, Epi epi) {
   constexpr int BS = BR * BC;
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(256) k_chunk_spmv(ChunkView<TA> A, const TX *_
   for (int q = 0; q < BR; q++) acc[q] = TA(0);
   if (valid) {
     const int c0 = __ldg(A.rc + row), c1 = __ldg(A.rc + row + 1);
-#pragma unroll 4
+#pragma unroll kChunkUnroll
     for (int c = c0; c < c1; c++) {
       const int col = __ldg(A.ci + (int64_t)c * G + lane);
       const TA *__restrict__ v = A.val + (int64_t)c * BS * G + lane;
